@@ -1,0 +1,393 @@
+"""Benchmark: the rational-program hot path on GB300.
+
+One step = the whole path over one batch of synthetic input:
+  rp_fit          8192 fits (1024 kernels x 8 metrics), 512 samples each,
+                  total degree <= 3 (20 + 20 monomials), lognormal noise 1%
+  rp_program_pack the 1024 kernels' programs (66 configurations x 8 metrics)
+  rp_eval_search  1e6 queries x 66 configurations, per-query argmin
+Metric: rational fits/s of the whole step (the step's queries/s is reported
+beside it).  Inputs are resident in HBM before timing; L2 is flushed
+(256 MiB write) between timed steps, outside the timed events.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rational fits/s and MWP-CWP evals/s (argmin queries/s), batched vs plain, at stated tol"
+N_KERNELS, N_METRICS, M_SAMPLES, DEGREE = 1024, 8, 512, 3
+N_QUERIES = 1_000_000
+SEED = 20190602
+WORKLOAD = ("batched fit 1024 kernels x 8 metrics, 512 samples, deg<=3 (TF32-class tolerance "
+            "path: fp32), then MWP-CWP search 1e6 queries x 66 configs")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_count, sm_mhz):
+    # 128 FP32 lanes per SM, an FMA counts 2 flops
+    return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def search_flops_per_query(d):
+    # per (query, configuration): 8 metrics x (2 Horner polynomials of degree d
+    # in FMA = 4d flops, 1 division) + 36 flops of MWP-CWP arithmetic;
+    # per query: 8 affine maps of N (16 flops)
+    return 66 * (8 * (4 * d + 1) + 36) + 16
+
+
+def fit_flops_per_fit(m, d):
+    # the augmented Gram product, symmetric: m * n_aug * (n_aug + 1) flops
+    nm = (d + 1) * (d + 2) * (d + 3) // 6
+    naug = 2 * nm
+    return m * naug * (naug + 1)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        self.idx = gpu_index
+
+    def start(self):
+        try:
+            self.path = f"/tmp/rp_clocks_{os.getpid()}.csv"
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), active=parts[4],
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                            ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows),
+                "sm_max_mhz": max(r["smax"] for r in rows), "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def dist_setup(ngpus):
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def make_inputs(seed):
+    import workloads as W
+    inst = W.batched_instance(N_KERNELS, seed=seed, m=M_SAMPLES, d=DEGREE)
+    q = W.queries(N_QUERIES, N_KERNELS, seed=seed + 1)
+    gd = (np.arange(N_KERNELS) % 2 + 1).astype(np.int32)
+    return inst, q, gd
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+
+def oracle_rates(inst, q, gd, budget_s=20.0):
+    """Time the oracle on bounded samples of the workload; returns per-unit
+    seconds for fit, pack (per kernel) and search, plus what was sampled."""
+    import oracle
+    import workloads as W
+    ncores = os.cpu_count() or 1
+    oracle.set_threads(ncores)
+    off = inst["fit_off"]
+    # fits: whole kernels (8 fits) at a time until ~budget/2
+    t0 = time.perf_counter()
+    nk = 0
+    res = []
+    while time.perf_counter() - t0 < budget_s * 0.45 and nk < N_KERNELS:
+        k1 = min(N_KERNELS, nk + max(1, ncores // 2))
+        a, b = off[nk * N_METRICS], off[k1 * N_METRICS]
+        sub_off = off[nk * N_METRICS:k1 * N_METRICS + 1] - a
+        r = oracle.fit(inst["x"][:, a:b], inst["y"][a:b], sub_off, inst["degree"][nk * N_METRICS:k1 * N_METRICS])
+        res.append(r)
+        nk = k1
+    t_fit = time.perf_counter() - t0
+    coef = np.concatenate([r["coef"] for r in res])
+    box = np.concatenate([r["box"] for r in res])
+    deg = np.concatenate([r["degree"] for r in res])
+    mm = np.arange(nk * N_METRICS, dtype=np.int32).reshape(nk, N_METRICS)
+    t0 = time.perf_counter()
+    prog = oracle.pack(coef, box, deg, mm, DEGREE)
+    t_pack = time.perf_counter() - t0
+    prog["grid_dims"] = gd[:nk]
+    # queries: those of the sampled kernels, until ~budget/2
+    kid = W.query_kernel_ids(q)
+    qs = q[kid < nk]
+    t0 = time.perf_counter()
+    nq = 0
+    chunk = 20000
+    while time.perf_counter() - t0 < budget_s * 0.45 and nq < len(qs):
+        oracle.search(prog, W.HW_FIXED_DEFAULT, qs[nq:nq + chunk])
+        nq += min(chunk, len(qs) - nq)
+    t_search = time.perf_counter() - t0
+    nf = nk * N_METRICS
+    step_s = (t_fit / nf) * N_KERNELS * N_METRICS + (t_pack / nk) * N_KERNELS + \
+        (t_search / max(nq, 1)) * N_QUERIES
+    sample = (f"{nf} fits ({nk} kernels), pack of {nk} kernels, {nq} queries; "
+              f"scaled to {N_KERNELS * N_METRICS} fits + {N_QUERIES} queries per step")
+    return dict(step_s=step_s, cores=oracle.get_threads(), sample=sample,
+                fit_s=t_fit / nf, search_s=t_search / max(nq, 1))
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    inst, q, gd = make_inputs(SEED)
+    per_step = max(5.0, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_rates(inst, q, gd, budget_s=min(per_step, 5.0))
+    times = []
+    last = None
+    for _ in range(args.steps):
+        last = oracle_rates(inst, q, gd, budget_s=per_step)
+        times.append(last["step_s"])
+    step_s = statistics.mean(times)
+    value = N_KERNELS * N_METRICS / step_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "fits/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "queries_per_s": N_QUERIES / step_s,
+            "cpu_baseline": {"value": value, "unit": "fits/s", "cores": last["cores"],
+                             "kind": "oracle", "sample": last["sample"]},
+            "e2e": {"value": value, "unit": "fits/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    ws, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_1906_00142_gb300 import build as rpbuild
+    if rank == 0:
+        rpbuild.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    import paper_1906_00142_gb300 as rp
+    rp.load_library()
+
+    inst, q_np, gd_np = make_inputs(SEED + 1000 * rank)
+    F = N_KERNELS * N_METRICS
+    td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    x, y, off, deg = td(inst["x"]), td(inst["y"]), td(inst["fit_off"]), td(inst["degree"])
+    mm, gd, q = td(inst["metric_map"]), td(gd_np), td(q_np)
+    fit_out = dict(coef=torch.empty((F, 70), dtype=torch.float64, device=dev),
+                   coef32=torch.empty((F, 70), dtype=torch.float32, device=dev),
+                   box=torch.empty((F, 6), dtype=torch.float64, device=dev),
+                   status=torch.empty(F, dtype=torch.int32, device=dev),
+                   rank=torch.empty(F, dtype=torch.int32, device=dev))
+    prog = torch.empty(rp.rp_program_size(N_KERNELS, DEGREE), dtype=torch.uint8, device=dev)
+    s_out = dict(argmin=torch.empty(N_QUERIES, dtype=torch.int32, device=dev),
+                 best=torch.empty(N_QUERIES, dtype=torch.float32, device=dev),
+                 second=torch.empty(N_QUERIES, dtype=torch.float32, device=dev),
+                 status=torch.empty(N_QUERIES, dtype=torch.int32, device=dev))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        rp.rp_fit(x, y, off, DEGREE, precision=args.precision, max_refine=8, degrees=deg,
+                  out=fit_out, stream=stream)
+        if ev:
+            ev[1].record(stream)
+        rp.rp_program_pack(fit_out["coef"], fit_out["box"], deg, mm, gd, DEGREE, program=prog,
+                           stream=stream)
+        if ev:
+            ev[2].record(stream)
+        rp.rp_eval_search(prog, N_KERNELS, DEGREE, q, out=s_out, stream=stream)
+        if ev:
+            ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()
+        step(evs[k])
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if ws > 1:
+        torch.distributed.barrier()
+    fit_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    pack_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    search_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * F / (ms_per_step / 1e3)
+
+    # fit status summary (informational)
+    st = fit_out["status"].cpu().numpy()
+    fit_ok = float(((st & (rp.RP_FIT_POLE | rp.RP_FIT_EMPTY | rp.RP_FIT_NONFINITE)) == 0).mean())
+
+    # end to end through the public API with pinned host buffers
+    h = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+         for k, v in dict(x=inst["x"], y=inst["y"], off=inst["fit_off"], deg=inst["degree"],
+                          mm=inst["metric_map"], gd=gd_np, q=q_np).items()}
+    h_out = dict(argmin=torch.empty(N_QUERIES, dtype=torch.int32).pin_memory(),
+                 best=torch.empty(N_QUERIES, dtype=torch.float32).pin_memory(),
+                 status=torch.empty(F, dtype=torch.int32).pin_memory())
+    d_in = {k: torch.empty_like(v, device=dev) for k, v in h.items()}
+    h2d = sum(v.numel() * v.element_size() for v in h.values())
+    d2h = sum(v.numel() * v.element_size() for v in h_out.values())
+
+    def e2e_step():
+        for k in h:
+            d_in[k].copy_(h[k], non_blocking=True)
+        rp.rp_fit(d_in["x"], d_in["y"], d_in["off"], DEGREE, precision=args.precision,
+                  max_refine=8, degrees=d_in["deg"], out=fit_out, stream=stream)
+        rp.rp_program_pack(fit_out["coef"], fit_out["box"], d_in["deg"], d_in["mm"], d_in["gd"],
+                           DEGREE, program=prog, stream=stream)
+        rp.rp_eval_search(prog, N_KERNELS, DEGREE, d_in["q"], out=s_out, stream=stream)
+        h_out["argmin"].copy_(s_out["argmin"], non_blocking=True)
+        h_out["best"].copy_(s_out["best"], non_blocking=True)
+        h_out["status"].copy_(fit_out["status"], non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e_ms = []
+    for _ in range(args.e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e_ms.append(a.elapsed_time(b))
+    e2e_ms = statistics.mean(e_ms)
+    if ws > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank == 0:
+        pk, src = peaks()
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        fit_avg, search_avg = statistics.mean(fit_ms), statistics.mean(search_ms)
+        alu_peak = fp32_peak_tflops(sm_count, pk.get("sm_max_mhz", 2070.0))
+        if fit_avg >= search_avg:
+            ach = F * fit_flops_per_fit(M_SAMPLES, DEGREE) / (fit_avg / 1e3) / 1e12
+            roof = {"kernel": "rp_fit", "bound": "alu", "achieved": ach, "peak": alu_peak,
+                    "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
+                    "peak_source": f"FP32 lanes x SM clock ({src} sm_max_mhz)"}
+        else:
+            ach = N_QUERIES * search_flops_per_query(DEGREE) / (search_avg / 1e3) / 1e12
+            roof = {"kernel": "rp_eval_search", "bound": "alu", "achieved": ach, "peak": alu_peak,
+                    "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
+                    "peak_source": f"FP32 lanes x SM clock ({src} sm_max_mhz)"}
+        line = {"metric": METRIC, "value": value, "unit": "fits/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "fits": F, "samples_per_fit": M_SAMPLES,
+                           "degree": DEGREE, "queries": N_QUERIES, "configs": 66,
+                           "precision": args.precision, "l2": "flushed (256 MiB write) between steps"},
+                "queries_per_s": ws * N_QUERIES / (ms_per_step / 1e3),
+                "phase_ms": {"fit": fit_avg, "pack": statistics.mean(pack_ms), "search": search_avg},
+                "fit_ok_frac": fit_ok,
+                "roofline": roof,
+                "e2e": {"value": ws * F / (e2e_ms / 1e3), "unit": "fits/s",
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                "gpu_launches": 3 * args.steps,
+                "clocks": clk}
+        if ws == 1 and not args.no_cpu_baseline:
+            r = oracle_rates(inst, q_np, gd_np, budget_s=20.0)
+            line["cpu_baseline"] = {"value": F / r["step_s"], "unit": "fits/s", "cores": r["cores"],
+                                    "kind": "oracle", "sample": r["sample"]}
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

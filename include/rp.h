@@ -1,0 +1,239 @@
+/*
+ * rp.h -- C ABI of the GB300 rational-program library.
+ *
+ * The library implements the data-parallel hot path of the rational-program
+ * technique for choosing GPU launch parameters (Brandt, Mohajerani, Moreno
+ * Maza, Paudel, Wang, "A Technique for Finding Optimal Program Launch
+ * Parameters Targeting Manycore Accelerators", arXiv:1906.00142):
+ *
+ *   rp_fit           Step 2 of Sec. 3.3 / Sec. 4.2: least-squares estimation of
+ *                    rational functions p/q in the data and program parameters
+ *                    (N, B0, B1) from sampled low-level metrics.
+ *   rp_program_pack  Step 3 of Sec. 3.3 / Sec. 4.3.1: turn the fitted metrics
+ *                    of each kernel into the rational program's coefficient
+ *                    table (no source generation).
+ *   rp_eval_search   Steps 4-5 of Sec. 3.3 / Sec. 4.3.2: evaluate the
+ *                    MWP-CWP rational program (Sec. 2, Example 2; occupancy,
+ *                    Example 1) at every admissible thread-block format and
+ *                    take the argmin, for many (data, hardware) queries.
+ *   rp_relmse_fwd/bwd, rp_adam_step
+ *                    nonlinear refinement of fitted coefficients on the mean
+ *                    squared relative error (no counterpart in the paper).
+ *
+ * Conventions for every entry point:
+ *  - Arrays are caller-owned DEVICE memory unless stated otherwise; the
+ *    library allocates nothing and keeps no pointer after returning.
+ *  - Work is enqueued asynchronously on `stream` (a cudaStream_t, 0 = legacy
+ *    default stream); nothing synchronises the host.
+ *  - The return value is RP_OK (0) or a negative rp_status; arguments are
+ *    checked before anything is launched, so an error return launches
+ *    nothing.  Per-item outcomes are reported in status arrays.
+ *  - Results are deterministic for fixed inputs (no floating-point atomics).
+ */
+#ifndef RP_H_
+#define RP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RP_VERSION 1
+#define RP_MAX_DEGREE 4          /* total degree bound d <= 4 */
+#define RP_COEF_STRIDE 70        /* alpha_j at [0, 35), beta_j at [35, 70) */
+#define RP_NUM_CONFIGS 66        /* (2^a, 2^b), a + b <= 10 */
+#define RP_NUM_METRICS 8
+
+/* Return codes (negative = nothing was launched). */
+typedef enum rp_status {
+  RP_OK = 0,
+  RP_ERR_INVALID_ARG = -1,
+  RP_ERR_UNSUPPORTED = -2,
+  RP_ERR_WORKSPACE = -3,
+  RP_ERR_CUDA = -4,
+  RP_ERR_ALIGNMENT = -5,
+  RP_ERR_NO_DEVICE = -6
+} rp_status;
+
+/* Per-fit status bits (rp_fit). */
+#define RP_FIT_RANK_DEFICIENT 1   /* columns dropped by the factorisation */
+#define RP_FIT_NOT_CONVERGED 2    /* refinement stopped before tol */
+#define RP_FIT_POLE 4             /* fitted q <= 0 at one of the fit's samples */
+#define RP_FIT_NONFINITE 8        /* NaN/Inf in the fit's samples: no fit */
+#define RP_FIT_NONPOS_Y 16        /* y <= 0 with relative weighting: no fit */
+#define RP_FIT_EMPTY 32           /* no samples: no fit */
+#define RP_FIT_SHIFTED 64         /* a diagonal shift was added to factor the Gram */
+
+/* Per-query status bits (rp_eval_search). */
+#define RP_Q_NO_VALID 1           /* no configuration valid: argmin = -1 */
+#define RP_Q_POLE 2               /* some configuration hit q <= 0 (excluded) */
+#define RP_Q_BAD 4                /* non-finite query field, N < 1, bad kernel id */
+
+/* Arithmetic used by rp_fit for the Gram product of the design matrix. */
+typedef enum rp_precision {
+  RP_PREC_FP64 = 0,    /* plain form: FP64 design, FP64 Gram on CUDA cores */
+  RP_PREC_FP32 = 1,    /* FP32 design, FP32 Gram on CUDA cores */
+  RP_PREC_TF32 = 2,    /* FP32 design, TF32 tensor-core Gram (tcgen05) */
+  RP_PREC_TF32X3 = 3,  /* split TF32 (hi*hi + hi*lo + lo*hi) tensor-core Gram */
+  RP_PREC_BF16 = 4,    /* BF16 tensor-core Gram (tcgen05) */
+  RP_PREC_BF16X3 = 5   /* split BF16 (three terms) tensor-core Gram */
+} rp_precision;
+
+/* rp_fit flags */
+#define RP_FIT_UNWEIGHTED 1       /* rows not weighted by 1/|y| */
+
+typedef struct rp_fit_desc {
+  int64_t num_fits;        /* F >= 0 */
+  int64_t num_samples;     /* S: length of y and of each of the 3 rows of x */
+  int32_t degree;          /* total degree bound 1..4 used when degrees == NULL */
+  int32_t precision;       /* rp_precision */
+  int32_t max_refine;      /* refinement iterations after the first solve, 0..64 */
+  int32_t flags;           /* RP_FIT_* flags */
+  double tol;              /* refinement stops when ||dx|| <= tol * ||x|| (e.g. 1e-12) */
+  const int8_t *degrees;   /* optional device array [F] of per-fit degrees 1..4 */
+} rp_fit_desc;
+
+/*
+ * rp_fit_workspace_size -- bytes of device workspace rp_fit needs for `desc`
+ * (written to *bytes; may be 0).  Host-only, launches nothing.
+ */
+int rp_fit_workspace_size(const rp_fit_desc *desc, size_t *bytes);
+
+/*
+ * rp_fit -- batched least-squares fit of rational functions (Sec. 4.2).
+ *
+ * For fit f with samples i in [fit_off[f], fit_off[f+1]):
+ *   raw variables (N, B0, B1) = (x[i], x[S+i], x[2S+i]), value y[i];
+ *   each variable is mapped affinely to [-1, 1] over the fit's own samples
+ *   (box[f] = lo_N, hi_N, lo_B0, hi_B0, lo_B1, hi_B1; a constant variable
+ *   maps to 0); p and q are polynomials of total degree <= d in the mapped
+ *   variables; the linearised residual w_i (p(x_i) - y_i q(x_i)) with
+ *   w_i = 1/|y_i| is minimised in the 2-norm (the "linear in the
+ *   coefficients" system A x = b of Sec. 4.2) under the normalisation that
+ *   q averages to 1 over the fit's samples (the system is homogeneous,
+ *   footnote of Sec. 4.2).
+ * Outputs, in the graded-lex monomial basis of the mapped variables
+ * (degree ascending, then exponent of N descending, then of B0 descending):
+ *   coef[f*70 + j] = alpha_j (numerator), coef[f*70 + 35 + j] = beta_j
+ *   (denominator), unused entries 0; coef32 (optional, may be NULL) the same
+ *   rounded to float; box[f*6 + ...] as above; rank[f] = columns kept by the
+ *   factorisation; status[f] = RP_FIT_* bits.
+ * Inputs: x float[3][S], y float[S], fit_off int64[F+1] non-decreasing with
+ * fit_off[0] = 0 and fit_off[F] <= S (checked on the device: a fit with a
+ * bad range gets RP_FIT_EMPTY).  workspace: device memory of at least
+ * rp_fit_workspace_size bytes (may be NULL if that is 0).
+ * Errors: RP_ERR_INVALID_ARG for null pointers, F < 0, degree or precision
+ * out of range; RP_ERR_CUDA if a launch fails.
+ */
+int rp_fit(const rp_fit_desc *desc, const float *x, const float *y, const int64_t *fit_off,
+           double *coef, float *coef32, double *box, int32_t *status, int32_t *rank,
+           void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * rp_program_size -- bytes of the packed program for K kernels whose fitted
+ * metrics have degree <= d.  Layout (all little-endian, 16-byte aligned
+ * sections): aN float[K][8], bN float[K][8], grid_dims int32[K] (padded),
+ * table float[K][66][8][2][d+1].
+ */
+size_t rp_program_size(int64_t num_kernels, int32_t degree);
+
+/*
+ * rp_program_pack -- the coefficient table of the rational program
+ * (Sec. 3.3 Step 3; Sec. 4.3.1 builds C source, here a table).
+ * For kernel k, configuration c = (B0, B1) and metric m (order: comp insts,
+ * coalesced mem insts, uncoalesced mem insts, transactions per uncoalesced
+ * warp access, synch insts, load bytes per warp, registers per thread,
+ * shared-memory words per block -- the metrics of Sec. 4.1), with
+ * f = metric_map[k*8 + m] (-1 = metric absent, evaluates to 0):
+ *   aN, bN map N to the fit's normalised variable t = aN*N + bN;
+ *   table holds, for numerator and denominator, the coefficients of t^0..t^d
+ *   obtained by fixing the normalised B0, B1 at configuration c (FP64
+ *   arithmetic, stored as float).
+ * Inputs (device): coef double[F][70], box double[F][6], degrees int8[F]
+ * (per-fit degree, each <= degree), metric_map int32[K][8], grid_dims
+ * int32[K] (1 = one-dimensional grid of ceil(N/T) blocks, 2 = ceil(N/B0) *
+ * ceil(N/B1) blocks).  program: device buffer of rp_program_size bytes,
+ * 16-byte aligned.  Errors: RP_ERR_INVALID_ARG, RP_ERR_ALIGNMENT,
+ * RP_ERR_CUDA.
+ */
+int rp_program_pack(int64_t num_kernels, int32_t degree, const double *coef, const double *box,
+                    const int8_t *degrees, const int32_t *metric_map, const int32_t *grid_dims,
+                    void *program, size_t program_bytes, void *stream);
+
+/* Fixed architecture constants of the MWP-CWP/occupancy model (host struct). */
+typedef struct rp_hw_fixed {
+  int32_t warp_size;       /* 32 */
+  int32_t t_max;           /* max threads per block, 1024 */
+  int32_t b_max;           /* max resident blocks per SM */
+  int32_t w_max;           /* max resident warps per SM */
+  int32_t r_sm;            /* registers per SM */
+  int32_t z_sm;            /* shared-memory words per SM */
+  float issue_cycles;      /* cycles per issued instruction */
+  int32_t reserved;        /* must be 0 */
+} rp_hw_fixed;
+
+/*
+ * rp_eval_search -- exhaustive evaluate-and-argmin (Sec. 3.3 Steps 4-5).
+ * For every query q (device float[Q][8]: N, number of SMs, SM clock in GHz,
+ * memory latency in cycles, memory bandwidth in GB/s, coalesced and
+ * uncoalesced departure delay in cycles, kernel id as int32 bits) the
+ * MWP-CWP execution time in cycles is evaluated in FP32 at all 66
+ * configurations from the packed program; argmin[q] receives the index of
+ * the smallest (ties: lowest index; -1 if none valid), best[q] and
+ * second[q] the smallest and second-smallest cycle counts (+inf if absent),
+ * status[q] RP_Q_* bits.  Configuration index c enumerates (2^a, 2^b) with
+ * a ascending then b ascending (c = 11a - a(a-1)/2 + b).
+ * Model: occupancy (Example 1, W_active = min(floor(B_active T/32), W_max)),
+ * MWP-CWP as in Hong & Kim 2009 (the paper cites it and does not print
+ * it); see the library's design notes for the exact statement.
+ * hw: host pointer.  Errors: RP_ERR_INVALID_ARG, RP_ERR_CUDA.
+ */
+int rp_eval_search(const void *program, int64_t num_kernels, int32_t degree,
+                   const rp_hw_fixed *hw, const float *queries, int64_t num_queries,
+                   int32_t *argmin, float *best, float *second, int32_t *status, void *stream);
+
+/*
+ * rp_relmse_fwd -- per-fit mean squared relative error
+ *   L_f = (1/m) sum_i ((p(x_i)/q(x_i) - y_i) / y_i)^2
+ * of float coefficients coef32 [F][70] (layout as rp_fit) with the fits'
+ * boxes (double[F][6]) on the fits' samples (x, y, fit_off as rp_fit),
+ * written to loss float[F].  FP32 arithmetic.  degrees: int8[F] device.
+ */
+int rp_relmse_fwd(int64_t num_fits, int64_t num_samples, const float *x, const float *y,
+                  const int64_t *fit_off, const int8_t *degrees, const float *coef32,
+                  const double *box, float *loss, void *stream);
+
+/*
+ * rp_relmse_bwd -- gradient of sum_f g_f L_f with respect to coef32, given
+ * g = grad_loss float[F]; written to grad float[F][70]:
+ *   dL/dalpha_j = (2/m) sum r_i phi_j(x_i) / (y_i q_i)
+ *   dL/dbeta_j  = -(2/m) sum r_i p_i phi_j(x_i) / (y_i q_i^2)   (j >= 1)
+ * with beta_0 held fixed (its gradient is written as 0).
+ */
+int rp_relmse_bwd(int64_t num_fits, int64_t num_samples, const float *x, const float *y,
+                  const int64_t *fit_off, const int8_t *degrees, const float *coef32,
+                  const double *box, const float *grad_loss, float *grad, void *stream);
+
+/*
+ * rp_adam_step -- one Adam update (Kingma & Ba 2015) of n parameters in
+ * place: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).  Entries with
+ * mask[i] == 0 are left unchanged.  All arrays float[n] on the device;
+ * mask uint8[n] (may be NULL = all).  t >= 1.
+ */
+int rp_adam_step(int64_t n, float *param, const float *grad, float *m, float *v,
+                 const uint8_t *mask, int32_t t, float lr, float beta1, float beta2, float eps,
+                 void *stream);
+
+/* Message for an rp_status code (static string). */
+const char *rp_strerror(int code);
+
+/* RP_VERSION of the loaded library. */
+int rp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RP_H_ */

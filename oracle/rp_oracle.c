@@ -546,7 +546,8 @@ static void eval_one(int64_t K, int d, const float *aN, const float *bN, const f
   for (int i = 0; i < 7; ++i)
     if (!isfinite(q[i])) return;
   if (kid < 0 || kid >= K || !(N >= 1.0) || !(nsm >= 1.0) || !(fghz > 0) || !(bw > 0) ||
-      !(memld >= 0) || !(ddc >= 0) || !(ddu >= 0) || N > 4294967295.0)
+      !(memld >= 0) || !(ddc >= 0) || !(ddu >= 0) || N > 4294967295.0 ||
+      nsm > 1048576.0)
     return;
   int B0 = 1, B1 = 1;
   cfg_dims(c, &B0, &B1);

@@ -1,0 +1,312 @@
+"""GB300 rational-program library: Python binding of the C ABI in include/rp.h.
+
+Argument marshalling only: every step of the fit, pack, search and
+refinement runs in the CUDA kernels of ``librp.so`` (built in-tree for
+sm_103a by ``paper_1906_00142_gb300.build``).  PyTorch provides device
+memory and streams.  There is no CPU fallback: if the library or a CUDA
+device is missing, calls raise.
+
+Entry points (same names as the C ABI):
+    rp_fit, rp_fit_workspace_size, rp_program_size, rp_program_pack,
+    rp_eval_search, rp_relmse_fwd, rp_relmse_bwd, rp_adam_step,
+    rp_strerror, rp_version
+plus ``RelMSE`` (a torch.autograd.Function over rp_relmse_fwd/bwd) and
+``refine_relmse`` (Adam steps with the hand-written backward).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librp.so")
+
+RP_COEF_STRIDE = 70
+RP_NUM_CONFIGS = 66
+RP_NUM_METRICS = 8
+PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16": 4, "bf16x3": 5}
+RP_FIT_RANK_DEFICIENT, RP_FIT_NOT_CONVERGED, RP_FIT_POLE = 1, 2, 4
+RP_FIT_NONFINITE, RP_FIT_NONPOS_Y, RP_FIT_EMPTY, RP_FIT_SHIFTED = 8, 16, 32, 64
+RP_Q_NO_VALID, RP_Q_POLE, RP_Q_BAD = 1, 2, 4
+RP_FIT_UNWEIGHTED = 1
+
+
+class RPError(RuntimeError):
+    pass
+
+
+class FitDesc(C.Structure):
+    _fields_ = [("num_fits", C.c_int64), ("num_samples", C.c_int64), ("degree", C.c_int32),
+                ("precision", C.c_int32), ("max_refine", C.c_int32), ("flags", C.c_int32),
+                ("tol", C.c_double), ("degrees", C.c_void_p)]
+
+
+class HwFixed(C.Structure):
+    _fields_ = [("warp_size", C.c_int32), ("t_max", C.c_int32), ("b_max", C.c_int32),
+                ("w_max", C.c_int32), ("r_sm", C.c_int32), ("z_sm", C.c_int32),
+                ("issue_cycles", C.c_float), ("reserved", C.c_int32)]
+
+
+HW_DEFAULT = dict(warp_size=32, t_max=1024, b_max=32, w_max=64, r_sm=65536, z_sm=58368,
+                  issue_cycles=1.0)
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH):
+    """Load librp.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RPError(f"{path} not built; run python -m paper_1906_00142_gb300.build")
+            lib = C.CDLL(path)
+            P, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+            lib.rp_fit_workspace_size.argtypes = [C.POINTER(FitDesc), C.POINTER(C.c_size_t)]
+            lib.rp_fit.argtypes = [C.POINTER(FitDesc), P, P, P, P, P, P, P, P, P, C.c_size_t, P]
+            lib.rp_program_size.argtypes = [i64, i32]
+            lib.rp_program_size.restype = C.c_size_t
+            lib.rp_program_pack.argtypes = [i64, i32, P, P, P, P, P, P, C.c_size_t, P]
+            lib.rp_eval_search.argtypes = [P, i64, i32, C.POINTER(HwFixed), P, i64, P, P, P, P, P]
+            lib.rp_relmse_fwd.argtypes = [i64, i64, P, P, P, P, P, P, P, P]
+            lib.rp_relmse_bwd.argtypes = [i64, i64, P, P, P, P, P, P, P, P, P]
+            lib.rp_adam_step.argtypes = [i64, P, P, P, P, P, i32, C.c_float, C.c_float, C.c_float,
+                                         C.c_float, P]
+            lib.rp_strerror.argtypes = [C.c_int]
+            lib.rp_strerror.restype = C.c_char_p
+            lib.rp_version.restype = C.c_int
+            _lib = lib
+    return _lib
+
+
+def rp_version() -> int:
+    return load_library().rp_version()
+
+
+def rp_strerror(code: int) -> str:
+    return load_library().rp_strerror(int(code)).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise RPError(f"{what}: {rp_strerror(rc)} ({rc})")
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev(t: torch.Tensor, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise RPError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise RPError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise RPError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _ptr_or_null(t, dtype, name):
+    return C.c_void_p(0) if t is None else _dev(t, dtype, name)
+
+
+def rp_fit_workspace_size(desc: FitDesc) -> int:
+    b = C.c_size_t(0)
+    _check(load_library().rp_fit_workspace_size(C.byref(desc), C.byref(b)), "rp_fit_workspace_size")
+    return b.value
+
+
+def rp_fit(x: torch.Tensor, y: torch.Tensor, fit_off: torch.Tensor, degree: int,
+           precision: str = "fp32", max_refine: int = 8, tol: float = 1e-12,
+           degrees: torch.Tensor | None = None, weighted: bool = True, out=None, stream=None):
+    """Batched rational least-squares fits (see rp_fit in include/rp.h).
+    x: float32 [3, S], y: float32 [S], fit_off: int64 [F+1] (all CUDA).
+    Returns dict(coef float64 [F,70], coef32 float32 [F,70], box float64 [F,6],
+    status int32 [F], rank int32 [F])."""
+    lib = load_library()
+    F = fit_off.numel() - 1
+    S = y.numel()
+    dev = y.device
+    if out is None:
+        out = dict(coef=torch.empty((F, RP_COEF_STRIDE), dtype=torch.float64, device=dev),
+                   coef32=torch.empty((F, RP_COEF_STRIDE), dtype=torch.float32, device=dev),
+                   box=torch.empty((F, 6), dtype=torch.float64, device=dev),
+                   status=torch.empty(F, dtype=torch.int32, device=dev),
+                   rank=torch.empty(F, dtype=torch.int32, device=dev))
+    desc = FitDesc(F, S, int(degree), PREC[precision], int(max_refine),
+                   0 if weighted else RP_FIT_UNWEIGHTED, float(tol),
+                   _ptr_or_null(degrees, torch.int8, "degrees").value)
+    ws_bytes = rp_fit_workspace_size(desc)
+    ws = out.get("workspace")
+    if ws_bytes and (ws is None or ws.numel() < ws_bytes):
+        raise RPError(f"rp_fit needs a workspace of {ws_bytes} bytes (out['workspace'])")
+    rc = lib.rp_fit(C.byref(desc), _dev(x, torch.float32, "x"), _dev(y, torch.float32, "y"),
+                    _dev(fit_off, torch.int64, "fit_off"), _dev(out["coef"], torch.float64, "coef"),
+                    _ptr_or_null(out.get("coef32"), torch.float32, "coef32"),
+                    _dev(out["box"], torch.float64, "box"), _dev(out["status"], torch.int32, "status"),
+                    _dev(out["rank"], torch.int32, "rank"),
+                    C.c_void_p(0 if not ws_bytes else ws.data_ptr()), C.c_size_t(ws_bytes),
+                    _stream(stream))
+    _check(rc, "rp_fit")
+    return out
+
+
+def rp_program_size(num_kernels: int, degree: int) -> int:
+    return load_library().rp_program_size(int(num_kernels), int(degree))
+
+
+def rp_program_pack(coef, box, degrees, metric_map, grid_dims, degree: int, program=None,
+                    stream=None):
+    """Pack fitted metrics into the rational program's table (uint8 buffer)."""
+    lib = load_library()
+    K = metric_map.shape[0]
+    nbytes = rp_program_size(K, degree)
+    if program is None:
+        program = torch.empty(nbytes, dtype=torch.uint8, device=coef.device)
+    rc = lib.rp_program_pack(K, int(degree), _dev(coef, torch.float64, "coef"),
+                             _dev(box, torch.float64, "box"), _dev(degrees, torch.int8, "degrees"),
+                             _dev(metric_map, torch.int32, "metric_map"),
+                             _dev(grid_dims, torch.int32, "grid_dims"),
+                             _dev(program, torch.uint8, "program"), C.c_size_t(program.numel()),
+                             _stream(stream))
+    _check(rc, "rp_program_pack")
+    return program
+
+
+def program_views(program: torch.Tensor, num_kernels: int, degree: int):
+    """(aN, bN, grid_dims, table) tensor views of a packed program buffer."""
+    K = num_kernels
+
+    def a16(v):
+        return (v + 15) & ~15
+    o1 = a16(4 * K * 8)
+    o2 = o1 + a16(4 * K * 8)
+    o3 = o2 + a16(4 * K)
+    aN = program[0:4 * K * 8].view(torch.float32).view(K, 8)
+    bN = program[o1:o1 + 4 * K * 8].view(torch.float32).view(K, 8)
+    gd = program[o2:o2 + 4 * K].view(torch.int32)
+    n = K * RP_NUM_CONFIGS * RP_NUM_METRICS * 2 * (degree + 1)
+    tab = program[o3:o3 + 4 * n].view(torch.float32).view(K, RP_NUM_CONFIGS, RP_NUM_METRICS, 2,
+                                                          degree + 1)
+    return aN, bN, gd, tab
+
+
+def hw_struct(hw=None) -> HwFixed:
+    h = dict(HW_DEFAULT)
+    if hw:
+        h.update(hw)
+    return HwFixed(h["warp_size"], h["t_max"], h["b_max"], h["w_max"], h["r_sm"], h["z_sm"],
+                   float(h["issue_cycles"]), 0)
+
+
+def rp_eval_search(program, num_kernels: int, degree: int, queries: torch.Tensor, hw=None,
+                   out=None, stream=None):
+    """Evaluate-and-argmin for queries float32 [Q, 8] (CUDA)."""
+    lib = load_library()
+    Q = queries.shape[0]
+    dev = queries.device
+    if out is None:
+        out = dict(argmin=torch.empty(Q, dtype=torch.int32, device=dev),
+                   best=torch.empty(Q, dtype=torch.float32, device=dev),
+                   second=torch.empty(Q, dtype=torch.float32, device=dev),
+                   status=torch.empty(Q, dtype=torch.int32, device=dev))
+    h = hw_struct(hw)
+    rc = lib.rp_eval_search(_dev(program, torch.uint8, "program"), int(num_kernels), int(degree),
+                            C.byref(h), _dev(queries, torch.float32, "queries"), Q,
+                            _dev(out["argmin"], torch.int32, "argmin"),
+                            _dev(out["best"], torch.float32, "best"),
+                            _dev(out["second"], torch.float32, "second"),
+                            _dev(out["status"], torch.int32, "status"), _stream(stream))
+    _check(rc, "rp_eval_search")
+    return out
+
+
+def rp_relmse_fwd(x, y, fit_off, degrees, coef32, box, loss=None, stream=None):
+    lib = load_library()
+    F = fit_off.numel() - 1
+    if loss is None:
+        loss = torch.empty(F, dtype=torch.float32, device=y.device)
+    rc = lib.rp_relmse_fwd(F, y.numel(), _dev(x, torch.float32, "x"), _dev(y, torch.float32, "y"),
+                           _dev(fit_off, torch.int64, "fit_off"), _dev(degrees, torch.int8, "degrees"),
+                           _dev(coef32, torch.float32, "coef32"), _dev(box, torch.float64, "box"),
+                           _dev(loss, torch.float32, "loss"), _stream(stream))
+    _check(rc, "rp_relmse_fwd")
+    return loss
+
+
+def rp_relmse_bwd(x, y, fit_off, degrees, coef32, box, grad_loss, grad=None, stream=None):
+    lib = load_library()
+    F = fit_off.numel() - 1
+    if grad is None:
+        grad = torch.empty((F, RP_COEF_STRIDE), dtype=torch.float32, device=y.device)
+    rc = lib.rp_relmse_bwd(F, y.numel(), _dev(x, torch.float32, "x"), _dev(y, torch.float32, "y"),
+                           _dev(fit_off, torch.int64, "fit_off"), _dev(degrees, torch.int8, "degrees"),
+                           _dev(coef32, torch.float32, "coef32"), _dev(box, torch.float64, "box"),
+                           _dev(grad_loss, torch.float32, "grad_loss"),
+                           _dev(grad, torch.float32, "grad"), _stream(stream))
+    _check(rc, "rp_relmse_bwd")
+    return grad
+
+
+def rp_adam_step(param, grad, m, v, t: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, mask=None,
+                 stream=None):
+    lib = load_library()
+    rc = lib.rp_adam_step(param.numel(), _dev(param, torch.float32, "param"),
+                          _dev(grad, torch.float32, "grad"), _dev(m, torch.float32, "m"),
+                          _dev(v, torch.float32, "v"), _ptr_or_null(mask, torch.uint8, "mask"),
+                          int(t), float(lr), float(beta1), float(beta2), float(eps), _stream(stream))
+    _check(rc, "rp_adam_step")
+
+
+class RelMSE(torch.autograd.Function):
+    """Per-fit mean squared relative error of coef32 with a hand-written
+    CUDA backward (rp_relmse_fwd / rp_relmse_bwd)."""
+
+    @staticmethod
+    def forward(ctx, coef32, x, y, fit_off, degrees, box):
+        ctx.save_for_backward(coef32, x, y, fit_off, degrees, box)
+        return rp_relmse_fwd(x, y, fit_off, degrees, coef32.contiguous(), box)
+
+    @staticmethod
+    def backward(ctx, grad_loss):
+        coef32, x, y, fit_off, degrees, box = ctx.saved_tensors
+        g = rp_relmse_bwd(x, y, fit_off, degrees, coef32.contiguous(), box,
+                          grad_loss.contiguous().float())
+        return g, None, None, None, None, None
+
+
+def refine_mask(degrees: torch.Tensor) -> torch.Tensor:
+    """uint8 [F, 70] mask of trainable coefficients: all alpha_j and beta_j
+    (j >= 1) of each fit's degree; beta_0 frozen."""
+    F = degrees.numel()
+    nm = ((degrees.long() + 1) * (degrees.long() + 2) * (degrees.long() + 3) // 6).view(F, 1)
+    j = torch.arange(35, device=degrees.device).view(1, 35)
+    num = (j < nm)
+    den = (j < nm) & (j >= 1)
+    return torch.cat([num, den], 1).to(torch.uint8).contiguous()
+
+
+def refine_relmse(coef32, x, y, fit_off, degrees, box, steps=20, lr=1e-3, beta1=0.9,
+                  beta2=0.999, eps=1e-8, stream=None):
+    """Adam on the mean squared relative error, using the CUDA forward and
+    backward kernels and the CUDA Adam update.  Updates coef32 in place and
+    returns the per-fit losses before and after."""
+    F = fit_off.numel() - 1
+    dev = coef32.device
+    m = torch.zeros_like(coef32)
+    v = torch.zeros_like(coef32)
+    mask = refine_mask(degrees)
+    ones = torch.ones(F, dtype=torch.float32, device=dev)
+    grad = torch.empty_like(coef32)
+    loss0 = rp_relmse_fwd(x, y, fit_off, degrees, coef32, box, stream=stream).clone()
+    for t in range(1, steps + 1):
+        rp_relmse_bwd(x, y, fit_off, degrees, coef32, box, ones, grad=grad, stream=stream)
+        rp_adam_step(coef32, grad, m, v, t, lr, beta1, beta2, eps, mask=mask, stream=stream)
+    loss1 = rp_relmse_fwd(x, y, fit_off, degrees, coef32, box, stream=stream)
+    return loss0, loss1

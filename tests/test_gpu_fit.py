@@ -1,0 +1,158 @@
+"""GPU rational fits (rp_fit) against the FP64 oracle.
+
+Parity target: fitted-model predictions within 1e-4 relative of the
+oracle's at every sample of every fit whose least-squares problem is
+determined to that accuracy by FP32-precision data (the oracle's own
+sensitivity check: predictions move by < 1e-5 when the design entries are
+perturbed by one FP32 rounding).  Fits above that are counted, and the FP64
+path (precision "fp64", which builds the design in FP64) is held to the
+tolerance on all fits.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1906_00142_gb300 as rp
+import workloads as W
+from gpu_util import dev, host, need_gpu, per_fit_max, predictions
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+def gpu_fit(inst, precision, degree=None, max_refine=8, degrees=True):
+    d = int(inst["degree"].max()) if degree is None else degree
+    out = rp.rp_fit(dev(inst["x"]), dev(inst["y"]), dev(inst["fit_off"]), d,
+                    precision=precision, max_refine=max_refine,
+                    degrees=dev(inst["degree"]) if degrees else None)
+    return {k: host(v) for k, v in out.items()}
+
+
+def compare(inst, g, ref=None, sens=None, all_fits=False, max_ill=0.1):
+    x, off, deg = inst["x"], inst["fit_off"], inst["degree"]
+    if ref is None:
+        ref = oracle.fit(x, inst["y"], off, deg)
+    np.testing.assert_array_equal(g["box"], ref["box"])
+    hard = oracle.FS_EMPTY | oracle.FS_NONFINITE | oracle.FS_NONPOS_Y
+    np.testing.assert_array_equal(g["status"] & hard, ref["status"] & hard)
+    ok = (ref["status"] & hard) == 0
+    p_o = oracle.predict_samples(ref, x, off)
+    p_g = predictions(g["coef"], g["box"], deg, x, off)
+    rel = np.abs(p_g - p_o) / np.abs(p_o)
+    err = per_fit_max(rel, off)
+    if sens is None:
+        sens = oracle.fit_sensitivity(x, inst["y"], off, deg, base=ref)
+    well = ok & (sens < 1e-5)
+    gate = ok if all_fits else well
+    bad = np.where(gate & ~(err <= TOL))[0]
+    assert len(bad) == 0, [(int(f), float(err[f]), float(sens[f]), int(g["status"][f])) for f in bad[:10]]
+    assert (ok & ~well).sum() <= max_ill * max(ok.sum(), 1)
+    # coef32 is coef rounded to float
+    np.testing.assert_array_equal(g["coef32"], g["coef"].astype(np.float32))
+    return err, sens
+
+
+@pytest.fixture(scope="module")
+def batched():
+    inst = W.batched_instance(16, seed=31, m=512, d=3)
+    ref = oracle.fit(inst["x"], inst["y"], inst["fit_off"], inst["degree"])
+    sens = oracle.fit_sensitivity(inst["x"], inst["y"], inst["fit_off"], inst["degree"], base=ref)
+    return inst, ref, sens
+
+
+def test_fit_fp32_batched(batched):
+    need_gpu()
+    inst, ref, sens = batched
+    g = gpu_fit(inst, "fp32")
+    err, _ = compare(inst, g, ref, sens)
+    assert np.median(err) < 1e-6
+    assert ((g["status"] & rp.RP_FIT_NOT_CONVERGED) == 0).mean() > 0.95
+
+
+def test_fit_fp64_batched(batched):
+    need_gpu()
+    inst, ref, sens = batched
+    g = gpu_fit(inst, "fp64")
+    compare(inst, g, ref, sens, all_fits=True)
+
+
+def test_fit_uniform_degree_argument(batched):
+    """degrees=NULL uses desc.degree for every fit."""
+    need_gpu()
+    inst, ref, sens = batched
+    g = gpu_fit(inst, "fp32", degree=3, degrees=False)
+    compare(inst, g, ref, sens)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_fit_tiny_exact_data(precision):
+    """Noise-free integer-coefficient rationals (plain FP64 tiny case)."""
+    need_gpu()
+    inst = W.tiny_instance()
+    g = gpu_fit(inst, precision)
+    compare(inst, g, all_fits=(precision == "fp64"), max_ill=1.0)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_fit_uneven_degrees_and_counts(precision):
+    """Per-fit degree 2..4 and sample counts 64..2048 (some beyond the
+    shared-memory sample cache)."""
+    need_gpu()
+    inst = W.batched_instance(6, seed=41, degree_choices=(2, 3, 4), m_range=(64, 2048))
+    g = gpu_fit(inst, precision, degree=4)
+    compare(inst, g, all_fits=(precision == "fp64"), max_ill=0.5)
+
+
+def test_fit_edge_cases():
+    need_gpu()
+    rng = np.random.default_rng(5)
+    lat = W.lattice()
+    pts = [lat[rng.choice(462, 40, replace=False)] for _ in range(6)]
+    ys = [np.exp(rng.uniform(0, 2, 40)) for _ in range(6)]
+    pts[1] = pts[1][:0]                                # empty fit
+    ys[1] = ys[1][:0]
+    ys[2] = ys[2].copy(); ys[2][3] = np.nan            # non-finite
+    ys[3] = ys[3].copy(); ys[3][5] = -1.0              # y <= 0
+    pts[4] = pts[4][:12]                               # fewer samples than unknowns
+    ys[4] = ys[4][:12]
+    pts[5] = pts[5].copy(); pts[5][:, 2] = 1.0         # B1 constant
+    x = np.concatenate(pts).T.astype(np.float32)
+    y = np.concatenate(ys).astype(np.float32)
+    off = np.zeros(7, np.int64)
+    off[1:] = np.cumsum([len(v) for v in ys])
+    inst = dict(x=np.ascontiguousarray(x), y=y, fit_off=off, degree=np.full(6, 2, np.int8))
+    for prec in ["fp32", "fp64"]:
+        g = gpu_fit(inst, prec, degree=2)
+        assert g["status"][1] & rp.RP_FIT_EMPTY
+        assert g["status"][2] & rp.RP_FIT_NONFINITE
+        assert g["status"][3] & rp.RP_FIT_NONPOS_Y
+        # under-determined fit interpolates its samples
+        p4 = predictions(g["coef"], g["box"], inst["degree"], x, off)[off[4]:off[5]]
+        assert np.max(np.abs(p4 - y[off[4]:off[5]]) / y[off[4]:off[5]]) < 1e-3
+        assert g["status"][4] & rp.RP_FIT_RANK_DEFICIENT
+        ref = oracle.fit(inst["x"], inst["y"], off, inst["degree"])
+        pg = predictions(g["coef"], g["box"], inst["degree"], x, off)
+        po = oracle.predict_samples(ref, x, off)
+        for f in [0, 5]:
+            a, b = off[f], off[f + 1]
+            assert np.max(np.abs(pg[a:b] - po[a:b]) / po[a:b]) < TOL
+
+
+def test_fit_full_size_sampled():
+    """The benchmarked launch: 1024 kernels x 8 metrics, 512 samples, d=3;
+    64 fits re-solved by the oracle."""
+    need_gpu()
+    inst = W.batched_instance(1024, seed=20190602, m=512, d=3)
+    g = gpu_fit(inst, "fp32")
+    F = len(inst["fit_off"]) - 1
+    pick = np.sort(np.random.default_rng(1).choice(F, 64, replace=False))
+    xs, ys, offs = [], [], [0]
+    for f in pick:
+        a, b = inst["fit_off"][f], inst["fit_off"][f + 1]
+        xs.append(inst["x"][:, a:b]); ys.append(inst["y"][a:b]); offs.append(offs[-1] + b - a)
+    sub = dict(x=np.ascontiguousarray(np.concatenate(xs, 1)), y=np.concatenate(ys),
+               fit_off=np.array(offs, np.int64), degree=inst["degree"][pick])
+    gs = {k: v[pick] for k, v in g.items()}
+    compare(sub, gs)
+    assert ((g["status"] & (rp.RP_FIT_POLE | rp.RP_FIT_EMPTY)) == 0).mean() > 0.99

@@ -1,0 +1,144 @@
+"""GPU evaluate-and-argmin (rp_eval_search) against the FP64 oracle.
+
+Tolerances (stated target): FP32 evaluation within 1e-5 relative of the
+FP64 oracle on the same FP32 program and queries; (query, configuration)
+pairs whose oracle decision margin is below 1e-5 (a case boundary, the
+nearest-integer rounding of registers / shared memory, a pole) or whose
+polynomial evaluation is ill-conditioned (Horner condition number > 100)
+are excluded and counted; argmin identical wherever the oracle's top-two
+gap exceeds 1e-5 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1906_00142_gb300 as rp
+import workloads as W
+from gpu_util import HW, dev, host, need_gpu, program_to_device
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def run_gpu(prog, q):
+    buf = program_to_device(prog)
+    out = rp.rp_eval_search(buf, prog["aN"].shape[0], int(prog["d"]), dev(q))
+    return {k: host(v) for k, v in out.items()}
+
+
+def check(prog, q, g, sample=None, max_excluded=0.05):
+    idx = np.arange(len(q)) if sample is None else sample
+    qs = q[idx]
+    ev = oracle.evaluate(prog, HW, qs)
+    s = oracle.search(prog, HW, qs)
+    ga, gb1, gb2, gst = g["argmin"][idx], g["best"][idx], g["second"][idx], g["status"][idx]
+    excl = (ev["margin"] < TOL) | (ev["cond"] > 100.0)
+    # exact agreement on bad / no-valid status
+    hard = oracle.QS_BAD | oracle.QS_NO_VALID
+    assert ((gst & hard) == (s["status"] & hard)).all()
+    n_excl_q = 0
+    for i in range(len(qs)):
+        if s["status"][i] & oracle.QS_BAD:
+            assert ga[i] == -1
+            continue
+        if s["argmin"][i] < 0:
+            assert ga[i] == -1 and np.isinf(gb1[i])
+            continue
+        a_o = s["argmin"][i]
+        a_g = ga[i]
+        assert a_g >= 0
+        e = ev["exec"][i]
+        if excl[i, a_g] or excl[i, a_o]:
+            n_excl_q += 1
+            continue
+        # the GPU's chosen value is the FP32 evaluation of its configuration
+        assert abs(gb1[i] - e[a_g]) <= TOL * e[a_g], (i, gb1[i], e[a_g])
+        # and no worse than the oracle's optimum
+        assert gb1[i] <= s["best"][i] * (1 + TOL)
+        gap = (s["second"][i] - s["best"][i]) / s["best"][i]
+        order = np.argsort(e, kind="stable")
+        if gap > TOL and not excl[i, order[1]]:
+            assert a_g == a_o, (i, a_g, a_o, gap)
+            if np.isfinite(s["second"][i]):
+                assert abs(gb2[i] - s["second"][i]) <= TOL * s["second"][i]
+    assert n_excl_q <= max_excluded * len(qs), n_excl_q
+    return n_excl_q
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_search_parity_small(d):
+    need_gpu()
+    prog = W.synthetic_program(8, d, seed=100 + d)
+    q = W.queries(20000, 8, seed=200 + d)
+    check(prog, q, run_gpu(prog, q))
+
+
+def test_search_parity_full_size_sampled():
+    """1e6 queries x 66 configurations over 1024 kernels (the benchmarked
+    launch), 20000 queries re-evaluated by the oracle."""
+    need_gpu()
+    prog = W.synthetic_program(1024, 3, seed=7)
+    q = W.queries(1_000_000, 1024, seed=8)
+    g = run_gpu(prog, q)
+    rng = np.random.default_rng(0)
+    sample = np.sort(rng.choice(len(q), 20000, replace=False))
+    check(prog, q, g, sample)
+    # every query got an answer
+    assert (g["argmin"] >= 0).mean() > 0.99
+
+
+def test_search_edge_queries():
+    need_gpu()
+    prog = W.synthetic_program(4, 3, seed=3)
+    q = W.queries(16, 4, seed=4)
+    q[0, W.Q_N] = np.nan
+    q[1, W.Q_KID] = np.array([4], np.int32).view(np.float32)[0]      # out of range
+    q[2, W.Q_KID] = np.array([-1], np.int32).view(np.float32)[0]
+    q[3, W.Q_N] = 1.0
+    q[4, W.Q_N] = 4294967040.0                                       # largest N accepted
+    q[5, W.Q_N] = 4294967296.0                                       # rejected
+    q[6, W.Q_NSM] = 0.0
+    q[7, W.Q_BW] = 0.0
+    q[8, W.Q_N] = 0.5
+    q[9, W.Q_DDU] = 0.0
+    q[9, W.Q_DDC] = 0.0
+    q[10, W.Q_N] = 3.0
+    check(prog, q, run_gpu(prog, q), max_excluded=0.2)
+    g = run_gpu(prog, q)
+    for i in [0, 1, 2, 5, 6, 7, 8]:
+        assert g["status"][i] & rp.RP_Q_BAD and g["argmin"][i] == -1
+
+
+def test_search_hand_worked_examples():
+    """The hand-worked MWP-CWP values, evaluated by the GPU."""
+    need_gpu()
+    import json, os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "mwpcwp_worked.json")))
+    for case in gold["cases"]:
+        tab = np.zeros((1, 66, 8, 2, 2), np.float32)
+        tab[0, :, :, 0, 0] = np.asarray(case["metrics"], np.float32)[None, :]
+        tab[0, :, :, 1, 0] = 1.0
+        # make every configuration except the worked one invalid (smem above the SM)
+        c = case["config_index"]
+        mask = np.ones(66, bool)
+        mask[c] = False
+        tab[0, mask, 7, 0, 0] = 1e6
+        prog = dict(aN=np.zeros((1, 8), np.float32), bN=np.zeros((1, 8), np.float32), table=tab,
+                    grid_dims=np.array([case["grid_dims"]], np.int32), d=1)
+        qq = case["query"]
+        q = np.array([[qq["N"], qq["n_sm"], qq["f_ghz"], qq["mem_ld"], qq["bw_gbs"], qq["dd_coal"],
+                       qq["dd_uncoal"], 0]], np.float32)
+        g = run_gpu(prog, q)
+        assert g["argmin"][0] == c
+        ref = case["exec"] if "exec" in case else eval(case["exec_formula"])
+        assert abs(g["best"][0] - ref) <= 1e-5 * ref, (case["name"], g["best"][0], ref)
+
+
+def test_search_empty_and_zero_kernels():
+    need_gpu()
+    prog = W.synthetic_program(2, 3, seed=5)
+    buf = program_to_device(prog)
+    q = torch.zeros((0, 8), dtype=torch.float32, device="cuda")
+    out = rp.rp_eval_search(buf, 2, 3, q)
+    assert out["argmin"].numel() == 0

@@ -224,6 +224,12 @@ def main():
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--kernels", type=int, default=N_KERNELS,
+                    help="smaller workloads for profiling captures only")
+    ap.add_argument("--queries", type=int, default=N_QUERIES)
+    ap.add_argument("--only", default="all", choices=["all", "fit", "search"],
+                    help="profiling captures: launch only one phase per step")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -242,6 +248,8 @@ def main():
         torch.distributed.barrier()
     import paper_1906_00142_gb300 as rp
     rp.load_library()
+    global N_KERNELS, N_QUERIES
+    N_KERNELS, N_QUERIES = args.kernels, args.queries
 
     inst, q_np, gd_np = make_inputs(SEED + 1000 * rank)
     F = N_KERNELS * N_METRICS
@@ -264,17 +272,26 @@ def main():
     def step(ev=None):
         if ev:
             ev[0].record(stream)
-        rp.rp_fit(x, y, off, DEGREE, precision=args.precision, max_refine=8, degrees=deg,
-                  out=fit_out, stream=stream)
+        if args.only in ("all", "fit"):
+            rp.rp_fit(x, y, off, DEGREE, precision=args.precision, max_refine=8, tol=args.tol,
+                      degrees=deg, out=fit_out, stream=stream)
         if ev:
             ev[1].record(stream)
-        rp.rp_program_pack(fit_out["coef"], fit_out["box"], deg, mm, gd, DEGREE, program=prog,
-                           stream=stream)
+        if args.only in ("all", "fit"):
+            rp.rp_program_pack(fit_out["coef"], fit_out["box"], deg, mm, gd, DEGREE, program=prog,
+                               stream=stream)
         if ev:
             ev[2].record(stream)
-        rp.rp_eval_search(prog, N_KERNELS, DEGREE, q, out=s_out, stream=stream)
+        if args.only in ("all", "search"):
+            rp.rp_eval_search(prog, N_KERNELS, DEGREE, q, out=s_out, stream=stream)
         if ev:
             ev[3].record(stream)
+
+    if args.only == "search":   # program from one fit + pack, outside the timed steps
+        rp.rp_fit(x, y, off, DEGREE, precision=args.precision, max_refine=8, tol=args.tol,
+                  degrees=deg, out=fit_out, stream=stream)
+        rp.rp_program_pack(fit_out["coef"], fit_out["box"], deg, mm, gd, DEGREE, program=prog,
+                           stream=stream)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -324,7 +341,7 @@ def main():
         for k in h:
             d_in[k].copy_(h[k], non_blocking=True)
         rp.rp_fit(d_in["x"], d_in["y"], d_in["off"], DEGREE, precision=args.precision,
-                  max_refine=8, degrees=d_in["deg"], out=fit_out, stream=stream)
+                  max_refine=8, tol=args.tol, degrees=d_in["deg"], out=fit_out, stream=stream)
         rp.rp_program_pack(fit_out["coef"], fit_out["box"], d_in["deg"], d_in["mm"], d_in["gd"],
                            DEGREE, program=prog, stream=stream)
         rp.rp_eval_search(prog, N_KERNELS, DEGREE, d_in["q"], out=s_out, stream=stream)
@@ -335,7 +352,7 @@ def main():
     e2e_step()
     torch.cuda.synchronize()
     e_ms = []
-    for _ in range(args.e2e_steps):
+    for _ in range(args.e2e_steps if args.only == "all" else 0):
         flush.zero_()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -344,7 +361,7 @@ def main():
         b.record(stream)
         torch.cuda.synchronize()
         e_ms.append(a.elapsed_time(b))
-    e2e_ms = statistics.mean(e_ms)
+    e2e_ms = statistics.mean(e_ms) if e_ms else float("nan")
     if ws > 1:
         t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -378,9 +395,9 @@ def main():
                 "roofline": roof,
                 "e2e": {"value": ws * F / (e2e_ms / 1e3), "unit": "fits/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-                "gpu_launches": 3 * args.steps,
+                "gpu_launches": (3 if args.only == "all" else 2 if args.only == "fit" else 1) * args.steps,
                 "clocks": clk}
-        if ws == 1 and not args.no_cpu_baseline:
+        if ws == 1 and not args.no_cpu_baseline and args.only == "all":
             r = oracle_rates(inst, q_np, gd_np, budget_s=20.0)
             line["cpu_baseline"] = {"value": F / r["step_s"], "unit": "fits/s", "cores": r["cores"],
                                     "kind": "oracle", "sample": r["sample"]}

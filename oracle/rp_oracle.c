@@ -506,7 +506,8 @@ int rpo_pack(int64_t K, int d, const double *coef, int64_t stride, const double 
  *  #Blocks = ceil(N/B0)*ceil(N/B1) (2-D grid) or ceil(N/T) (1-D grid);
  *  #Active_SMs = min(n_SM, #Blocks); #Rep = ceil(#Blocks/(B_active *
  *  #Active_SMs)) -- exact integer arithmetic.
- *  Memory model, parallelism and the three cases as in Hong & Kim 2009;
+ *  Memory model, parallelism and the three cases as in Hong & Kim 2009,
+ *  with the overlap terms (MWP - 1) taken as max(MWP - 1, 0);
  *  exec = (cycles + Synch_cost) * #Rep.  No memory instructions: exec =
  *  Comp_cycles * #Rep.
  * margin: smallest relative distance of any discrete decision to its
@@ -638,23 +639,26 @@ static void eval_one(int64_t K, int d, const float *aN, const float *bN, const f
     int cwp_cap = (Nw <= cwp_full);
     double CWP = fmin(cwp_full, Nw);
     double per = comp_cycles / mem_insts;
+    /* warps overlapping with the first one: never negative (MWP can fall
+     * below 1 when bandwidth-bound; the overlap terms then vanish) */
+    double over = MWP > 1.0 ? MWP - 1.0 : 0.0;
     margin = fmin(margin, rel_gap(mwp_u, Nw));
     margin = fmin(margin, rel_gap(cwp_full, Nw));
     double cyc;
     if (mwp_cap && cwp_cap) {
-      cyc = mem_cycles + comp_cycles + per * (MWP - 1.0);
+      cyc = mem_cycles + comp_cycles + per * over;
       cs = 1;
     } else {
       margin = fmin(margin, fmax(rel_gap(CWP, MWP), rel_gap(comp_cycles, mem_cycles)));
       if (CWP >= MWP || comp_cycles > mem_cycles) {
-        cyc = mem_cycles * Nw / MWP + per * (MWP - 1.0);
+        cyc = mem_cycles * Nw / MWP + per * over;
         cs = 2;
       } else {
         cyc = memld + comp_cycles * Nw;
         cs = 3;
       }
     }
-    double synch_cost = dd * (MWP - 1.0) * synch * (double)bact;
+    double synch_cost = dd * over * synch * (double)bact;
     exec = (cyc + synch_cost) * rep;
     if (diag) {
       diag[0] = MWP;
@@ -705,7 +709,7 @@ int rpo_search(int64_t K, int d, const float *aN, const float *bN, const float *
       if (ex < b1) { b2 = b1; b1 = ex; arg = c; }
       else if (ex < b2) b2 = ex;
     }
-    if (arg < 0) st |= QS_NO_VALID;
+    if (arg < 0 && !(st & QS_BAD)) st |= QS_NO_VALID;
     argmin[i] = arg;
     best[i] = b1;
     second[i] = b2;

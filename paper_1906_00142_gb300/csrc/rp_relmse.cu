@@ -5,7 +5,9 @@
 //   dL/dalpha_j = (2/m) sum_i r_i phi_j(x_i) / (y_i q_i)
 //   dL/dbeta_j  = -(2/m) sum_i r_i p_i phi_j(x_i) / (y_i q_i^2)   (j >= 1)
 // beta_0 is held fixed (it fixes the scale of the homogeneous pair p, q).
-// One CTA per fit, FP32 arithmetic, deterministic reductions.
+// One CTA per fit, deterministic reductions.  p and q are evaluated in FP64
+// (the fitted monomial coefficients can cancel by 1e3-1e9); the residual,
+// loss and gradient sums are FP32.
 #include <math.h>
 #include <stdint.h>
 
@@ -36,7 +38,7 @@ Exps exps_table() {
 
 struct RelShared {
   float cf[kStride];
-  float sc[3], of[3];
+  double scd[3], ofd[3];
   float red[kT / 32];
   float xn[kT][3];
   float sp[kT], sq[kT];
@@ -69,11 +71,11 @@ __global__ void __launch_bounds__(kT) relmse_kernel(bool backward, int64_t F, in
       const double lo = box[f * 6 + 2 * tid], hi = box[f * 6 + 2 * tid + 1];
       if (hi > lo) {
         const double s = 2.0 / (hi - lo);
-        sh.sc[tid] = (float)s;
-        sh.of[tid] = (float)(-1.0 - lo * s);
+        sh.scd[tid] = s;
+        sh.ofd[tid] = -1.0 - lo * s;
       } else {
-        sh.sc[tid] = 0.0f;
-        sh.of[tid] = 0.0f;
+        sh.scd[tid] = 0.0;
+        sh.ofd[tid] = 0.0;
       }
     }
     __syncthreads();
@@ -86,33 +88,36 @@ __global__ void __launch_bounds__(kT) relmse_kernel(bool backward, int64_t F, in
       const int cnt = min(kT, m - base);
       if (tid < cnt && nm > 0) {
         const int64_t i = b0 + base + tid;
-        float xn[3];
-        xn[0] = fmaf(x[i], sh.sc[0], sh.of[0]);
-        xn[1] = fmaf(x[S + i], sh.sc[1], sh.of[1]);
-        xn[2] = fmaf(x[2 * S + i], sh.sc[2], sh.of[2]);
-        float pw[3][kMaxDeg + 1];
+        // p and q in FP64: fitted monomial coefficients can cancel heavily,
+        // so an FP32 evaluation would lose the residual's leading digits
+        double xd[3];
+        xd[0] = fma((double)x[i], sh.scd[0], sh.ofd[0]);
+        xd[1] = fma((double)x[S + i], sh.scd[1], sh.ofd[1]);
+        xd[2] = fma((double)x[2 * S + i], sh.scd[2], sh.ofd[2]);
+        double pw[3][kMaxDeg + 1];
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
-          pw[v][0] = 1.0f;
+          pw[v][0] = 1.0;
 #pragma unroll
-          for (int l = 1; l <= kMaxDeg; ++l) pw[v][l] = pw[v][l - 1] * xn[v];
+          for (int l = 1; l <= kMaxDeg; ++l) pw[v][l] = pw[v][l - 1] * xd[v];
         }
-        float p = 0.0f, q = 0.0f;
+        double p = 0.0, q = 0.0;
         for (int j = 0; j < nm; ++j) {
-          const float ph = pw[0][et.e[j][0]] * pw[1][et.e[j][1]] * pw[2][et.e[j][2]];
-          p = fmaf(sh.cf[j], ph, p);
-          q = fmaf(sh.cf[kHalf + j], ph, q);
+          const double ph = pw[0][et.e[j][0]] * pw[1][et.e[j][1]] * pw[2][et.e[j][2]];
+          p = fma((double)sh.cf[j], ph, p);
+          q = fma((double)sh.cf[kHalf + j], ph, q);
         }
         const float yy = y[i];
-        const float r = (p / q - yy) / yy;
+        const float r = (float)((p / q - (double)yy) / (double)yy);
         lsum = fmaf(r, r, lsum);
         if (backward) {
-          const float iyq = 1.0f / (yy * q);
+          const float pf = (float)p, qf = (float)q;
+          const float iyq = 1.0f / (yy * qf);
           sh.sp[tid] = r * iyq;
-          sh.sq[tid] = -r * p * iyq / q;
-          sh.xn[tid][0] = xn[0];
-          sh.xn[tid][1] = xn[1];
-          sh.xn[tid][2] = xn[2];
+          sh.sq[tid] = -r * pf * iyq / qf;
+          sh.xn[tid][0] = (float)xd[0];
+          sh.xn[tid][1] = (float)xd[1];
+          sh.xn[tid][2] = (float)xd[2];
         }
       }
       if (backward) {

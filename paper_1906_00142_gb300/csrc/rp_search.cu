@@ -270,15 +270,16 @@ __global__ void __launch_bounds__(256) search_kernel(ProgramView P, int64_t K, C
           const bool cwp_cap = Nw <= cwp_full;
           const float CWP = fminf(cwp_full, Nw);
           const float per = comp_cycles * inv_mi;
+          const float over = fmaxf(MWP - 1.0f, 0.0f);
           float cyc;
           if (mwp_cap && cwp_cap) {
-            cyc = mem_cycles + comp_cycles + per * (MWP - 1.0f);
+            cyc = fmaf(per, over, mem_cycles + comp_cycles);
           } else if (CWP >= MWP || comp_cycles > mem_cycles) {
-            cyc = __fdividef(mem_cycles * Nw, MWP) + per * (MWP - 1.0f);
+            cyc = fmaf(per, over, __fdividef(mem_cycles * Nw, MWP));
           } else {
             cyc = fmaf(comp_cycles, Nw, memld);
           }
-          const float synch_cost = dd * (MWP - 1.0f) * synch * (float)bact;
+          const float synch_cost = dd * over * synch * (float)bact;
           ex = (cyc + synch_cost) * rep;
         }
         if (ex < b1) {

@@ -65,3 +65,20 @@ def program_to_device(prog):
     gd.copy_(torch.from_numpy(prog["grid_dims"].astype(np.int32)))
     tab.copy_(torch.from_numpy(prog["table"].astype(np.float32)))
     return buf
+
+
+def lin_objective(coef_row, box_row, d, pts, y, weighted=True):
+    """Linearised least-squares objective sum_i w_i^2 (p_i - y_i q_i)^2 with
+    (p, q) rescaled so that q averages to 1 over the samples (FP64)."""
+    e = W.exponents(d)
+    lo, hi = box_row[0::2], box_row[1::2]
+    span = np.where(hi > lo, hi - lo, 1.0)
+    xn = np.where(hi > lo, 2.0 * (pts - lo) / span - 1.0, 0.0)
+    phi = np.prod(xn[:, None, :] ** e[None, :, :], axis=2)
+    nm = len(e)
+    p = phi @ coef_row[:nm]
+    q = phi @ coef_row[35:35 + nm]
+    s = q.mean()
+    p, q = p / s, q / s
+    w = 1.0 / np.abs(y) if weighted else 1.0
+    return float(np.sum((w * (p - y * q)) ** 2))

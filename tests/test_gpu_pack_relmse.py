@@ -77,10 +77,14 @@ def test_pipeline_fit_pack_search():
 
 
 def test_relmse_forward_backward(fitted):
+    """Loss within 1e-4 relative and gradient within 1e-4 of its largest
+    entry, against the oracle's FP64 loss and closed-form gradient (the
+    oracle's gradient is itself pinned to central finite differences)."""
     need_gpu()
     inst, ref = fitted
     x, y, off, deg = inst["x"], inst["y"], inst["fit_off"], inst["degree"]
-    c32 = (ref["coef"] * (1 + 0.02 * np.random.default_rng(0).standard_normal(ref["coef"].shape))).astype(np.float32)
+    rng = np.random.default_rng(0)
+    c32 = (ref["coef"] * (1 + 1e-3 * rng.standard_normal(ref["coef"].shape))).astype(np.float32)
     loss_o, grad_o = oracle.relmse(x, y, off, deg, c32.astype(np.float64), ref["box"])
     loss_g = host(rp.rp_relmse_fwd(dev(x), dev(y), dev(off), dev(deg), dev(c32), dev(ref["box"])))
     np.testing.assert_allclose(loss_g, loss_o, rtol=1e-4)
@@ -97,7 +101,7 @@ def test_relmse_autograd_and_adam(fitted):
     inst, ref = fitted
     x, y, off, deg = (dev(inst[k]) for k in ("x", "y", "fit_off", "degree"))
     box = dev(ref["box"])
-    c0 = (ref["coef"] * (1 + 0.01 * np.random.default_rng(1).standard_normal(ref["coef"].shape))).astype(np.float32)
+    c0 = (ref["coef"] * (1 + 1e-3 * np.random.default_rng(1).standard_normal(ref["coef"].shape))).astype(np.float32)
     c = dev(c0).requires_grad_(True)
     loss = rp.RelMSE.apply(c, x, y, off, deg, box)
     loss.sum().backward()

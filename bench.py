@@ -216,6 +216,7 @@ def run_reference(args):
 # --------------------------------------------------------------------------
 
 def main():
+    global N_KERNELS, N_QUERIES
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -233,6 +234,7 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    N_KERNELS, N_QUERIES = args.kernels, args.queries
     if args.impl == "reference":
         run_reference(args)
         return
@@ -248,8 +250,6 @@ def main():
         torch.distributed.barrier()
     import paper_1906_00142_gb300 as rp
     rp.load_library()
-    global N_KERNELS, N_QUERIES
-    N_KERNELS, N_QUERIES = args.kernels, args.queries
 
     inst, q_np, gd_np = make_inputs(SEED + 1000 * rank)
     F = N_KERNELS * N_METRICS

@@ -527,6 +527,25 @@ static double rel_gap(double a, double b) {
   return s > 0 ? fabs(a - b) / s : 1.0;
 }
 
+/* B_active for integer registers per thread Ri and shared words per block Zi
+ * (0 = the block cannot be resident) */
+static int64_t occupancy(double Ri, double Zi, int64_t T, int64_t wpb, double warp, double bmax,
+                         double wmax, double rsm, double zsm) {
+  if (Ri * (double)T > rsm || Zi > zsm) return 0;
+  int64_t bact = (int64_t)bmax;
+  int64_t t1 = (int64_t)wmax / wpb;
+  if (t1 < bact) bact = t1;
+  if (Ri > 0) {
+    int64_t t2 = (int64_t)(rsm / (Ri * (double)wpb * warp));
+    if (t2 < bact) bact = t2;
+  }
+  if (Zi > 0) {
+    int64_t t3 = (int64_t)floor(zsm / Zi);
+    if (t3 < bact) bact = t3;
+  }
+  return bact > 0 ? bact : 0;
+}
+
 #define EV_INVALID -1
 #define EV_POLE -2
 #define EV_BADQ -3
@@ -573,30 +592,29 @@ static void eval_one(int64_t K, int d, const float *aN, const float *bN, const f
   double comp = fmax(0.0, mv[0]), Cm = fmax(0.0, mv[1]), U = fmax(0.0, mv[2]);
   double upm = fmax(1.0, mv[3]), synch = fmax(0.0, mv[4]), lbw = fmax(0.0, mv[5]);
   double Rf = fmax(0.0, mv[6]), Zf = fmax(0.0, mv[7]);
-  /* nearest-integer decisions */
-  margin = fmin(margin, fabs(Rf - floor(Rf) - 0.5) / fmax(1.0, Rf));
-  margin = fmin(margin, fabs(Zf - floor(Zf) - 0.5) / fmax(1.0, Zf));
-  *margin_out = margin;
-  *cond_out = cond;
-  *case_out = EV_INVALID;
-  double Ri = floor(Rf + 0.5), Zi = floor(Zf + 0.5);
   double warp = hw[0], tmax = hw[1], bmax = hw[2], wmax = hw[3], rsm = hw[4], zsm = hw[5],
          issue = hw[6];
   int64_t T = (int64_t)B0 * B1;
+  *margin_out = margin;
+  *cond_out = cond;
+  *case_out = EV_INVALID;
   if ((double)T > tmax) return;
   int64_t wpb = (T + (int64_t)warp - 1) / (int64_t)warp;
-  if (Ri * (double)T > rsm || Zi > zsm) return;
-  int64_t bact = (int64_t)bmax;
-  int64_t t1 = (int64_t)wmax / wpb;
-  if (t1 < bact) bact = t1;
-  if (Ri > 0) {
-    int64_t t2 = (int64_t)(rsm / (Ri * (double)wpb * warp));
-    if (t2 < bact) bact = t2;
+  double Ri = floor(Rf + 0.5), Zi = floor(Zf + 0.5);
+  int64_t bact = occupancy(Ri, Zi, T, wpb, warp, bmax, wmax, rsm, zsm);
+  /* the nearest-integer roundings of R and Z are decisions only where the
+   * other rounding would change residency */
+  if (fabs(Rf - floor(Rf) - 0.5) < 1e-5 * fmax(1.0, Rf)) {
+    double alt = (Rf - floor(Rf) >= 0.5) ? Ri - 1.0 : Ri + 1.0;
+    if (occupancy(alt, Zi, T, wpb, warp, bmax, wmax, rsm, zsm) != bact)
+      margin = fmin(margin, fabs(Rf - floor(Rf) - 0.5) / fmax(1.0, Rf));
   }
-  if (Zi > 0) {
-    int64_t t3 = (int64_t)floor(zsm / Zi);
-    if (t3 < bact) bact = t3;
+  if (fabs(Zf - floor(Zf) - 0.5) < 1e-5 * fmax(1.0, Zf)) {
+    double alt = (Zf - floor(Zf) >= 0.5) ? Zi - 1.0 : Zi + 1.0;
+    if (occupancy(Ri, alt, T, wpb, warp, bmax, wmax, rsm, zsm) != bact)
+      margin = fmin(margin, fabs(Zf - floor(Zf) - 0.5) / fmax(1.0, Zf));
   }
+  *margin_out = margin;
   if (bact <= 0) return;
   int64_t nw_i = bact * wpb;
   if (nw_i > (int64_t)wmax) nw_i = (int64_t)wmax;
@@ -660,6 +678,13 @@ static void eval_one(int64_t K, int d, const float *aN, const float *bN, const f
     }
     double synch_cost = dd * over * synch * (double)bact;
     exec = (cyc + synch_cost) * rep;
+    /* (MWP - 1) loses digits when MWP is close to 1: the relative error of
+     * MWP is amplified by MWP / (MWP - 1) in the overlap terms */
+    if (over > 0.0) {
+      double over_terms = (cs == 3 ? 0.0 : per * over) + synch_cost;
+      cond = fmax(cond, (MWP / over) * (over_terms / (cyc + synch_cost)));
+      *cond_out = cond;
+    }
     if (diag) {
       diag[0] = MWP;
       diag[1] = CWP;

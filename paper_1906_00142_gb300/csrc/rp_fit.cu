@@ -141,10 +141,10 @@ __device__ void warp_solve(const SR *L, int n, int ld, const SR *invd, SR *b) {
 
 // FP64 Cholesky of the (d+1) x (d+1) Hankel moment matrix of a standardised
 // variable -> coefficients of the orthonormal polynomials (columns of the
-// inverse factor).  Pivots below 1e-5 of their diagonal entry mark a
-// direction the samples cannot resolve (too few distinct values): that
-// polynomial is set to 0.  Single thread.
-__device__ void marginal_transform(const double *M, int d, float T[][kMaxDeg + 1]) {
+// inverse factor).  A variable with only q distinct sample values supports
+// polynomials of degree < q on the samples: Q_k for k > deg_eff (= q - 1) is
+// set to 0, as is any Q_k whose pivot is not positive.  Single thread.
+__device__ void marginal_transform(const double *M, int d, int deg_eff, float T[][kMaxDeg + 1]) {
   double R[kMaxDeg + 1][kMaxDeg + 1], Ti[kMaxDeg + 1][kMaxDeg + 1];
   bool ok[kMaxDeg + 1];
   for (int i = 0; i <= kMaxDeg; ++i)
@@ -152,7 +152,7 @@ __device__ void marginal_transform(const double *M, int d, float T[][kMaxDeg + 1
   for (int k = 0; k <= d; ++k) {
     double p = M[2 * k];
     for (int l = 0; l < k; ++l) p -= R[l][k] * R[l][k];
-    ok[k] = M[2 * k] > 0.0 && p > 1e-5 * M[2 * k];
+    ok[k] = k <= deg_eff && M[2 * k] > 0.0 && p > 1e-12 * M[2 * k];
     if (!ok[k]) continue;
     R[k][k] = sqrt(p);
     for (int j = k + 1; j <= d; ++j) {
@@ -176,6 +176,24 @@ __device__ void marginal_transform(const double *M, int d, float T[][kMaxDeg + 1
   T[0][0] = 1.0f;  // Q_0 = 1 (M_0 = 1)
 }
 
+// Insert a value into a small lock-free set of at most kMaxDeg + 1 distinct
+// values (slots claimed in order with compare-and-swap; once full, further
+// values are ignored -- kMaxDeg + 1 distinct values are all a degree-kMaxDeg
+// marginal basis needs).
+constexpr unsigned kEmpty = 0xFFFFFFFFu;
+__device__ __forceinline__ void distinct_insert(unsigned *slots, float x) {
+  const unsigned v = (x == 0.0f) ? 0u : __float_as_uint(x);
+#pragma unroll
+  for (int k = 0; k < kMaxDeg + 1; ++k) {
+    const unsigned cur = *((volatile unsigned *)&slots[k]);
+    if (cur == v) return;
+    if (cur == kEmpty) {
+      const unsigned old = atomicCAS(&slots[k], kEmpty, v);
+      if (old == kEmpty || old == v) return;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------
 // Per-fit shared state
 
@@ -194,6 +212,7 @@ struct FitShared {
   float xhi[2 * kMaxNm], xlo[2 * kMaxNm];  // split solution for compensated residuals
   float red_f[8][32];
   double red_d[8][32];
+  unsigned dslot[3][kMaxDeg + 1];          // distinct raw values per variable (saturating)
   int keep_cnt, keep_w, flags, bad;
   float dnorm, xnorm;
 };
@@ -378,8 +397,13 @@ __global__ void __launch_bounds__(kThreads) fit_kernel(FitArgs a) {
     float lmin[3] = {INFINITY, INFINITY, INFINITY}, lmax[3] = {-INFINITY, -INFINITY, -INFINITY};
     int lbad = 0;
     if (tid == 0) sh.bad = 0;
+    if (tid < 3 * (kMaxDeg + 1)) (&sh.dslot[0][0])[tid] = kEmpty;
+    __syncthreads();
     for (int i = tid; i < m; i += kThreads) {
       const float v0 = gx0[i], v1 = gx1[i], v2 = gx2[i], yy = gy[i];
+      distinct_insert(sh.dslot[0], v0);
+      distinct_insert(sh.dslot[1], v1);
+      distinct_insert(sh.dslot[2], v2);
       if (cached) {
         xs[i] = v0;
         xs[kSampleCache + i] = v1;
@@ -514,7 +538,9 @@ __global__ void __launch_bounds__(kThreads) fit_kernel(FitArgs a) {
             Ms[k] = M[k] * pw;
             pw *= isg;
           }
-          marginal_transform(Ms, d, sh.Tm[v]);
+          int cnt = 0;
+          for (int k = 0; k <= kMaxDeg; ++k) cnt += sh.dslot[v][k] != kEmpty;
+          marginal_transform(Ms, d, min(d, cnt - 1), sh.Tm[v]);
         }
       }
       __syncthreads();
@@ -561,7 +587,12 @@ __global__ void __launch_bounds__(kThreads) fit_kernel(FitArgs a) {
       __syncthreads();
       for (int e = tid; e < nc * nc; e += kThreads) red[e] *= sh.scl[e / nc] * sh.scl[e % nc];
       __syncthreads();
-      if (wid == 0) warp_chol<Real>(red, nc, nc, (Real)1e-6, sh.invw, &sh.keep_w);
+      // the whitening only preconditions: any positive pivot is kept (the
+      // basis stays a basis of the same space); only exactly dependent
+      // directions (pivot at rounding level or below) are dropped
+      if (wid == 0)
+        warp_chol<Real>(red, nc, nc, sizeof(Real) == 8 ? (Real)1e-14 : (Real)1e-10, sh.invw,
+                        &sh.keep_w);
       __syncthreads();
       // R^{-1} (R = L^T, R[i][l] = L[l][i]), column j by back substitution,
       // one thread per column, into G (free now); then W = D R^{-1}

@@ -2,10 +2,11 @@
 
 Tolerances (stated target): FP32 evaluation within 1e-5 relative of the
 FP64 oracle on the same FP32 program and queries; (query, configuration)
-pairs whose oracle decision margin is below 1e-5 (a case boundary, the
-nearest-integer rounding of registers / shared memory, a pole) or whose
-polynomial evaluation is ill-conditioned (Horner condition number > 100)
-are excluded and counted; argmin identical wherever the oracle's top-two
+pairs whose oracle decision margin is below 1e-5 (a case boundary, a
+nearest-integer rounding of registers / shared memory that changes
+residency, a pole) or whose FP32 evaluation is ill-conditioned (Horner
+condition number, or the amplification of MWP's error through MWP - 1,
+above 30: three FP32 roundings times 30 is ~5e-6) are excluded and counted; argmin identical wherever the oracle's top-two
 gap exceeds 1e-5 relative.
 """
 import numpy as np
@@ -33,7 +34,7 @@ def check(prog, q, g, sample=None, max_excluded=0.05):
     ev = oracle.evaluate(prog, HW, qs)
     s = oracle.search(prog, HW, qs)
     ga, gb1, gb2, gst = g["argmin"][idx], g["best"][idx], g["second"][idx], g["status"][idx]
-    excl = (ev["margin"] < TOL) | (ev["cond"] > 100.0)
+    excl = (ev["margin"] < TOL) | (ev["cond"] > 30.0)
     # exact agreement on bad / no-valid status
     hard = oracle.QS_BAD | oracle.QS_NO_VALID
     assert ((gst & hard) == (s["status"] & hard)).all()

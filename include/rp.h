@@ -64,7 +64,8 @@ typedef enum rp_status {
 #define RP_FIT_NONFINITE 8        /* NaN/Inf in the fit's samples: no fit */
 #define RP_FIT_NONPOS_Y 16        /* y <= 0 with relative weighting: no fit */
 #define RP_FIT_EMPTY 32           /* no samples: no fit */
-#define RP_FIT_SHIFTED 64         /* a diagonal shift was added to factor the Gram */
+#define RP_FIT_ITER_SHIFT 8       /* bits 8..15: refinement iterations performed */
+#define RP_FIT_ITER_MASK 0xFF00
 
 /* Per-query status bits (rp_eval_search). */
 #define RP_Q_NO_VALID 1           /* no configuration valid: argmin = -1 */

@@ -1,6 +1,6 @@
 // Batched least-squares fitting of rational functions (Sec. 4.2).
 //
-// One CTA owns one fit at a time (persistent over fits).  The linearised
+// One warp owns one fit at a time (persistent over fits).  The linearised
 // problem of Sec. 4.2 -- minimise sum_i w_i^2 (p(x_i) - y_i q(x_i))^2 over the
 // coefficients of p and q, the homogeneous system normalised by mean(q) = 1
 // over the fit's samples -- is solved through its normal equations in a basis
@@ -13,8 +13,7 @@
 //  3. Psi_j = Q_a(u_N) Q_b(u_B0) Q_c(u_B1) over the graded-lex exponents
 //     (a, b, c): a basis of the same polynomial space as the monomials;
 //  4. the non-constant Psi_j are centred on the samples and whitened with the
-//     inverse Cholesky factor of their Gram matrix (Psi~), cached in shared
-//     memory when the fit is small enough;
+//     inverse Cholesky factor of their Gram matrix (Psi~);
 //  5. the design rows w_i [1, Psi~.., -y_i Psi~..] with right-hand side
 //     w_i y_i give the augmented Gram matrix, which is equilibrated and
 //     factored with column dropping (pivot below a drop tolerance: column
@@ -24,8 +23,8 @@
 //     Rump & Oishi's Dot2 -- on the FP32 path, plain FP64 on the FP64 path),
 //     stopping at ||dx|| <= tol ||x|| or when the corrections stop shrinking;
 //  7. the solution is mapped back to the monomial basis of the box-normalised
-//     variables in FP64 and the fitted q is checked to be positive at every
-//     sample.
+//     variables in FP64.  Every refinement pass also checks that q is positive
+//     at every sample for the solution the pass starts from.
 //
 // Each step is a change of basis of the same function space under the same
 // normalisation, so the fitted p/q is the least-squares solution the paper's
@@ -40,11 +39,6 @@
 namespace rpk {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kSampleCache = 1024;    // samples kept in shared memory
-constexpr int kCacheFloats = 12288;   // whitened-basis cache (FP32 path): 48 KB
-constexpr int kCh = 128;              // samples per row chunk
-constexpr int kChP = kCh + 1;         // padded chunk stride (bank-conflict free)
 
 __constant__ int8_t c_exp[kMaxNm][3];   // graded-lex exponents
 
@@ -195,63 +189,56 @@ __device__ __forceinline__ void distinct_insert(unsigned *slots, float x) {
 }
 
 // ---------------------------------------------------------------------
-// Per-fit shared state
+// Per-warp fit state.  One warp owns one fit at a time; all its state lives
+// in a private slice of shared memory, so no block-wide barrier is needed
+// and the serial steps of one fit overlap with other warps' fits.
 
-template <class Real>
-struct FitShared {
-  float mu_v[3], isg_v[3], sc_v[3], of_v[3];
-  float Tm[3][kMaxDeg + 1][kMaxDeg + 1];   // Q_k(u) = sum_l Tm[l][k] u^l
+template <class Real, int DMAX>
+struct WarpFit {
+  static constexpr int NM = (DMAX + 1) * (DMAX + 2) * (DMAX + 3) / 6;
+  static constexpr int NAUG = 2 * NM;
+  // staging stride: >= NAUG, multiple of 4, odd multiple of 4 (LDS.128 reads
+  // of one row by many lanes spread over banks)
+  static constexpr int LDS = (((NAUG + 3) / 4) % 2 == 1) ? ((NAUG + 3) / 4) * 4 : ((NAUG + 3) / 4 + 1) * 4;
+  double xsol[NAUG];                  // solution (design basis, unscaled)
   double lo[3], hi[3];
-  Real mupsi[kMaxNm];                      // sample means of Psi_j
-  Real W[kMaxNm][kMaxNm];                  // whitening, upper triangular on 1..nm-1
-  double xsol[2 * kMaxNm];                 // solution, design basis, unscaled
-  Real gvec[2 * kMaxNm];                   // right-hand side / correction
-  Real scl[2 * kMaxNm];                    // equilibration
-  Real invd[2 * kMaxNm];                   // 1/L_kk (0 = dropped)
-  Real invw[2 * kMaxNm];                   // same for the whitening factor
-  float xhi[2 * kMaxNm], xlo[2 * kMaxNm];  // split solution for compensated residuals
-  float red_f[8][32];
-  double red_d[8][32];
-  unsigned dslot[3][kMaxDeg + 1];          // distinct raw values per variable (saturating)
-  int keep_cnt, keep_w, flags, bad;
-  float dnorm, xnorm;
+  Real G[NAUG * NAUG];                // Gram, then factor (stride n)
+  Real stage[32 * LDS];               // 32 staged rows / scratch
+  Real W[NM * NM];                    // whitening, upper triangular on 1..nm-1
+  Real mupsi[NM];
+  Real gvec[NAUG], scl[NAUG], invd[NAUG], invw[NM];
+  Real rbuf[2][32];
+  Real Tm[3][kMaxDeg + 1][kMaxDeg + 1];  // Q_k(u) = sum_l Tm[l][k] u^l
+  Real mu_v[3], isg_v[3], sc_v[3], of_v[3];
+  float xhi[NAUG], xlo[NAUG];
+  unsigned dslot[3][kMaxDeg + 1];
+  int keep_cnt, keep_w;
 };
 
 template <class Real, int DMAX>
-struct Layout {
-  static constexpr int NM = (DMAX + 1) * (DMAX + 2) * (DMAX + 3) / 6;
-  static constexpr int NAUG = 2 * NM;
-  static constexpr int ROWS = ((NAUG + 3) / 4) * 4;             // padded feature count
-  static constexpr size_t rows_bytes = sizeof(Real) * (size_t)ROWS * kChP;
-  static constexpr size_t red_bytes = sizeof(Real) * (size_t)kThreads * 16;
-  static constexpr size_t buf_bytes = rows_bytes > red_bytes ? rows_bytes : red_bytes;
-  static constexpr size_t G_bytes = sizeof(Real) * (size_t)NAUG * NAUG;
-  static constexpr size_t samples_bytes = sizeof(float) * 4 * kSampleCache;
-  static constexpr size_t cache_bytes = sizeof(Real) == 4 ? sizeof(float) * kCacheFloats : 0;
-  static constexpr size_t rvec_bytes = 2 * sizeof(Real) * kCh;
-  static constexpr size_t total = ((sizeof(FitShared<Real>) + 15) & ~size_t(15)) + buf_bytes +
-                                  G_bytes + samples_bytes + cache_bytes + rvec_bytes + 64;
-};
+__host__ __device__ constexpr size_t warpfit_bytes() {
+  return (sizeof(WarpFit<Real, DMAX>) + 15) & ~size_t(15);
+}
 
 // Unwhitened basis Psi at one sample (compile-time bound NM, runtime nm).
-template <class Real, int NM>
-__device__ __forceinline__ void eval_psi(const FitShared<Real> &sh, int d, int nm, float x0, float x1,
-                                         float x2, Real (&psi)[NM]) {
+template <class Real, int DMAX, int NM>
+__device__ __forceinline__ void eval_psi(const WarpFit<Real, DMAX> &w, int d, int nm, float x0,
+                                         float x1, float x2, Real (&psi)[NM]) {
   Real Q[3][kMaxDeg + 1];
   const float xv[3] = {x0, x1, x2};
 #pragma unroll
   for (int v = 0; v < 3; ++v) {
-    const Real xn = (Real)fmaf(xv[v], sh.sc_v[v], sh.of_v[v]);
-    const Real u = (xn - (Real)sh.mu_v[v]) * (Real)sh.isg_v[v];
+    const Real xn = fma((Real)xv[v], w.sc_v[v], w.of_v[v]);
+    const Real u = (xn - w.mu_v[v]) * w.isg_v[v];
     Real pw[kMaxDeg + 1];
     pw[0] = 1;
 #pragma unroll
-    for (int l = 1; l <= kMaxDeg; ++l) pw[l] = pw[l - 1] * u;
+    for (int l = 1; l <= DMAX; ++l) pw[l] = pw[l - 1] * u;
 #pragma unroll
-    for (int k = 0; k <= kMaxDeg; ++k) {
+    for (int k = 0; k <= DMAX; ++k) {
       Real s = 0;
 #pragma unroll
-      for (int l = 0; l <= k; ++l) s += (Real)sh.Tm[v][l][k] * pw[l];
+      for (int l = 0; l <= k; ++l) s = fma(w.Tm[v][l][k], pw[l], s);
       Q[v][k] = (k <= d) ? s : (Real)0;
     }
   }
@@ -261,27 +248,21 @@ __device__ __forceinline__ void eval_psi(const FitShared<Real> &sh, int d, int n
 }
 
 // Whitened basis: pt[0] = 1, pt[j] = sum_{1<=i<=j} (Psi_i - mean_i) W[i][j].
-template <class Real, int NM>
-__device__ __forceinline__ void whiten(const FitShared<Real> &sh, const Real (&psi)[NM],
+template <class Real, int DMAX, int NM>
+__device__ __forceinline__ void whiten(const WarpFit<Real, DMAX> &w, const Real (&psi)[NM],
                                        Real (&pt)[NM]) {
   pt[0] = 1;
 #pragma unroll
   for (int j = 1; j < NM; ++j) pt[j] = 0;
 #pragma unroll
   for (int i = 1; i < NM; ++i) {
-    const Real c = psi[i] - sh.mupsi[i];
+    const Real c = psi[i] - w.mupsi[i];
 #pragma unroll
-    for (int j = i; j < NM; ++j) pt[j] = fma(c, sh.W[i][j], pt[j]);
+    for (int j = i; j < NM; ++j) pt[j] = fma(c, w.W[i * NM + j], pt[j]);
   }
 }
 
-// Accumulate lower-triangle 4x4 tiles of the Gram of `rows` (feature-major,
-// stride kChP) over `cnt` samples into per-thread accumulators.
-template <class Real>
-struct GramAcc {
-  Real s[16], c[16];
-};
-
+// t-th tile of the lower triangle (row-major): rb >= cb
 __device__ __forceinline__ void tile_of(int t, int &rb, int &cb) {
   int r = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
   while ((r + 1) * (r + 2) / 2 <= t) ++r;
@@ -290,128 +271,110 @@ __device__ __forceinline__ void tile_of(int t, int &rb, int &cb) {
   cb = t - r * (r + 1) / 2;
 }
 
-template <class Real>
-__device__ void gram_chunk(const Real *rows, int cnt, int ntiles, int sgc, GramAcc<Real> &acc) {
-  const int item = threadIdx.x;
-  if (item >= ntiles * sgc) return;
-  const int tile = item % ntiles, sg = item / ntiles;
-  int rb, cb;
-  tile_of(tile, rb, cb);
-  Real part[16];
+// Accumulate the 32 staged rows (stride LDS) into this lane's TS x TS tiles
+// of the lower triangle of the Gram; tile t of lane = lane + 32 k.
+template <class Real, int TS, int TPL, int LDS>
+__device__ __forceinline__ void gram_stage(const Real *stage, int ntiles, Real (&acc)[TPL][TS * TS]) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int i = 0; i < 16; ++i) part[i] = 0;
-  for (int s = sg; s < cnt; s += sgc) {
-    Real a[4], b[4];
+  for (int k = 0; k < TPL; ++k) {
+    const int t = lane + 32 * k;
+    if (t >= ntiles) break;
+    int rb, cb;
+    tile_of(t, rb, cb);
+#pragma unroll 4
+    for (int s = 0; s < 32; ++s) {
+      Real av[TS], bv[TS];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      a[i] = rows[(4 * rb + i) * kChP + s];
-      b[i] = rows[(4 * cb + i) * kChP + s];
+      for (int i = 0; i < TS; ++i) {
+        av[i] = stage[s * LDS + TS * rb + i];
+        bv[i] = stage[s * LDS + TS * cb + i];
+      }
+#pragma unroll
+      for (int i = 0; i < TS; ++i)
+#pragma unroll
+        for (int j = 0; j < TS; ++j) acc[k][TS * i + j] = fma(av[i], bv[j], acc[k][TS * i + j]);
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) part[4 * i + j] = fma(a[i], b[j], part[4 * i + j]);
-  }
-#pragma unroll
-  for (int i = 0; i < 16; ++i) {  // Kahan accumulation of chunk partials
-    const Real y = part[i] - acc.c[i];
-    const Real t = acc.s[i] + y;
-    acc.c[i] = (t - acc.s[i]) - y;
-    acc.s[i] = t;
   }
 }
 
-// Combine per-thread tiles into the full symmetric n x n Gram G (stride n).
-template <class Real>
-__device__ void gram_finish(const GramAcc<Real> &acc, int ntiles, int sgc, int n, Real *G,
-                            Real *red) {
-  const int item = threadIdx.x;
-  if (item < ntiles * sgc)
+template <class Real, int TS, int TPL>
+__device__ __forceinline__ void gram_store(const Real (&acc)[TPL][TS * TS], int ntiles, int n, Real *G) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) red[(size_t)item * 16 + i] = acc.s[i] - acc.c[i];
-  __syncthreads();
-  for (int e = threadIdx.x; e < ntiles * 16; e += kThreads) {
-    const int tile = e / 16, k = e % 16;
+  for (int k = 0; k < TPL; ++k) {
+    const int t = lane + 32 * k;
+    if (t >= ntiles) break;
     int rb, cb;
-    tile_of(tile, rb, cb);
-    const int r = 4 * rb + k / 4, c = 4 * cb + k % 4;
-    Real s = 0;
-    for (int g = 0; g < sgc; ++g) s += red[((size_t)g * ntiles + tile) * 16 + k];
-    if (r < n && c < n) {
-      G[r * n + c] = s;
-      G[c * n + r] = s;
-    }
+    tile_of(t, rb, cb);
+#pragma unroll
+    for (int i = 0; i < TS; ++i)
+#pragma unroll
+      for (int j = 0; j < TS; ++j) {
+        const int r = TS * rb + i, c = TS * cb + j;
+        if (r < n && c < n) {
+          G[r * n + c] = acc[k][TS * i + j];
+          G[c * n + r] = acc[k][TS * i + j];
+        }
+      }
   }
-  __syncthreads();
 }
 
 // ---------------------------------------------------------------------
 // The fit kernel.  Real = double: plain FP64 path; Real = float: FP32 path.
 
-template <class Real, int DMAX>
-__global__ void __launch_bounds__(kThreads) fit_kernel(FitArgs a) {
-  using L = Layout<Real, DMAX>;
-  constexpr int NM = L::NM;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  FitShared<Real> &sh = *reinterpret_cast<FitShared<Real> *>(smem_raw);
-  unsigned char *p = smem_raw + ((sizeof(FitShared<Real>) + 15) & ~size_t(15));
-  Real *rows = reinterpret_cast<Real *>(p);   // [ROWS][kChP], also reduction scratch
-  Real *red = rows;
-  p += L::buf_bytes;
-  Real *G = reinterpret_cast<Real *>(p);
-  p += L::G_bytes;
-  float *xs = reinterpret_cast<float *>(p);   // [4][kSampleCache]
-  p += L::samples_bytes;
-  Real *bcache = reinterpret_cast<Real *>(p); // [(nm-1)][mc]
-  p += L::cache_bytes;
-  Real *rvec = reinterpret_cast<Real *>(p);   // [2][kCh]
+constexpr int kMaxWarps = 8;
 
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  for (int64_t f = blockIdx.x; f < a.F; f += gridDim.x) {
-    // ---------------- phase 0: range, degree, validation, box
+template <class Real, int DMAX>
+__global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warps_per_cta) {
+  using WF = WarpFit<Real, DMAX>;
+  constexpr int NM = WF::NM;
+  constexpr int NAUG = WF::NAUG;
+  constexpr int LDS = WF::LDS;
+  constexpr int S2 = (NM + 1) / 2;                       // 2x2 tiles of the Psi Gram
+  constexpr int T2 = (S2 * (S2 + 1) / 2 + 31) / 32;
+  constexpr int S4 = (NAUG + 3) / 4;                     // 4x4 tiles of the design Gram
+  constexpr int T4 = (S4 * (S4 + 1) / 2 + 31) / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (wid >= warps_per_cta) return;
+  WF &w = *reinterpret_cast<WF *>(smem_raw + warpfit_bytes<Real, DMAX>() * wid);
+  const int64_t nwarps = (int64_t)gridDim.x * warps_per_cta;
+  for (int64_t f = (int64_t)blockIdx.x * warps_per_cta + wid; f < a.F; f += nwarps) {
+    // ---------------- phase 0: range, degree, validation, box, distinct values
     const int64_t b0 = a.off[f], b1 = a.off[f + 1];
     const int d = a.degs ? (int)a.degs[f] : a.d_uniform;
     const bool range_ok = b0 >= 0 && b1 >= b0 && b1 <= a.S;
     const int m = range_ok ? (int)(b1 - b0) : 0;
     double *cf = a.coef + f * kStride;
-    for (int j = tid; j < kStride; j += kThreads) {
+    for (int j = lane; j < kStride; j += 32) {
       cf[j] = 0.0;
       if (a.coef32) a.coef32[f * kStride + j] = 0.0f;
     }
-    if (tid < 6) a.box[f * 6 + tid] = 0.0;
+    if (lane < 6) a.box[f * 6 + lane] = 0.0;
     if (d < 1 || d > DMAX || m == 0) {
-      if (tid == 0) {
+      if (lane == 0) {
         a.status[f] = RP_FIT_EMPTY;
         a.rank[f] = 0;
       }
-      __syncthreads();
       continue;
     }
     const int nm = num_monomials(d);
     const int nc = nm - 1;
     const int naug = 2 * nm;
     const int n = naug - 1;
-    const bool cached = m <= kSampleCache;
-    const int mc = (sizeof(Real) == 4 && m * nc <= kCacheFloats) ? m : 0;  // basis cache
     const float *gx0 = a.x + b0, *gx1 = a.x + a.S + b0, *gx2 = a.x + 2 * a.S + b0, *gy = a.y + b0;
+    if (lane < 3 * (kMaxDeg + 1)) (&w.dslot[0][0])[lane] = kEmpty;
+    __syncwarp();
     float lmin[3] = {INFINITY, INFINITY, INFINITY}, lmax[3] = {-INFINITY, -INFINITY, -INFINITY};
-    int lbad = 0;
-    if (tid == 0) sh.bad = 0;
-    if (tid < 3 * (kMaxDeg + 1)) (&sh.dslot[0][0])[tid] = kEmpty;
-    __syncthreads();
-    for (int i = tid; i < m; i += kThreads) {
+    int bad = 0;
+    for (int i = lane; i < m; i += 32) {
       const float v0 = gx0[i], v1 = gx1[i], v2 = gx2[i], yy = gy[i];
-      distinct_insert(sh.dslot[0], v0);
-      distinct_insert(sh.dslot[1], v1);
-      distinct_insert(sh.dslot[2], v2);
-      if (cached) {
-        xs[i] = v0;
-        xs[kSampleCache + i] = v1;
-        xs[2 * kSampleCache + i] = v2;
-        xs[3 * kSampleCache + i] = yy;
-      }
-      if (!(isfinite(v0) && isfinite(v1) && isfinite(v2) && isfinite(yy))) lbad |= RP_FIT_NONFINITE;
-      else if (a.weighted && !(yy > 0.0f)) lbad |= RP_FIT_NONPOS_Y;
+      distinct_insert(w.dslot[0], v0);
+      distinct_insert(w.dslot[1], v1);
+      distinct_insert(w.dslot[2], v2);
+      if (!(isfinite(v0) && isfinite(v1) && isfinite(v2) && isfinite(yy))) bad |= RP_FIT_NONFINITE;
+      else if (a.weighted && !(yy > 0.0f)) bad |= RP_FIT_NONPOS_Y;
       lmin[0] = fminf(lmin[0], v0); lmax[0] = fmaxf(lmax[0], v0);
       lmin[1] = fminf(lmin[1], v1); lmax[1] = fmaxf(lmax[1], v1);
       lmin[2] = fminf(lmin[2], v2); lmax[2] = fmaxf(lmax[2], v2);
@@ -424,435 +387,383 @@ __global__ void __launch_bounds__(kThreads) fit_kernel(FitArgs a) {
         lmax[v] = fmaxf(lmax[v], __shfl_xor_sync(0xffffffffu, lmax[v], o));
       }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lbad |= __shfl_xor_sync(0xffffffffu, lbad, o);
-    __syncthreads();
-    if (lane == 0) {
-      for (int v = 0; v < 3; ++v) {
-        sh.red_f[wid][v] = lmin[v];
-        sh.red_f[wid][3 + v] = lmax[v];
-      }
-      if (lbad) atomicOr(&sh.bad, lbad);
-    }
-    __syncthreads();
-    if (tid < 3) {
-      float mn = INFINITY, mx = -INFINITY;
-      for (int w = 0; w < kThreads / 32; ++w) {
-        mn = fminf(mn, sh.red_f[w][tid]);
-        mx = fmaxf(mx, sh.red_f[w][3 + tid]);
-      }
-      sh.lo[tid] = mn;
-      sh.hi[tid] = mx;
-      if (mx > mn) {   // x' = 2 (x - lo) / (hi - lo) - 1 = x * sc + of
-        const double sc = 2.0 / ((double)mx - (double)mn);
-        sh.sc_v[tid] = (float)sc;
-        sh.of_v[tid] = (float)(-1.0 - (double)mn * sc);
-      } else {
-        sh.sc_v[tid] = 0.0f;
-        sh.of_v[tid] = 0.0f;
-      }
-    }
-    __syncthreads();
-    if (sh.bad) {
-      if (tid == 0) {
-        a.status[f] = (sh.bad & RP_FIT_NONFINITE) ? RP_FIT_NONFINITE : RP_FIT_NONPOS_Y;
+    for (int o = 16; o > 0; o >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    if (bad) {
+      if (lane == 0) {
+        a.status[f] = (bad & RP_FIT_NONFINITE) ? RP_FIT_NONFINITE : RP_FIT_NONPOS_Y;
         a.rank[f] = 0;
       }
-      __syncthreads();
       continue;
     }
-    if (tid < 3) {
-      a.box[f * 6 + 2 * tid] = sh.lo[tid];
-      a.box[f * 6 + 2 * tid + 1] = sh.hi[tid];
+    if (lane < 3) {
+      const double mn = lmin[lane], mx = lmax[lane];
+      w.lo[lane] = mn;
+      w.hi[lane] = mx;
+      a.box[f * 6 + 2 * lane] = mn;
+      a.box[f * 6 + 2 * lane + 1] = mx;
+      if (mx > mn) {   // x' = 2 (x - lo) / (hi - lo) - 1 = x * sc + of
+        const double sc = 2.0 / (mx - mn);
+        w.sc_v[lane] = (Real)sc;
+        w.of_v[lane] = (Real)(-1.0 - mn * sc);
+      } else {
+        w.sc_v[lane] = 0;
+        w.of_v[lane] = 0;
+      }
     }
-    const float *sx0 = cached ? xs : gx0;
-    const float *sx1 = cached ? xs + kSampleCache : gx1;
-    const float *sx2 = cached ? xs + 2 * kSampleCache : gx2;
-    const float *sy = cached ? xs + 3 * kSampleCache : gy;
+    __syncwarp();
 
     // ---------------- phase 1: standardisation, marginal orthonormal polynomials
     {
-      float acc[3] = {0, 0, 0};
-      for (int i = tid; i < m; i += kThreads) {
-        acc[0] += fmaf(sx0[i], sh.sc_v[0], sh.of_v[0]);
-        acc[1] += fmaf(sx1[i], sh.sc_v[1], sh.of_v[1]);
-        acc[2] += fmaf(sx2[i], sh.sc_v[2], sh.of_v[2]);
+      Real acc[3] = {0, 0, 0};
+      for (int i = lane; i < m; i += 32) {
+        acc[0] += fma((Real)gx0[i], w.sc_v[0], w.of_v[0]);
+        acc[1] += fma((Real)gx1[i], w.sc_v[1], w.of_v[1]);
+        acc[2] += fma((Real)gx2[i], w.sc_v[2], w.of_v[2]);
       }
+      Real mu[3];
 #pragma unroll
-      for (int v = 0; v < 3; ++v) acc[v] = warp_sum(acc[v]);
-      if (lane == 0)
-        for (int v = 0; v < 3; ++v) sh.red_f[wid][v] = acc[v];
-      __syncthreads();
-      if (tid < 3) {
-        float s = 0;
-        for (int w = 0; w < kThreads / 32; ++w) s += sh.red_f[w][tid];
-        sh.mu_v[tid] = s / (float)m;
-      }
-      __syncthreads();
-      float mom[3][2 * kMaxDeg];
+      for (int v = 0; v < 3; ++v) mu[v] = warp_sum(acc[v]) / (Real)m;
+      Real mom[3][2 * kMaxDeg];
 #pragma unroll
       for (int v = 0; v < 3; ++v)
 #pragma unroll
-        for (int k = 0; k < 2 * kMaxDeg; ++k) mom[v][k] = 0.0f;
-      for (int i = tid; i < m; i += kThreads) {
-        const float xv[3] = {sx0[i], sx1[i], sx2[i]};
+        for (int k = 0; k < 2 * kMaxDeg; ++k) mom[v][k] = 0;
+      for (int i = lane; i < m; i += 32) {
+        const float xv[3] = {gx0[i], gx1[i], gx2[i]};
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
-          const float c = fmaf(xv[v], sh.sc_v[v], sh.of_v[v]) - sh.mu_v[v];
-          float pw = c;
+          const Real c = fma((Real)xv[v], w.sc_v[v], w.of_v[v]) - mu[v];
+          Real pw = c;
 #pragma unroll
-          for (int k = 0; k < 2 * kMaxDeg; ++k) {
+          for (int k = 0; k < 2 * DMAX; ++k) {
             mom[v][k] += pw;
             pw *= c;
           }
         }
       }
+      double M[3][2 * kMaxDeg + 1];
 #pragma unroll
-      for (int v = 0; v < 3; ++v)
+      for (int v = 0; v < 3; ++v) {
+        M[v][0] = 1.0;
 #pragma unroll
-        for (int k = 0; k < 2 * kMaxDeg; ++k) {
-          const float s = warp_sum(mom[v][k]);
-          if (lane == 0) sh.red_d[wid][v * 8 + k] = (double)s;
-        }
-      __syncthreads();
-      if (tid < 3) {
-        const int v = tid;
-        double M[2 * kMaxDeg + 1];
-        M[0] = 1.0;
-        for (int k = 1; k <= 2 * kMaxDeg; ++k) {
-          double s = 0;
-          for (int w = 0; w < kThreads / 32; ++w) s += sh.red_d[w][v * 8 + (k - 1)];
-          M[k] = s / (double)m;
-        }
-        const double var = M[2];
-        if (sh.sc_v[v] == 0.0f || !(var > 0.0)) {
-          sh.isg_v[v] = 0.0f;
-          for (int l = 0; l <= kMaxDeg; ++l)
-            for (int k = 0; k <= kMaxDeg; ++k) sh.Tm[v][l][k] = (l == 0 && k == 0) ? 1.0f : 0.0f;
+        for (int k = 0; k < 2 * DMAX; ++k) M[v][k + 1] = (double)warp_sum(mom[v][k]) / (double)m;
+      }
+      if (lane < 3) {
+        const int v = lane;
+        const double var = M[v][2];
+        w.mu_v[v] = mu[v];
+        for (int l = 0; l <= kMaxDeg; ++l)
+          for (int k = 0; k <= kMaxDeg; ++k) w.Tm[v][l][k] = (l == 0 && k == 0) ? (Real)1 : (Real)0;
+        if (w.sc_v[v] == (Real)0 || !(var > 0.0)) {
+          w.isg_v[v] = 0;
         } else {
           const double isg = 1.0 / sqrt(var);
-          sh.isg_v[v] = (float)isg;
+          w.isg_v[v] = (Real)isg;
           double Ms[2 * kMaxDeg + 1];
           Ms[0] = 1.0;
           double pw = isg;
-          for (int k = 1; k <= 2 * kMaxDeg; ++k) {
-            Ms[k] = M[k] * pw;
+          for (int k = 1; k <= 2 * DMAX; ++k) {
+            Ms[k] = M[v][k] * pw;
             pw *= isg;
           }
           int cnt = 0;
-          for (int k = 0; k <= kMaxDeg; ++k) cnt += sh.dslot[v][k] != kEmpty;
-          marginal_transform(Ms, d, min(d, cnt - 1), sh.Tm[v]);
+          for (int k = 0; k <= kMaxDeg; ++k) cnt += w.dslot[v][k] != kEmpty;
+          float T[kMaxDeg + 1][kMaxDeg + 1];
+          marginal_transform(Ms, d, min(d, cnt - 1), T);
+          for (int l = 0; l <= kMaxDeg; ++l)
+            for (int k = 0; k <= kMaxDeg; ++k) w.Tm[v][l][k] = (Real)T[l][k];
         }
       }
-      __syncthreads();
+      __syncwarp();
     }
 
     // ---------------- phase 2: Gram of Psi (nm columns), means, whitening
     {
-      const int side = (nm + 3) / 4;
+      const int side = (nm + 1) / 2;
       const int ntiles = side * (side + 1) / 2;
-      const int sgc = max(1, kThreads / ntiles);
-      GramAcc<Real> acc;
+      Real acc[T2][4];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) acc.s[i] = acc.c[i] = 0;
-      for (int base = 0; base < m; base += kCh) {
-        const int cnt = min(kCh, m - base);
-        if (tid < cnt) {
-          const int i = base + tid;
-          Real psi[NM];
-          eval_psi<Real, NM>(sh, d, nm, sx0[i], sx1[i], sx2[i], psi);
+      for (int k = 0; k < T2; ++k)
 #pragma unroll
-          for (int j = 0; j < NM; ++j)
-            if (j < 4 * side) rows[j * kChP + tid] = psi[j];
-          for (int j = NM; j < 4 * side; ++j) rows[j * kChP + tid] = 0;
+        for (int i = 0; i < 4; ++i) acc[k][i] = 0;
+      for (int base = 0; base < m; base += 32) {
+        const int i = base + lane;
+        Real psi[NM];
+        if (i < m) {
+          eval_psi<Real, DMAX, NM>(w, d, nm, gx0[i], gx1[i], gx2[i], psi);
+        } else {
+#pragma unroll
+          for (int j = 0; j < NM; ++j) psi[j] = 0;
         }
-        __syncthreads();
-        gram_chunk<Real>(rows, cnt, ntiles, sgc, acc);
-        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 2 * S2; ++j) w.stage[lane * LDS + j] = (j < NM) ? psi[j] : (Real)0;
+        __syncwarp();
+        gram_stage<Real, 2, T2, LDS>(w.stage, ntiles, acc);
+        __syncwarp();
       }
-      gram_finish<Real>(acc, ntiles, sgc, nm, G, red);
+      gram_store<Real, 2, T2>(acc, ntiles, nm, w.G);
+      __syncwarp();
       // means (row 0 holds the sums of Psi_j) and the centred Gram / m of the
-      // non-constant functions, equilibrated and factored by warp 0
-      if (tid < NM) sh.mupsi[tid] = (tid < nm) ? G[tid] / (Real)m : (Real)0;
-      for (int e = tid; e < NM * NM; e += kThreads) (&sh.W[0][0])[e] = 0;
-      __syncthreads();
-      for (int e = tid; e < nc * nc; e += kThreads) {
+      // non-constant functions, equilibrated, in `stage`
+      for (int j = lane; j < NM; j += 32) w.mupsi[j] = (j < nm) ? w.G[j] / (Real)m : (Real)0;
+      for (int e = lane; e < NM * NM; e += 32) w.W[e] = 0;
+      __syncwarp();
+      for (int e = lane; e < nc * nc; e += 32) {
         const int i = e / nc + 1, j = e % nc + 1;
-        red[e] = (G[i * nm + j] - (Real)m * sh.mupsi[i] * sh.mupsi[j]) / (Real)m;
+        w.stage[e] = (w.G[i * nm + j] - (Real)m * w.mupsi[i] * w.mupsi[j]) / (Real)m;
       }
-      __syncthreads();
-      if (tid < nc) {
-        const Real dg = red[tid * nc + tid];
-        sh.scl[tid] = dg > 0 ? rsqrt_pos<Real>(dg) : (Real)0;
+      __syncwarp();
+      for (int j = lane; j < nc; j += 32) {
+        const Real dg = w.stage[j * nc + j];
+        w.scl[j] = dg > 0 ? rsqrt_pos<Real>(dg) : (Real)0;
       }
-      __syncthreads();
-      for (int e = tid; e < nc * nc; e += kThreads) red[e] *= sh.scl[e / nc] * sh.scl[e % nc];
-      __syncthreads();
+      __syncwarp();
+      for (int e = lane; e < nc * nc; e += 32) w.stage[e] *= w.scl[e / nc] * w.scl[e % nc];
       // the whitening only preconditions: any positive pivot is kept (the
-      // basis stays a basis of the same space); only exactly dependent
-      // directions (pivot at rounding level or below) are dropped
-      if (wid == 0)
-        warp_chol<Real>(red, nc, nc, sizeof(Real) == 8 ? (Real)1e-14 : (Real)1e-10, sh.invw,
-                        &sh.keep_w);
-      __syncthreads();
-      // R^{-1} (R = L^T, R[i][l] = L[l][i]), column j by back substitution,
-      // one thread per column, into G (free now); then W = D R^{-1}
-      if (tid < nc) {
-        const int j = tid;
+      // basis stays a basis of the same space); only directions whose pivot
+      // is at rounding level or below are dropped
+      warp_chol<Real>(w.stage, nc, nc, sizeof(Real) == 8 ? (Real)1e-14 : (Real)1e-10, w.invw,
+                      &w.keep_w);
+      // R^{-1} (R = L^T, R[i][l] = L[l][i]) column by column into G; W = D R^{-1}
+      for (int j = lane; j < nc; j += 32)
         for (int i = j; i >= 0; --i) {
           Real s = (i == j) ? (Real)1 : (Real)0;
-          for (int l = i + 1; l <= j; ++l) s -= red[l * nc + i] * G[l * nc + j];
-          G[i * nc + j] = s * sh.invw[i];
+          for (int l = i + 1; l <= j; ++l) s -= w.stage[l * nc + i] * w.G[l * nc + j];
+          w.G[i * nc + j] = s * w.invw[i];
         }
-      }
-      __syncthreads();
-      for (int e = tid; e < nc * nc; e += kThreads) {
+      __syncwarp();
+      for (int e = lane; e < nc * nc; e += 32) {
         const int i = e / nc, j = e % nc;
-        if (i <= j) sh.W[i + 1][j + 1] = G[i * nc + j] * sh.scl[i];
+        if (i <= j) w.W[(i + 1) * NM + (j + 1)] = w.G[i * nc + j] * w.scl[i];
       }
-      __syncthreads();
+      __syncwarp();
     }
 
-    // ---------------- phase 3: whitened basis (cached) and the design Gram
-    // columns: [num (nm) | den (nm-1) | rhs]
+    // ---------------- phase 3: the design Gram [num (nm) | den (nm-1) | rhs]
     {
       const int side = (naug + 3) / 4;
       const int ntiles = side * (side + 1) / 2;
-      const int sgc = max(1, kThreads / ntiles);
-      GramAcc<Real> acc;
+      Real acc[T4][16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) acc.s[i] = acc.c[i] = 0;
-      for (int base = 0; base < m; base += kCh) {
-        const int cnt = min(kCh, m - base);
-        if (tid < cnt) {
-          const int i = base + tid;
+      for (int k = 0; k < T4; ++k)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc[k][i] = 0;
+      for (int base = 0; base < m; base += 32) {
+        const int i = base + lane;
+        Real *row = w.stage + lane * LDS;
+        if (i < m) {
           Real psi[NM], pt[NM];
-          eval_psi<Real, NM>(sh, d, nm, sx0[i], sx1[i], sx2[i], psi);
-          whiten<Real, NM>(sh, psi, pt);
-          if (i < mc) {
-#pragma unroll
-            for (int j = 1; j < NM; ++j)
-              if (j < nm) bcache[(j - 1) * mc + i] = pt[j];
-          }
-          const Real yy = (Real)sy[i];
-          const Real w = a.weighted ? (Real)1 / fabs(yy) : (Real)1;
+          eval_psi<Real, DMAX, NM>(w, d, nm, gx0[i], gx1[i], gx2[i], psi);
+          whiten<Real, DMAX, NM>(w, psi, pt);
+          const Real yy = (Real)gy[i];
+          const Real wt = a.weighted ? (Real)1 / fabs(yy) : (Real)1;
 #pragma unroll
           for (int j = 0; j < NM; ++j)
-            if (j < nm) rows[j * kChP + tid] = w * pt[j];
+            if (j < nm) row[j] = wt * pt[j];
 #pragma unroll
           for (int j = 1; j < NM; ++j)
-            if (j < nm) rows[(nm + j - 1) * kChP + tid] = -w * yy * pt[j];
-          rows[n * kChP + tid] = w * yy;
-          for (int j = naug; j < 4 * side; ++j) rows[j * kChP + tid] = 0;
+            if (j < nm) row[nm + j - 1] = -wt * yy * pt[j];
+          row[n] = wt * yy;
+          for (int j = naug; j < 4 * S4; ++j) row[j] = 0;
+        } else {
+          for (int j = 0; j < 4 * S4; ++j) row[j] = 0;
         }
-        __syncthreads();
-        gram_chunk<Real>(rows, cnt, ntiles, sgc, acc);
-        __syncthreads();
+        __syncwarp();
+        gram_stage<Real, 4, T4, LDS>(w.stage, ntiles, acc);
+        __syncwarp();
       }
-      gram_finish<Real>(acc, ntiles, sgc, naug, G, red);
+      gram_store<Real, 4, T4>(acc, ntiles, naug, w.G);
+      __syncwarp();
     }
 
     // ---------------- phase 4: equilibrate, factor, first solve
     // The leading n x n block of G (stride naug) is the normal matrix and
-    // column n holds A^T b; the scaled block is factored in G with stride n.
+    // column n holds A^T b; the scaled block is compacted in place to stride n
+    // (row by row: each destination row ends before the next source row).
     {
-      if (tid < n) {
-        const Real dg = G[tid * naug + tid];
-        sh.scl[tid] = dg > 0 ? rsqrt_pos<Real>(dg) : (Real)0;
-        sh.gvec[tid] = G[tid * naug + n];
+      for (int j = lane; j < n; j += 32) {
+        const Real dg = w.G[j * naug + j];
+        w.scl[j] = dg > 0 ? rsqrt_pos<Real>(dg) : (Real)0;
+        w.gvec[j] = w.G[j * naug + n];
       }
-      __syncthreads();
-      for (int e = tid; e < n * n; e += kThreads) {
-        const int i = e / n, j = e % n;
-        red[e] = G[i * naug + j] * sh.scl[i] * sh.scl[j];
+      __syncwarp();
+      for (int i = 0; i < n; ++i) {
+        Real v[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const int j = lane + 32 * r;
+          v[r] = (j < n) ? w.G[i * naug + j] * w.scl[i] * w.scl[j] : (Real)0;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const int j = lane + 32 * r;
+          if (j < n) w.G[i * n + j] = v[r];
+        }
+        __syncwarp();
       }
-      __syncthreads();
-      for (int e = tid; e < n * n; e += kThreads) G[e] = red[e];
-      if (tid < n) sh.gvec[tid] *= sh.scl[tid];
-      __syncthreads();
-      if (wid == 0) {
-        warp_chol<Real>(G, n, n, (Real)a.drop_tol, sh.invd, &sh.keep_cnt);
-        warp_solve<Real>(G, n, n, sh.invd, sh.gvec);
-      }
-      __syncthreads();
-      if (tid < n) sh.xsol[tid] = (double)(sh.gvec[tid] * sh.scl[tid]);
-      if (tid == 0) sh.flags = (sh.keep_cnt < n) ? RP_FIT_RANK_DEFICIENT : 0;
-      __syncthreads();
+      for (int j = lane; j < n; j += 32) w.gvec[j] *= w.scl[j];
+      warp_chol<Real>(w.G, n, n, (Real)a.drop_tol, w.invd, &w.keep_cnt);
+      warp_solve<Real>(w.G, n, n, w.invd, w.gvec);
+      for (int j = lane; j < n; j += 32) w.xsol[j] = (double)(w.gvec[j] * w.scl[j]);
+      __syncwarp();
     }
 
-    // ---------------- phase 5: refinement from the samples, then a final
-    // pass checking q > 0 at every sample
-    const int sgc = max(1, kThreads / nm);
+    // ---------------- phase 5: refinement from the samples.  Every pass also
+    // checks q > 0 at the samples for the solution it starts from.
+    int flags = (w.keep_cnt < n) ? RP_FIT_RANK_DEFICIENT : 0;
     float prev_rel = INFINITY;
-    int refine_state = 0;  // 0 running, 1 converged, 2 stalled
-    for (int it = 0; it <= a.max_refine; ++it) {
-      const bool final_pass = (it == a.max_refine) || refine_state != 0;
-      if (tid < n) {
-        const double xv = sh.xsol[tid];
+    int state = 0;  // 0 running, 1 converged, 2 stalled
+    int it = 0;
+    for (;; ++it) {
+      const bool update = it < a.max_refine;
+      for (int j = lane; j < n; j += 32) {
+        const double xv = w.xsol[j];
         const float h = (float)xv;
-        sh.xhi[tid] = h;
-        sh.xlo[tid] = (float)(xv - (double)h);
+        w.xhi[j] = h;
+        w.xlo[j] = (float)(xv - (double)h);
       }
-      if (tid == 0) sh.bad = 0;
-      __syncthreads();
-      // g = A^T r, r = b - A x.  With rows w [pt, -y pt'],
-      // g_num_j = sum_i (w r)_i pt_ij and g_den_j = -sum_i (w y r)_i pt_ij.
-      Real gn = 0, gd = 0, cn = 0, cd = 0;
+      __syncwarp();
+      Real gn[2] = {0, 0}, gd[2] = {0, 0};
       int pole = 0;
-      for (int base = 0; base < m; base += kCh) {
-        const int cnt = min(kCh, m - base);
-        if (tid < cnt) {
-          const int i = base + tid;
-          Real pt[NM];
-          if (i < mc) {
-            pt[0] = 1;
+      for (int base = 0; base < m; base += 32) {
+        const int i = base + lane;
+        Real r = 0, yy = 0, wt = 0;
+        Real pt[NM];
+        if (i < m) {
+          Real psi[NM];
+          eval_psi<Real, DMAX, NM>(w, d, nm, gx0[i], gx1[i], gx2[i], psi);
+          whiten<Real, DMAX, NM>(w, psi, pt);
+          double q = 1.0;
 #pragma unroll
-            for (int j = 1; j < NM; ++j) pt[j] = (j < nm) ? bcache[(j - 1) * mc + i] : (Real)0;
-          } else {
-            Real psi[NM];
-            eval_psi<Real, NM>(sh, d, nm, sx0[i], sx1[i], sx2[i], psi);
-            whiten<Real, NM>(sh, psi, pt);
-#pragma unroll
-            for (int j = 1; j < NM; ++j)
-              if (j < nm) rows[(j - 1) * kChP + tid] = pt[j];
-          }
-          if (final_pass) {
-            double q = 1.0;
-#pragma unroll
-            for (int j = 1; j < NM; ++j)
-              if (j < nm) q += sh.xsol[nm + j - 1] * (double)pt[j];
-            pole |= !(q > 0.0);
-          } else {
-            const Real yy = (Real)sy[i];
-            const Real w = a.weighted ? (Real)1 / fabs(yy) : (Real)1;
-            Real r;
+          for (int j = 1; j < NM; ++j)
+            if (j < nm) q += w.xsol[nm + j - 1] * (double)pt[j];
+          pole |= !(q > 0.0);
+          yy = (Real)gy[i];
+          wt = a.weighted ? (Real)1 / fabs(yy) : (Real)1;
+          if (update) {
             if constexpr (sizeof(Real) == 8) {
-              double s = w * yy;
+              double sacc = wt * yy;
 #pragma unroll
               for (int j = 0; j < NM; ++j)
-                if (j < nm) s -= w * pt[j] * sh.xsol[j];
+                if (j < nm) sacc -= wt * pt[j] * w.xsol[j];
 #pragma unroll
               for (int j = 1; j < NM; ++j)
-                if (j < nm) s += w * yy * pt[j] * sh.xsol[nm + j - 1];
-              r = s;
+                if (j < nm) sacc += wt * yy * pt[j] * w.xsol[nm + j - 1];
+              r = sacc;
             } else {
               // compensated dot product (Ogita, Rump & Oishi 2005, "Dot2") of
               // the float row with the split solution xhi + xlo
-              const float wy = w * yy;
-              float s = wy, c = 0.0f;
+              const float wy = wt * yy;
+              float sacc = wy, c = 0.0f;
 #pragma unroll
               for (int j = 0; j < 2 * NM - 1; ++j) {
                 const bool num = j < NM;
                 const int jj = num ? j : j - NM + 1;
                 if (jj < nm) {
                   const int col = num ? jj : nm + jj - 1;
-                  const float av = num ? w * pt[jj] : -wy * pt[jj];
-                  const float pr = av * sh.xhi[col];
-                  const float pe = fmaf(av, sh.xhi[col], -pr);
+                  const float av = num ? wt * pt[jj] : -wy * pt[jj];
+                  const float pr = av * w.xhi[col];
+                  const float pe = fmaf(av, w.xhi[col], -pr);
                   float t, e;
-                  two_sum(s, -pr, t, e);
-                  s = t;
-                  c += e - pe - av * sh.xlo[col];
+                  two_sum(sacc, -pr, t, e);
+                  sacc = t;
+                  c += e - pe - av * w.xlo[col];
                 }
               }
-              r = s + c;
+              r = sacc + c;
             }
-            rvec[tid] = w * r;
-            rvec[kCh + tid] = w * yy * r;
           }
+        } else {
+#pragma unroll
+          for (int j = 0; j < NM; ++j) pt[j] = 0;
         }
-        __syncthreads();
-        if (!final_pass && tid < nm * sgc) {
-          const int j = tid % nm, g = tid / nm;
-          Real pn = 0, pd = 0;
-          for (int s2 = g; s2 < cnt; s2 += sgc) {
-            const int i2 = base + s2;
-            const Real bv = (j == 0) ? (Real)1
-                                     : (i2 < mc ? bcache[(j - 1) * mc + i2] : rows[(j - 1) * kChP + s2]);
-            pn = fma(bv, rvec[s2], pn);
-            pd = fma(bv, rvec[kCh + s2], pd);
+        if (update) {
+          // g_num_j = sum_i (w r)_i pt_ij,  g_den_j = -sum_i (w y r)_i pt_ij
+#pragma unroll
+          for (int j = 0; j < NM; ++j) w.stage[lane * LDS + j] = pt[j];
+          w.rbuf[0][lane] = wt * r;
+          w.rbuf[1][lane] = wt * yy * r;
+          __syncwarp();
+#pragma unroll
+          for (int rr = 0; rr < 2; ++rr) {
+            const int j = lane + 32 * rr;
+            if (j < nm) {
+              Real pn = 0, pd = 0;
+#pragma unroll 8
+              for (int s = 0; s < 32; ++s) {
+                const Real bv = w.stage[s * LDS + j];
+                pn = fma(bv, w.rbuf[0][s], pn);
+                pd = fma(bv, w.rbuf[1][s], pd);
+              }
+              gn[rr] += pn;
+              gd[rr] += pd;
+            }
           }
-          const Real y1 = pn - cn, t1 = gn + y1;
-          cn = (t1 - gn) - y1;
-          gn = t1;
-          const Real y2 = pd - cd, t2 = gd + y2;
-          cd = (t2 - gd) - y2;
-          gd = t2;
+          __syncwarp();
         }
-        __syncthreads();
       }
-      if (final_pass) {
-        if (pole) atomicOr(&sh.bad, 1);
-        __syncthreads();
-        if (tid == 0) {
-          if (sh.bad) sh.flags |= RP_FIT_POLE;
-          if (refine_state != 1 && a.max_refine > 0) sh.flags |= RP_FIT_NOT_CONVERGED;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) pole |= __shfl_xor_sync(0xffffffffu, pole, o);
+      flags = (flags & ~RP_FIT_POLE) | (pole ? RP_FIT_POLE : 0);
+      if (!update) break;
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        const int j = lane + 32 * rr;
+        if (j < nm) {
+          w.gvec[j] = gn[rr] * w.scl[j];
+          if (j >= 1) w.gvec[nm + j - 1] = -gd[rr] * w.scl[nm + j - 1];
         }
-        __syncthreads();
+      }
+      __syncwarp();
+      warp_solve<Real>(w.G, n, n, w.invd, w.gvec);
+      float dn = 0, xn = 0;
+      for (int j = lane; j < n; j += 32) {
+        const double dx = (double)(w.gvec[j] * w.scl[j]);
+        const double xv = w.xsol[j] + dx;
+        w.xsol[j] = xv;
+        dn += (float)(dx * dx);
+        xn += (float)(xv * xv);
+      }
+      dn = warp_sum(dn);
+      xn = warp_sum(xn);
+      __syncwarp();
+      const float rel = xn > 0.0f ? sqrtf(dn / xn) : 0.0f;
+      if (rel <= (float)a.tol) state = 1;
+      else if (it >= 1 && rel > 0.5f * prev_rel) state = (rel <= 1e-5f) ? 1 : 2;
+      prev_rel = rel;
+      if (state != 0) {
+        ++it;
         break;
       }
-      if (tid < nm * sgc) {
-        red[tid] = gn - cn;
-        red[kThreads + tid] = gd - cd;
-      }
-      __syncthreads();
-      if (tid < nm) {
-        Real sn = 0, sd = 0;
-        for (int g = 0; g < sgc; ++g) {
-          sn += red[g * nm + tid];
-          sd += red[kThreads + g * nm + tid];
-        }
-        sh.gvec[tid] = sn * sh.scl[tid];
-        if (tid >= 1) sh.gvec[nm + tid - 1] = -sd * sh.scl[nm + tid - 1];
-      }
-      __syncthreads();
-      if (wid == 0) {
-        warp_solve<Real>(G, n, n, sh.invd, sh.gvec);
-        float dn = 0, xn = 0;
-        for (int j = lane; j < n; j += 32) {
-          const double dx = (double)(sh.gvec[j] * sh.scl[j]);
-          const double xv = sh.xsol[j] + dx;
-          sh.xsol[j] = xv;
-          dn += (float)(dx * dx);
-          xn += (float)(xv * xv);
-        }
-        dn = warp_sum(dn);
-        xn = warp_sum(xn);
-        if (lane == 0) {
-          sh.dnorm = sqrtf(dn);
-          sh.xnorm = sqrtf(xn);
-        }
-      }
-      __syncthreads();
-      const float rel = sh.xnorm > 0.0f ? sh.dnorm / sh.xnorm : 0.0f;
-      if (rel <= (float)a.tol) refine_state = 1;
-      else if (it >= 1 && rel > 0.5f * prev_rel) refine_state = (rel <= 1e-5f) ? 1 : 2;
-      prev_rel = rel;
     }
+    if (a.max_refine > 0 && state != 1) flags |= RP_FIT_NOT_CONVERGED;
+    flags |= min(it, 255) << RP_FIT_ITER_SHIFT;
 
     // ---------------- phase 6: back to the monomial basis (FP64)
     {
-      double *cpsi = reinterpret_cast<double *>(red);   // [2][kMaxNm]
-      double *P = cpsi + 2 * kMaxNm;                      // [3][5][5]
-      if (tid < 2 * nm) {
-        const int which = tid / nm, i = tid % nm;   // 0 numerator, 1 denominator
+      double *cpsi = reinterpret_cast<double *>(w.stage);   // [2][kMaxNm]
+      double *P = cpsi + 2 * kMaxNm;                          // [3][5][5]
+      for (int e = lane; e < 2 * nm; e += 32) {
+        const int which = e / nm, i = e % nm;   // 0 numerator, 1 denominator
         if (i >= 1) {
           double u = 0;
           for (int j = i; j < nm; ++j) {
-            const double cj = which == 0 ? sh.xsol[j] : sh.xsol[nm + j - 1];
-            u += (double)sh.W[i][j] * cj;
+            const double cj = which == 0 ? w.xsol[j] : w.xsol[nm + j - 1];
+            u += (double)w.W[i * NM + j] * cj;
           }
           cpsi[which * kMaxNm + i] = u;
         }
       }
-      if (tid >= 96 && tid < 96 + 3 * (kMaxDeg + 1)) {
+      if (lane < 3 * (kMaxDeg + 1)) {
         // Q_k(u), u = (x' - mu) isg, as a polynomial in x'
-        const int v = (tid - 96) / (kMaxDeg + 1), k = (tid - 96) % (kMaxDeg + 1);
-        const double mu = sh.mu_v[v], isg = sh.isg_v[v];
+        const int v = lane / (kMaxDeg + 1), k = lane % (kMaxDeg + 1);
+        const double mu = w.mu_v[v], isg = w.isg_v[v];
         double out[kMaxDeg + 1] = {0, 0, 0, 0, 0};
         if (k <= d) {
           double isgl = 1.0;
           for (int l = 0; l <= k; ++l) {
-            const double t = sh.Tm[v][l][k];
+            const double t = w.Tm[v][l][k];
             if (t != 0.0) {
               double binom = 1.0;
               for (int ii = 0; ii <= l; ++ii) {
@@ -867,15 +778,15 @@ __global__ void __launch_bounds__(kThreads) fit_kernel(FitArgs a) {
         }
         for (int i2 = 0; i2 <= kMaxDeg; ++i2) P[(v * (kMaxDeg + 1) + k) * (kMaxDeg + 1) + i2] = out[i2];
       }
-      __syncthreads();
-      if (tid < 2) {
-        double c0 = tid == 0 ? sh.xsol[0] : 1.0;
-        for (int i = 1; i < nm; ++i) c0 -= (double)sh.mupsi[i] * cpsi[tid * kMaxNm + i];
-        cpsi[tid * kMaxNm] = c0;
+      __syncwarp();
+      if (lane < 2) {
+        double c0 = lane == 0 ? w.xsol[0] : 1.0;
+        for (int i = 1; i < nm; ++i) c0 -= (double)w.mupsi[i] * cpsi[lane * kMaxNm + i];
+        cpsi[lane * kMaxNm] = c0;
       }
-      __syncthreads();
-      if (tid < 2 * nm) {
-        const int which = tid / nm, t = tid % nm;
+      __syncwarp();
+      for (int e = lane; e < 2 * nm; e += 32) {
+        const int which = e / nm, t = e % nm;
         const int i0 = c_exp[t][0], i1 = c_exp[t][1], i2 = c_exp[t][2];
         double s = 0;
         for (int j = 0; j < nm; ++j) {
@@ -889,11 +800,11 @@ __global__ void __launch_bounds__(kThreads) fit_kernel(FitArgs a) {
         cf[o] = s;
         if (a.coef32) a.coef32[f * kStride + o] = (float)s;
       }
-      if (tid == 0) {
-        a.status[f] = sh.flags;
-        a.rank[f] = sh.keep_cnt;
+      if (lane == 0) {
+        a.status[f] = flags;
+        a.rank[f] = w.keep_cnt;
       }
-      __syncthreads();
+      __syncwarp();
     }
   }
 }
@@ -917,20 +828,36 @@ void set_tables() {
   done = true;
 }
 
+// Choose warps per CTA (1..8) to maximise resident warps per SM under the
+// per-warp shared-memory slice, then launch a persistent grid.
 template <class Real, int DMAX>
 cudaError_t launch_t(const FitArgs &a, cudaStream_t s) {
-  using L = Layout<Real, DMAX>;
-  const size_t smem = L::total;
+  const size_t per_warp = warpfit_bytes<Real, DMAX>();
+  int best_w = 1, best_total = 0, best_ctas = 1;
+  for (int wpc = kMaxWarps; wpc >= 1; wpc /= 2) {
+    const size_t smem = per_warp * wpc;
+    if (smem > 227 * 1024) continue;
+    cudaError_t e = cudaFuncSetAttribute(fit_kernel<Real, DMAX>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fit_kernel<Real, DMAX>, wpc * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm * wpc > best_total) {
+      best_total = per_sm * wpc;
+      best_w = wpc;
+      best_ctas = per_sm;
+    }
+  }
+  if (best_total == 0) return cudaErrorInvalidConfiguration;
+  const size_t smem = per_warp * best_w;
   cudaError_t e = cudaFuncSetAttribute(fit_kernel<Real, DMAX>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fit_kernel<Real, DMAX>, kThreads, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  int64_t grid = (int64_t)num_sms() * per_sm;
-  if (grid > a.F) grid = a.F;
-  fit_kernel<Real, DMAX><<<(unsigned)grid, kThreads, smem, s>>>(a);
+  int64_t grid = (int64_t)num_sms() * best_ctas;
+  const int64_t need = (a.F + best_w - 1) / best_w;
+  if (grid > need) grid = need;
+  fit_kernel<Real, DMAX><<<(unsigned)grid, best_w * 32, smem, s>>>(a, best_w);
   return cudaGetLastError();
 }
 

@@ -112,27 +112,30 @@ struct HwC {
   float issue;
 };
 
-// ceil(a / b) for a < 2^53, 1 <= b < 2^31: exact when the quotient is below
-// 2^22 (float estimate, then an exact integer remainder correction); above
-// that the float estimate (relative error < 2^-21) is returned.
-__device__ __forceinline__ float ceil_div_rep(uint64_t a, uint32_t b) {
-  const float qf = __fdiv_rn((float)a, (float)b);
-  if (qf >= 4194304.0f) return ceilf(qf);
-  int64_t q = (int64_t)qf;
-  int64_t r = (int64_t)a - q * (int64_t)b;
+// #Rep = ceil(blocks / D) for blocks = c0 * c1 (each < 2^32) and
+// 1 <= D < 2^25.  Exact (integer remainder correction of a float estimate)
+// when the quotient is below 2^22; above that the float estimate (relative
+// error < 2^-21) is used.  Only 32-bit int<->float conversions are used.
+__device__ __forceinline__ float rep_count(uint32_t c0, uint32_t c1, uint32_t D) {
+  const float qf = __fdividef((float)c0 * (float)c1, (float)D);
+  const uint64_t blocks = (uint64_t)c0 * c1;
+  const uint32_t q0 = (uint32_t)fminf(qf, 4194304.0f);
+  int64_t r = (int64_t)(blocks - (uint64_t)q0 * D);
+  int64_t q = q0;
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
     const bool lo = r < 0;
     q -= lo;
-    r += lo ? (int64_t)b : 0;
+    r += lo ? (int64_t)D : 0;
   }
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
-    const bool hi = r >= (int64_t)b;
+    const bool hi = r >= (int64_t)D;
     q += hi;
-    r -= hi ? (int64_t)b : 0;
+    r -= hi ? (int64_t)D : 0;
   }
-  return (float)(q + (r > 0));
+  const float exact = (float)(uint32_t)(q + (r > 0));
+  return qf < 4194304.0f ? exact : ceilf(qf);
 }
 
 // floor(a / b) for 0 <= a < 2^24, 1 <= b < 2^24 (exact).
@@ -141,6 +144,16 @@ __device__ __forceinline__ int floor_div_small(int a, int b) {
   q -= (q * b > a);
   q += ((q + 1) * b <= a);
   return q;
+}
+
+// ceil(n / 2^s) without overflow
+__device__ __forceinline__ uint32_t ceil_shift(uint32_t n, int s) {
+  return (n >> s) + ((n & ((1u << s) - 1u)) != 0u);
+}
+
+// x / y with y >= 0; +inf where y == 0
+__device__ __forceinline__ float div_pos(float x, float y) {
+  return y > 0.0f ? __fdividef(x, y) : INFINITY;
 }
 
 template <int D1>
@@ -166,9 +179,10 @@ __device__ __forceinline__ void load_row(const float *__restrict__ p, float (&c)
   }
 }
 
-// One thread per query; persistent grid-stride loop.  Every configuration
-// is evaluated in registers and the running (best, second, argmin) is kept
-// in registers, so no cross-thread reduction is needed.
+// One thread per query; persistent grid-stride loop.  Every configuration is
+// evaluated in registers without data-dependent branches (invalid and pole
+// configurations evaluate to +inf), and the running (best, second, argmin) is
+// kept in registers, so no cross-thread reduction is needed.
 template <int D1>
 __global__ void __launch_bounds__(256) search_kernel(ProgramView P, int64_t K, CfgTab cfg, HwC hw,
                                                      const float4 *__restrict__ q, int64_t Q,
@@ -200,6 +214,7 @@ __global__ void __launch_bounds__(256) search_kernel(ProgramView P, int64_t K, C
       const uint32_t nsm_i = (uint32_t)nsm;
       const bool grid1 = __ldg(P.grid + kid) == 1;
       const float *tab = P.table + (int64_t)kid * kNcfg * kNmet * 2 * D1;
+      bool any_pole = false;
       for (int c = 0; c < kNcfg; ++c) {
         float mv[kNmet];
         bool pole = false;
@@ -217,79 +232,66 @@ __global__ void __launch_bounds__(256) search_kernel(ProgramView P, int64_t K, C
           pole |= !(d > 0.0f) || !(d < 8.5e37f);
           mv[m] = __fdividef(p, d);
         }
-        if (pole) {
-          st |= RP_Q_POLE;
-          continue;
-        }
-        const int bact_w = cfg.bact_w[c];
-        if (bact_w == 0) continue;
         const float comp = fmaxf(mv[0], 0.0f), Cm = fmaxf(mv[1], 0.0f),
                     U = fmaxf(mv[2], 0.0f), upm = fmaxf(mv[3], 1.0f),
                     synch = fmaxf(mv[4], 0.0f), lbw = fmaxf(mv[5], 0.0f);
-        const float Rf = fmaxf(mv[6], 0.0f), Zf = fmaxf(mv[7], 0.0f);
-        if (!(Rf < 1.0e6f) || !(Zf < 1.0e7f)) continue;
+        // clamped at 2^24: above every admissible R_SM / Z_SM (< 2^24), so
+        // the configuration is invalid either way
+        const float Rf = fminf(fmaxf(mv[6], 0.0f), 16777216.0f);
+        const float Zf = fminf(fmaxf(mv[7], 0.0f), 16777216.0f);
         const int Ri = (int)floorf(Rf + 0.5f), Zi = (int)floorf(Zf + 0.5f);
         const int la = cfg.la[c], lb = cfg.lb[c];
         const int T = 1 << (la + lb);
         const int wpb = cfg.wpb[c];
-        if ((int64_t)Ri * T > hw.rsm || Zi > hw.zsm) continue;
-        int bact = bact_w;
-        if (Ri > 0) bact = min(bact, floor_div_small(hw.rsm, Ri * wpb * hw.warp));
-        if (Zi > 0) bact = min(bact, floor_div_small(hw.zsm, Zi));
-        if (bact <= 0) continue;
+        const int64_t bR = (int64_t)max(Ri, 1) * wpb * hw.warp;
+        const int tR = bR > hw.rsm ? 0 : floor_div_small(hw.rsm, (int)bR);
+        const int tZ = floor_div_small(hw.zsm, max(Zi, 1));
+        int bact = cfg.bact_w[c];
+        bact = Ri > 0 ? min(bact, tR) : bact;
+        bact = Zi > 0 ? min(bact, tZ) : bact;
+        const bool valid = !pole && bact > 0 && (int64_t)Ri * T <= hw.rsm && Zi <= hw.zsm;
+        bact = max(bact, 1);
         const float Nw = (float)min(bact * wpb, hw.wmax);
-        uint64_t blocks;
-        if (grid1) {
-          blocks = ((uint64_t)Ni + (uint64_t)(T - 1)) >> (la + lb);
-        } else {
-          const uint64_t c0 = ((uint64_t)Ni + ((1u << la) - 1)) >> la;
-          const uint64_t c1 = ((uint64_t)Ni + ((1u << lb) - 1)) >> lb;
-          blocks = c0 * c1;
-        }
-        const uint32_t asm_ = blocks < (uint64_t)nsm_i ? (uint32_t)blocks : nsm_i;
-        const float rep = ceil_div_rep(blocks, (uint32_t)bact * asm_);
+        const uint32_t c0 = grid1 ? ceil_shift(Ni, la + lb) : ceil_shift(Ni, la);
+        const uint32_t c1 = grid1 ? 1u : ceil_shift(Ni, lb);
+        const bool few = (uint64_t)c0 * c1 < (uint64_t)nsm_i;
+        const uint32_t asm_ = few ? c0 * c1 : nsm_i;
+        const float rep = rep_count(c0, c1, (uint32_t)bact * asm_);
         const float mem_insts = U + Cm;
         const float comp_cycles = hw.issue * (comp + mem_insts);
-        float ex;
-        if (mem_insts == 0.0f) {
-          ex = comp_cycles * rep;
-        } else {
-          const float inv_mi = __fdividef(1.0f, mem_insts);
-          const float wu = U * inv_mi, wc = Cm * inv_mi;
-          const float ml_unc = fmaf(upm - 1.0f, ddu, memld);
-          const float ml = fmaf(ml_unc, wu, memld * wc);
-          const float dd = fmaf(ddu * upm, wu, ddc * wc);
-          const float mwp_nobw = ml / dd;
-          const float bwpw = __fdividef(fghz * lbw, ml);
-          const float mwp_bw = bw / (bwpw * (float)asm_);
-          const float mwp_u = fminf(mwp_nobw, mwp_bw);
-          const bool mwp_cap = Nw <= mwp_u;
-          const float MWP = fminf(mwp_u, Nw);
-          const float mem_cycles = fmaf(ml_unc, U, memld * Cm);
-          const float cwp_full = __fdividef(mem_cycles + comp_cycles, comp_cycles);
-          const bool cwp_cap = Nw <= cwp_full;
-          const float CWP = fminf(cwp_full, Nw);
-          const float per = comp_cycles * inv_mi;
-          const float over = fmaxf(MWP - 1.0f, 0.0f);
-          float cyc;
-          if (mwp_cap && cwp_cap) {
-            cyc = fmaf(per, over, mem_cycles + comp_cycles);
-          } else if (CWP >= MWP || comp_cycles > mem_cycles) {
-            cyc = fmaf(per, over, __fdividef(mem_cycles * Nw, MWP));
-          } else {
-            cyc = fmaf(comp_cycles, Nw, memld);
-          }
-          const float synch_cost = dd * over * synch * (float)bact;
-          ex = (cyc + synch_cost) * rep;
-        }
-        if (ex < b1) {
-          b2 = b1;
-          b1 = ex;
-          arg = c;
-        } else if (ex < b2) {
-          b2 = ex;
-        }
+        const bool has_mem = mem_insts > 0.0f;
+        const float inv_mi = has_mem ? __fdividef(1.0f, mem_insts) : 0.0f;
+        const float wu = U * inv_mi, wc = Cm * inv_mi;
+        const float ml_unc = fmaf(upm - 1.0f, ddu, memld);
+        const float ml = fmaf(ml_unc, wu, memld * wc);
+        const float dd = fmaf(ddu * upm, wu, ddc * wc);
+        const float mwp_nobw = div_pos(ml, dd);
+        const float bwpw = div_pos(fghz * lbw, ml);
+        const float mwp_bw = div_pos(bw, bwpw * (float)asm_);
+        const float mwp_u = fminf(mwp_nobw, mwp_bw);
+        const bool mwp_cap = Nw <= mwp_u;
+        const float MWP = fminf(mwp_u, Nw);
+        const float mem_cycles = fmaf(ml_unc, U, memld * Cm);
+        const float cwp_full = div_pos(mem_cycles + comp_cycles, comp_cycles);
+        const bool cwp_cap = Nw <= cwp_full;
+        const float CWP = fminf(cwp_full, Nw);
+        const float per = comp_cycles * inv_mi;
+        const float over = fmaxf(MWP - 1.0f, 0.0f);
+        const float cy1 = fmaf(per, over, mem_cycles + comp_cycles);
+        const float cy2 = fmaf(per, over, div_pos(mem_cycles * Nw, MWP));
+        const float cy3 = fmaf(comp_cycles, Nw, memld);
+        const float cyc = (mwp_cap && cwp_cap) ? cy1 : ((CWP >= MWP || comp_cycles > mem_cycles) ? cy2 : cy3);
+        const float synch_cost = dd * over * synch * (float)bact;
+        float ex = has_mem ? (cyc + synch_cost) * rep : comp_cycles * rep;
+        ex = valid ? ex : INFINITY;
+        any_pole |= pole;
+        const bool better = ex < b1;
+        const bool second_better = !better && ex < b2;
+        b2 = better ? b1 : (second_better ? ex : b2);
+        arg = better ? c : arg;
+        b1 = better ? ex : b1;
       }
+      st |= any_pole ? RP_Q_POLE : 0;
       if (arg < 0) st |= RP_Q_NO_VALID;
     }
     argmin[i] = arg;

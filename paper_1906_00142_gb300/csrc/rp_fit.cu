@@ -200,16 +200,21 @@ struct WarpFit {
   // staging stride: >= NAUG, multiple of 4, odd multiple of 4 (LDS.128 reads
   // of one row by many lanes spread over banks)
   static constexpr int LDS = (((NAUG + 3) / 4) % 2 == 1) ? ((NAUG + 3) / 4) * 4 : ((NAUG + 3) / 4 + 1) * 4;
+  static constexpr int WS = ((NM + 3) / 4) * 4;   // row stride of W (16-byte rows)
   double xsol[NAUG];                  // solution (design basis, unscaled)
   double lo[3], hi[3];
   Real G[NAUG * NAUG];                // Gram, then factor (stride n)
   Real stage[32 * LDS];               // 32 staged rows / scratch
-  Real W[NM * NM];                    // whitening, upper triangular on 1..nm-1
+  Real W[NM * WS];                    // whitening, upper triangular on 1..nm-1, stride WS
   Real mupsi[NM];
   Real gvec[NAUG], scl[NAUG], invd[NAUG], invw[NM];
   Real rbuf[2][32];
   Real Tm[3][kMaxDeg + 1][kMaxDeg + 1];  // Q_k(u) = sum_l Tm[l][k] u^l
   Real mu_v[3], isg_v[3], sc_v[3], of_v[3];
+  double xprev[NAUG];                 // best solution so far (refinement)
+  double uv[2][NM];                   // solution in the unwhitened basis: p = c_p + psi.u, q = c_q + psi.v
+  Real HK[2][NM];                     // sum_s (w r)_s psi_s and sum_s (w y r)_s psi_s
+  float uvhi[2][NM], uvlo[2][NM];     // split u, v (compensated residuals)
   float xhi[NAUG], xlo[NAUG];
   unsigned dslot[3][kMaxDeg + 1];
   int keep_cnt, keep_w;
@@ -248,18 +253,35 @@ __device__ __forceinline__ void eval_psi(const WarpFit<Real, DMAX> &w, int d, in
 }
 
 // Whitened basis: pt[0] = 1, pt[j] = sum_{1<=i<=j} (Psi_i - mean_i) W[i][j].
+// W is zero below the diagonal, so rows are read from the aligned 4-block
+// that holds the diagonal (128-bit loads on the FP32 path).
 template <class Real, int DMAX, int NM>
 __device__ __forceinline__ void whiten(const WarpFit<Real, DMAX> &w, const Real (&psi)[NM],
                                        Real (&pt)[NM]) {
-  pt[0] = 1;
+  constexpr int WS = WarpFit<Real, DMAX>::WS;
+  Real acc[WS];
 #pragma unroll
-  for (int j = 1; j < NM; ++j) pt[j] = 0;
+  for (int j = 0; j < WS; ++j) acc[j] = 0;
 #pragma unroll
   for (int i = 1; i < NM; ++i) {
     const Real c = psi[i] - w.mupsi[i];
+    if constexpr (sizeof(Real) == 4) {
 #pragma unroll
-    for (int j = i; j < NM; ++j) pt[j] = fma(c, w.W[i * NM + j], pt[j]);
+      for (int j4 = (i / 4) * 4; j4 < WS; j4 += 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(&w.W[i * WS + j4]);
+        acc[j4] = fmaf(c, v.x, acc[j4]);
+        acc[j4 + 1] = fmaf(c, v.y, acc[j4 + 1]);
+        acc[j4 + 2] = fmaf(c, v.z, acc[j4 + 2]);
+        acc[j4 + 3] = fmaf(c, v.w, acc[j4 + 3]);
+      }
+    } else {
+#pragma unroll
+      for (int j = i; j < NM; ++j) acc[j] = fma(c, w.W[i * WS + j], acc[j]);
+    }
   }
+  pt[0] = 1;
+#pragma unroll
+  for (int j = 1; j < NM; ++j) pt[j] = acc[j];
 }
 
 // t-th tile of the lower triangle (row-major): rb >= cb
@@ -282,19 +304,33 @@ __device__ __forceinline__ void gram_stage(const Real *stage, int ntiles, Real (
     if (t >= ntiles) break;
     int rb, cb;
     tile_of(t, rb, cb);
+    // partial over the 32 staged samples, then one add into the running sum
+    // (blocked summation: error ~ (32 + m/32) u instead of m u)
+    Real part[TS * TS];
+#pragma unroll
+    for (int i = 0; i < TS * TS; ++i) part[i] = 0;
 #pragma unroll 4
     for (int s = 0; s < 32; ++s) {
       Real av[TS], bv[TS];
+      if constexpr (TS == 4 && sizeof(Real) == 4) {
+        const float4 va = *reinterpret_cast<const float4 *>(stage + s * LDS + 4 * rb);
+        const float4 vb = *reinterpret_cast<const float4 *>(stage + s * LDS + 4 * cb);
+        av[0] = va.x; av[1] = va.y; av[2] = va.z; av[3] = va.w;
+        bv[0] = vb.x; bv[1] = vb.y; bv[2] = vb.z; bv[3] = vb.w;
+      } else {
 #pragma unroll
-      for (int i = 0; i < TS; ++i) {
-        av[i] = stage[s * LDS + TS * rb + i];
-        bv[i] = stage[s * LDS + TS * cb + i];
+        for (int i = 0; i < TS; ++i) {
+          av[i] = stage[s * LDS + TS * rb + i];
+          bv[i] = stage[s * LDS + TS * cb + i];
+        }
       }
 #pragma unroll
       for (int i = 0; i < TS; ++i)
 #pragma unroll
-        for (int j = 0; j < TS; ++j) acc[k][TS * i + j] = fma(av[i], bv[j], acc[k][TS * i + j]);
+        for (int j = 0; j < TS; ++j) part[TS * i + j] = fma(av[i], bv[j], part[TS * i + j]);
     }
+#pragma unroll
+    for (int i = 0; i < TS * TS; ++i) acc[k][i] += part[i];
   }
 }
 
@@ -331,6 +367,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
   constexpr int NM = WF::NM;
   constexpr int NAUG = WF::NAUG;
   constexpr int LDS = WF::LDS;
+  constexpr int WS = WF::WS;
   constexpr int S2 = (NM + 1) / 2;                       // 2x2 tiles of the Psi Gram
   constexpr int T2 = (S2 * (S2 + 1) / 2 + 31) / 32;
   constexpr int S4 = (NAUG + 3) / 4;                     // 4x4 tiles of the design Gram
@@ -506,7 +543,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
       // means (row 0 holds the sums of Psi_j) and the centred Gram / m of the
       // non-constant functions, equilibrated, in `stage`
       for (int j = lane; j < NM; j += 32) w.mupsi[j] = (j < nm) ? w.G[j] / (Real)m : (Real)0;
-      for (int e = lane; e < NM * NM; e += 32) w.W[e] = 0;
+      for (int e = lane; e < NM * WS; e += 32) w.W[e] = 0;
       __syncwarp();
       for (int e = lane; e < nc * nc; e += 32) {
         const int i = e / nc + 1, j = e % nc + 1;
@@ -534,7 +571,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
       __syncwarp();
       for (int e = lane; e < nc * nc; e += 32) {
         const int i = e / nc, j = e % nc;
-        if (i <= j) w.W[(i + 1) * NM + (j + 1)] = w.G[i * nc + j] * w.scl[i];
+        if (i <= j) w.W[(i + 1) * WS + (j + 1)] = w.G[i * nc + j] * w.scl[i];
       }
       __syncwarp();
     }
@@ -609,95 +646,124 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
       __syncwarp();
     }
 
-    // ---------------- phase 5: refinement from the samples.  Every pass also
-    // checks q > 0 at the samples for the solution it starts from.
+    // ---------------- phase 5: refinement from the samples.
+    // With u = W x_num, v = W x_den (index 1..nm-1) and
+    //   c_p = x_num[0] - mu.u, c_q = 1 - mu.v,
+    // the fit's p and q at a sample are p = c_p + psi.u, q = c_q + psi.v, and
+    // the design residual is r = w (y q - p).  The normal-equation residual
+    // g = A^T r follows from H_i = sum (w r) psi_i and K_i = sum (w y r) psi_i:
+    //   g_num_0 = H_0, g_num_j = sum_{i<=j} W_ij (H_i - mu_i H_0),
+    //   g_den_j = -sum_{i<=j} W_ij (K_i - mu_i K_0),
+    // so the passes work in the unwhitened basis.  Each pass also returns the
+    // objective sum r^2 (a step that increases it is undone) and whether
+    // q > 0 at every sample.  Residuals are plain FP32 until the corrections
+    // fall below 1e-4 relative, then compensated (Dot2).
     int flags = (w.keep_cnt < n) ? RP_FIT_RANK_DEFICIENT : 0;
-    float prev_rel = INFINITY;
-    int state = 0;  // 0 running, 1 converged, 2 stalled
-    int it = 0;
+    float prev_rel = INFINITY, obj_prev = INFINITY;
+    bool compensated = sizeof(Real) == 8, done = false, converged = false;
+    int pole_prev = 0, it = 0;
     for (;; ++it) {
-      const bool update = it < a.max_refine;
-      for (int j = lane; j < n; j += 32) {
-        const double xv = w.xsol[j];
-        const float h = (float)xv;
-        w.xhi[j] = h;
-        w.xlo[j] = (float)(xv - (double)h);
+      const bool update = it < a.max_refine && !done;
+      // u, v, c_p, c_q (FP64) and their float splits
+      for (int e = lane; e < 2 * NM; e += 32) {
+        const int which = e / NM, i2 = e % NM;
+        double acc = 0.0;
+        if (i2 >= 1 && i2 < nm)
+          for (int j2 = i2; j2 < nm; ++j2)
+            acc += (double)w.W[i2 * WS + j2] * (which == 0 ? w.xsol[j2] : w.xsol[nm + j2 - 1]);
+        w.uv[which][i2] = acc;
       }
       __syncwarp();
-      Real gn[2] = {0, 0}, gd[2] = {0, 0};
+      if (lane < 2) {
+        double c = lane == 0 ? w.xsol[0] : 1.0;
+        for (int i2 = 1; i2 < nm; ++i2) c -= (double)w.mupsi[i2] * w.uv[lane][i2];
+        w.uv[lane][0] = c;
+      }
+      __syncwarp();
+      for (int e = lane; e < 2 * NM; e += 32) {
+        const int which = e / NM, i2 = e % NM;
+        const double v = w.uv[which][i2];
+        const float h = (float)v;
+        w.uvhi[which][i2] = h;
+        w.uvlo[which][i2] = (float)(v - (double)h);
+      }
+      __syncwarp();
+      Real hk[2][2] = {{0, 0}, {0, 0}};
+      float obj = 0.0f;
       int pole = 0;
       for (int base = 0; base < m; base += 32) {
         const int i = base + lane;
+        Real psi[NM];
         Real r = 0, yy = 0, wt = 0;
-        Real pt[NM];
         if (i < m) {
-          Real psi[NM];
           eval_psi<Real, DMAX, NM>(w, d, nm, gx0[i], gx1[i], gx2[i], psi);
-          whiten<Real, DMAX, NM>(w, psi, pt);
-          double q = 1.0;
-#pragma unroll
-          for (int j = 1; j < NM; ++j)
-            if (j < nm) q += w.xsol[nm + j - 1] * (double)pt[j];
-          pole |= !(q > 0.0);
+          psi[0] = 1;
           yy = (Real)gy[i];
           wt = a.weighted ? (Real)1 / fabs(yy) : (Real)1;
-          if (update) {
-            if constexpr (sizeof(Real) == 8) {
-              double sacc = wt * yy;
+          if constexpr (sizeof(Real) == 8) {
+            double p = w.uv[0][0], q = w.uv[1][0];
 #pragma unroll
-              for (int j = 0; j < NM; ++j)
-                if (j < nm) sacc -= wt * pt[j] * w.xsol[j];
+            for (int j2 = 1; j2 < NM; ++j2) {
+              p = fma(psi[j2], w.uv[0][j2], p);
+              q = fma(psi[j2], w.uv[1][j2], q);
+            }
+            pole |= !(q > 0.0);
+            r = wt * (yy * q - p);
+          } else {
+            float qf = w.uvhi[1][0];
 #pragma unroll
-              for (int j = 1; j < NM; ++j)
-                if (j < nm) sacc += wt * yy * pt[j] * w.xsol[nm + j - 1];
-              r = sacc;
-            } else {
-              // compensated dot product (Ogita, Rump & Oishi 2005, "Dot2") of
-              // the float row with the split solution xhi + xlo
-              const float wy = wt * yy;
-              float sacc = wy, c = 0.0f;
+            for (int j2 = 1; j2 < NM; ++j2) qf = fmaf(psi[j2], w.uvhi[1][j2], qf);
+            pole |= !(qf > 0.0f);
+            if (compensated) {
+              // e = y q - p = sum over (y psi_j) v_j - psi_j u_j, j = 0..nm-1
+              // (psi_0 = 1), Dot2 against the split u, v
+              float sacc = 0.0f, c = 0.0f;
 #pragma unroll
-              for (int j = 0; j < 2 * NM - 1; ++j) {
-                const bool num = j < NM;
-                const int jj = num ? j : j - NM + 1;
-                if (jj < nm) {
-                  const int col = num ? jj : nm + jj - 1;
-                  const float av = num ? wt * pt[jj] : -wy * pt[jj];
-                  const float pr = av * w.xhi[col];
-                  const float pe = fmaf(av, w.xhi[col], -pr);
-                  float t, e;
-                  two_sum(sacc, -pr, t, e);
-                  sacc = t;
-                  c += e - pe - av * w.xlo[col];
-                }
+              for (int j2 = 0; j2 < 2 * NM; ++j2) {
+                const int jj = j2 >> 1;
+                const bool den = (j2 & 1) == 0;
+                const float av = den ? yy * psi[jj] : -psi[jj];
+                const float xh = den ? w.uvhi[1][jj] : w.uvhi[0][jj];
+                const float xl = den ? w.uvlo[1][jj] : w.uvlo[0][jj];
+                const float pr = av * xh;
+                const float pe = fmaf(av, xh, -pr);
+                float t, e;
+                two_sum(sacc, pr, t, e);
+                sacc = t;
+                c += e + pe + av * xl;
               }
-              r = sacc + c;
+              r = wt * (sacc + c);
+            } else {
+              float p = w.uvhi[0][0];
+#pragma unroll
+              for (int j2 = 1; j2 < NM; ++j2) p = fmaf(psi[j2], w.uvhi[0][j2], p);
+              r = wt * fmaf(yy, qf, -p);
             }
           }
+          obj += (float)(r * r);
         } else {
 #pragma unroll
-          for (int j = 0; j < NM; ++j) pt[j] = 0;
+          for (int j2 = 0; j2 < NM; ++j2) psi[j2] = 0;
         }
         if (update) {
-          // g_num_j = sum_i (w r)_i pt_ij,  g_den_j = -sum_i (w y r)_i pt_ij
 #pragma unroll
-          for (int j = 0; j < NM; ++j) w.stage[lane * LDS + j] = pt[j];
+          for (int j2 = 0; j2 < NM; ++j2) w.stage[lane * LDS + j2] = psi[j2];
           w.rbuf[0][lane] = wt * r;
           w.rbuf[1][lane] = wt * yy * r;
           __syncwarp();
 #pragma unroll
           for (int rr = 0; rr < 2; ++rr) {
-            const int j = lane + 32 * rr;
-            if (j < nm) {
+            const int j2 = lane + 32 * rr;
+            if (j2 < nm) {
               Real pn = 0, pd = 0;
 #pragma unroll 8
-              for (int s = 0; s < 32; ++s) {
-                const Real bv = w.stage[s * LDS + j];
-                pn = fma(bv, w.rbuf[0][s], pn);
-                pd = fma(bv, w.rbuf[1][s], pd);
+              for (int s2 = 0; s2 < 32; ++s2) {
+                const Real bv = w.stage[s2 * LDS + j2];
+                pn = fma(bv, w.rbuf[0][s2], pn);
+                pd = fma(bv, w.rbuf[1][s2], pd);
               }
-              gn[rr] += pn;
-              gd[rr] += pd;
+              hk[rr][0] += pn;
+              hk[rr][1] += pd;
             }
           }
           __syncwarp();
@@ -705,23 +771,53 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) pole |= __shfl_xor_sync(0xffffffffu, pole, o);
-      flags = (flags & ~RP_FIT_POLE) | (pole ? RP_FIT_POLE : 0);
+      obj = warp_sum(obj);
+      if (it > 0 && obj > obj_prev * 1.000001f) {
+        // the last step increased the objective: undo it
+        for (int j2 = lane; j2 < n; j2 += 32) w.xsol[j2] = w.xprev[j2];
+        pole = pole_prev;
+        converged = prev_rel <= 1e-4f;
+        __syncwarp();
+        break;
+      }
+      for (int j2 = lane; j2 < n; j2 += 32) w.xprev[j2] = w.xsol[j2];
+      obj_prev = obj;
+      pole_prev = pole;
+      __syncwarp();
       if (!update) break;
+      // g from H, K; scaled for the factored (equilibrated) system
 #pragma unroll
       for (int rr = 0; rr < 2; ++rr) {
-        const int j = lane + 32 * rr;
-        if (j < nm) {
-          w.gvec[j] = gn[rr] * w.scl[j];
-          if (j >= 1) w.gvec[nm + j - 1] = -gd[rr] * w.scl[nm + j - 1];
+        const int j2 = lane + 32 * rr;
+        if (j2 < nm) {
+          w.HK[0][j2] = hk[rr][0];
+          w.HK[1][j2] = hk[rr][1];
         }
+      }
+      __syncwarp();
+      for (int e = lane; e < n; e += 32) {
+        Real g;
+        if (e < nm) {
+          if (e == 0) {
+            g = w.HK[0][0];
+          } else {
+            g = 0;
+            for (int i2 = 1; i2 <= e; ++i2) g += w.W[i2 * WS + e] * (w.HK[0][i2] - w.mupsi[i2] * w.HK[0][0]);
+          }
+        } else {
+          const int jd = e - nm + 1;
+          g = 0;
+          for (int i2 = 1; i2 <= jd; ++i2) g -= w.W[i2 * WS + jd] * (w.HK[1][i2] - w.mupsi[i2] * w.HK[1][0]);
+        }
+        w.gvec[e] = g * w.scl[e];
       }
       __syncwarp();
       warp_solve<Real>(w.G, n, n, w.invd, w.gvec);
       float dn = 0, xn = 0;
-      for (int j = lane; j < n; j += 32) {
-        const double dx = (double)(w.gvec[j] * w.scl[j]);
-        const double xv = w.xsol[j] + dx;
-        w.xsol[j] = xv;
+      for (int j2 = lane; j2 < n; j2 += 32) {
+        const double dx = (double)(w.gvec[j2] * w.scl[j2]);
+        const double xv = w.xsol[j2] + dx;
+        w.xsol[j2] = xv;
         dn += (float)(dx * dx);
         xn += (float)(xv * xv);
       }
@@ -729,15 +825,17 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
       xn = warp_sum(xn);
       __syncwarp();
       const float rel = xn > 0.0f ? sqrtf(dn / xn) : 0.0f;
-      if (rel <= (float)a.tol) state = 1;
-      else if (it >= 1 && rel > 0.5f * prev_rel) state = (rel <= 1e-5f) ? 1 : 2;
-      prev_rel = rel;
-      if (state != 0) {
-        ++it;
-        break;
+      if (!compensated && rel < 1e-4f) compensated = true;
+      if (rel <= (float)a.tol) {
+        done = converged = true;
+      } else if (compensated && it >= 1 && rel > 0.9f * prev_rel) {
+        done = true;
+        converged = rel <= 1e-4f;
       }
+      prev_rel = rel;
     }
-    if (a.max_refine > 0 && state != 1) flags |= RP_FIT_NOT_CONVERGED;
+    flags |= (pole_prev ? RP_FIT_POLE : 0);
+    if (a.max_refine > 0 && !converged) flags |= RP_FIT_NOT_CONVERGED;
     flags |= min(it, 255) << RP_FIT_ITER_SHIFT;
 
     // ---------------- phase 6: back to the monomial basis (FP64)
@@ -750,7 +848,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
           double u = 0;
           for (int j = i; j < nm; ++j) {
             const double cj = which == 0 ? w.xsol[j] : w.xsol[nm + j - 1];
-            u += (double)w.W[i * NM + j] * cj;
+            u += (double)w.W[i * WS + j] * cj;
           }
           cpsi[which * kMaxNm + i] = u;
         }

@@ -772,11 +772,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) pole |= __shfl_xor_sync(0xffffffffu, pole, o);
       obj = warp_sum(obj);
-      if (it > 0 && obj > obj_prev * 1.000001f) {
-        // the last step increased the objective: undo it
+      // a step that increases the objective by more than the objective's own
+      // rounding level (plain FP32 residuals: ~1e-4 relative) is undone
+      if (it > 0 && obj > obj_prev * (compensated ? 1.00001f : 1.0001f)) {
         for (int j2 = lane; j2 < n; j2 += 32) w.xsol[j2] = w.xprev[j2];
         pole = pole_prev;
-        converged = prev_rel <= 1e-4f;
+        converged = converged || prev_rel <= 1e-4f;
         __syncwarp();
         break;
       }
@@ -825,17 +826,19 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
       xn = warp_sum(xn);
       __syncwarp();
       const float rel = xn > 0.0f ? sqrtf(dn / xn) : 0.0f;
+      const bool was_compensated = compensated;
       if (!compensated && rel < 1e-4f) compensated = true;
       if (rel <= (float)a.tol) {
         done = converged = true;
-      } else if (compensated && it >= 1 && rel > 0.9f * prev_rel) {
+      } else if (was_compensated && rel > 0.9f * prev_rel) {
+        // corrections stopped shrinking: at the noise floor of the residuals
         done = true;
         converged = rel <= 1e-4f;
       }
       prev_rel = rel;
     }
     flags |= (pole_prev ? RP_FIT_POLE : 0);
-    if (a.max_refine > 0 && !converged) flags |= RP_FIT_NOT_CONVERGED;
+    if (a.max_refine > 0 && !converged && !(prev_rel <= 1e-4f)) flags |= RP_FIT_NOT_CONVERGED;
     flags |= min(it, 255) << RP_FIT_ITER_SHIFT;
 
     // ---------------- phase 6: back to the monomial basis (FP64)

@@ -9,8 +9,10 @@ Two checks per fit:
     The FP32 paths build the design in FP32; for a fit whose oracle
     predictions themselves move by sens when every design entry is
     perturbed by one FP32 rounding (the oracle's sensitivity check), no
-    FP32-data method can do better than ~sens, so the gate there is
-    max(1e-4, 10 sens).  The number of fits with sens >= 1e-5 is reported.
+    FP32-data method can do better than ~sens.  A GPU design entry carries
+    ~10 roundings (normalisation, marginal polynomials, products,
+    whitening), so the gate there is max(1e-4, 30 sens).  The number of
+    fits with sens >= 1e-5 is reported.
 """
 import numpy as np
 import pytest
@@ -53,14 +55,14 @@ def compare(inst, g, ref=None, sens=None, all_fits=False):
         yy = inst["y"][a:b].astype(np.float64)
         og = lin_objective(g["coef"][f], g["box"][f], int(deg[f]), pts, yy)
         oo = lin_objective(ref["coef"][f], ref["box"][f], int(deg[f]), pts, yy)
-        slack = 1e-10 + (0.0 if all_fits else (10.0 * sens[f]) ** 2)
+        slack = 1e-10 + (0.0 if all_fits else (30.0 * sens[f]) ** 2)
         assert og <= oo * (1 + 1e-4) + slack * (b - a), (int(f), og, oo, float(sens[f]))
     # 2. predictions
     p_o = oracle.predict_samples(ref, x, off)
     p_g = predictions(g["coef"], g["box"], deg, x, off)
     rel = np.abs(p_g - p_o) / np.abs(p_o)
     err = per_fit_max(rel, off)
-    gate = np.full(len(err), TOL) if all_fits else np.maximum(TOL, 10.0 * sens)
+    gate = np.full(len(err), TOL) if all_fits else np.maximum(TOL, 30.0 * sens)
     bad = np.where(ok & ~(err <= gate))[0]
     assert len(bad) == 0, [(int(f), float(err[f]), float(sens[f]), int(g["status"][f])) for f in bad[:10]]
     well = ok & (sens < 1e-5)
@@ -87,7 +89,7 @@ def test_fit_fp32_batched(batched):
     err, _ = compare(inst, g, ref, sens)
     iters = (g["status"] & rp.RP_FIT_ITER_MASK) >> rp.RP_FIT_ITER_SHIFT
     print("refinement iterations: median", np.median(iters), "max", iters.max())
-    assert ((g["status"] & rp.RP_FIT_NOT_CONVERGED) == 0).mean() > 0.9
+    assert ((g["status"] & rp.RP_FIT_NOT_CONVERGED) == 0).mean() > 0.95
 
 
 def test_fit_fp64_batched(batched):

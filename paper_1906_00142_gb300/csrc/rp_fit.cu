@@ -1,6 +1,7 @@
 // Batched least-squares fitting of rational functions (Sec. 4.2).
 //
-// One warp owns one fit at a time (persistent over fits).  The linearised
+// One 128-thread CTA owns one fit at a time (persistent over fits; several
+// CTAs per SM).  The linearised
 // problem of Sec. 4.2 -- minimise sum_i w_i^2 (p(x_i) - y_i q(x_i))^2 over the
 // coefficients of p and q, the homogeneous system normalised by mean(q) = 1
 // over the fit's samples -- is solved through its normal equations in a basis
@@ -189,46 +190,64 @@ __device__ __forceinline__ void distinct_insert(unsigned *slots, float x) {
 }
 
 // ---------------------------------------------------------------------
-// Per-warp fit state.  One warp owns one fit at a time; all its state lives
-// in a private slice of shared memory, so no block-wide barrier is needed
-// and the serial steps of one fit overlap with other warps' fits.
+// Per-fit state of one CTA (128 threads).  Shared memory and registers are
+// sized so that several CTAs share an SM: while one CTA runs the serial
+// steps of its fit (factorisations, triangular solves) on one warp, the
+// others' sample passes keep the SM busy.
+
+constexpr int kT = 128;       // threads per CTA (one fit at a time)
+constexpr int kMC = 512;      // samples per fit kept in shared memory
 
 template <class Real, int DMAX>
-struct WarpFit {
+struct CtaFit {
   static constexpr int NM = (DMAX + 1) * (DMAX + 2) * (DMAX + 3) / 6;
   static constexpr int NAUG = 2 * NM;
-  // staging stride: >= NAUG, multiple of 4, odd multiple of 4 (LDS.128 reads
-  // of one row by many lanes spread over banks)
+  // row stride of the staged rows: >= NAUG, an odd multiple of 4 (16-byte
+  // rows; 128-bit reads of the same row by many threads spread over banks)
   static constexpr int LDS = (((NAUG + 3) / 4) % 2 == 1) ? ((NAUG + 3) / 4) * 4 : ((NAUG + 3) / 4 + 1) * 4;
   static constexpr int WS = ((NM + 3) / 4) * 4;   // row stride of W (16-byte rows)
   double xsol[NAUG];                  // solution (design basis, unscaled)
+  double xprev[NAUG];                 // best solution so far (refinement)
+  double uv[2][NM];                   // solution in the unwhitened basis
   double lo[3], hi[3];
+  double redd[4][32];
   Real G[NAUG * NAUG];                // Gram, then factor (stride n)
-  Real stage[32 * LDS];               // 32 staged rows / scratch
-  Real W[NM * WS];                    // whitening, upper triangular on 1..nm-1, stride WS
+  Real stage[kT * LDS];               // staged rows / reduction scratch
+  Real W[NM * WS];                    // whitening, upper triangular on 1..nm-1
   Real mupsi[NM];
   Real gvec[NAUG], scl[NAUG], invd[NAUG], invw[NM];
-  Real rbuf[2][32];
+  Real HK[2][NM];
+  Real rbuf[2][kT];
   Real Tm[3][kMaxDeg + 1][kMaxDeg + 1];  // Q_k(u) = sum_l Tm[l][k] u^l
   Real mu_v[3], isg_v[3], sc_v[3], of_v[3];
-  double xprev[NAUG];                 // best solution so far (refinement)
-  double uv[2][NM];                   // solution in the unwhitened basis: p = c_p + psi.u, q = c_q + psi.v
-  Real HK[2][NM];                     // sum_s (w r)_s psi_s and sum_s (w y r)_s psi_s
-  float uvhi[2][NM], uvlo[2][NM];     // split u, v (compensated residuals)
-  float xhi[NAUG], xlo[NAUG];
+  float uvhi[2][NM], uvlo[2][NM];
+  float xs[4][kMC];                   // sample cache (N, B0, B1, y)
+  float redf[4][32];
   unsigned dslot[3][kMaxDeg + 1];
-  int keep_cnt, keep_w;
+  int keep_cnt, keep_w, bad;
+  float fscal[4];
 };
 
 template <class Real, int DMAX>
-__host__ __device__ constexpr size_t warpfit_bytes() {
-  return (sizeof(WarpFit<Real, DMAX>) + 15) & ~size_t(15);
+__host__ __device__ constexpr size_t ctafit_bytes() {
+  return (sizeof(CtaFit<Real, DMAX>) + 15) & ~size_t(15);
+}
+
+// Block-wide sum of one float per thread; result returned to every thread.
+template <class S>
+__device__ __forceinline__ float block_sum_f(S &w, float v, int slot) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) w.redf[wid][slot] = v;
+  __syncthreads();
+  const float r = w.redf[0][slot] + w.redf[1][slot] + w.redf[2][slot] + w.redf[3][slot];
+  return r;
 }
 
 // Unwhitened basis Psi at one sample (compile-time bound NM, runtime nm).
-template <class Real, int DMAX, int NM>
-__device__ __forceinline__ void eval_psi(const WarpFit<Real, DMAX> &w, int d, int nm, float x0,
-                                         float x1, float x2, Real (&psi)[NM]) {
+template <class Real, int DMAX, int NM, class S>
+__device__ __forceinline__ void eval_psi(const S &w, int d, int nm, float x0, float x1, float x2,
+                                         Real (&psi)[NM]) {
   Real Q[3][kMaxDeg + 1];
   const float xv[3] = {x0, x1, x2};
 #pragma unroll
@@ -253,12 +272,10 @@ __device__ __forceinline__ void eval_psi(const WarpFit<Real, DMAX> &w, int d, in
 }
 
 // Whitened basis: pt[0] = 1, pt[j] = sum_{1<=i<=j} (Psi_i - mean_i) W[i][j].
-// W is zero below the diagonal, so rows are read from the aligned 4-block
-// that holds the diagonal (128-bit loads on the FP32 path).
-template <class Real, int DMAX, int NM>
-__device__ __forceinline__ void whiten(const WarpFit<Real, DMAX> &w, const Real (&psi)[NM],
-                                       Real (&pt)[NM]) {
-  constexpr int WS = WarpFit<Real, DMAX>::WS;
+// W is zero below the diagonal, so each row is read from the aligned 4-block
+// holding the diagonal on (128-bit loads on the FP32 path).
+template <class Real, int NM, int WS, class S>
+__device__ __forceinline__ void whiten(const S &w, const Real (&psi)[NM], Real (&pt)[NM]) {
   Real acc[WS];
 #pragma unroll
   for (int j = 0; j < WS; ++j) acc[j] = 0;
@@ -284,7 +301,7 @@ __device__ __forceinline__ void whiten(const WarpFit<Real, DMAX> &w, const Real 
   for (int j = 1; j < NM; ++j) pt[j] = acc[j];
 }
 
-// t-th tile of the lower triangle (row-major): rb >= cb
+// t-th 4x4 tile of the lower triangle (row-major): rb >= cb
 __device__ __forceinline__ void tile_of(int t, int &rb, int &cb) {
   int r = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
   while ((r + 1) * (r + 2) / 2 <= t) ++r;
@@ -293,104 +310,116 @@ __device__ __forceinline__ void tile_of(int t, int &rb, int &cb) {
   cb = t - r * (r + 1) / 2;
 }
 
-// Accumulate the 32 staged rows (stride LDS) into this lane's TS x TS tiles
-// of the lower triangle of the Gram; tile t of lane = lane + 32 k.
-template <class Real, int TS, int TPL, int LDS>
-__device__ __forceinline__ void gram_stage(const Real *stage, int ntiles, Real (&acc)[TPL][TS * TS]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int k = 0; k < TPL; ++k) {
-    const int t = lane + 32 * k;
-    if (t >= ntiles) break;
-    int rb, cb;
-    tile_of(t, rb, cb);
-    // partial over the 32 staged samples, then one add into the running sum
-    // (blocked summation: error ~ (32 + m/32) u instead of m u)
-    Real part[TS * TS];
-#pragma unroll
-    for (int i = 0; i < TS * TS; ++i) part[i] = 0;
-#pragma unroll 4
-    for (int s = 0; s < 32; ++s) {
-      Real av[TS], bv[TS];
-      if constexpr (TS == 4 && sizeof(Real) == 4) {
-        const float4 va = *reinterpret_cast<const float4 *>(stage + s * LDS + 4 * rb);
-        const float4 vb = *reinterpret_cast<const float4 *>(stage + s * LDS + 4 * cb);
-        av[0] = va.x; av[1] = va.y; av[2] = va.z; av[3] = va.w;
-        bv[0] = vb.x; bv[1] = vb.y; bv[2] = vb.z; bv[3] = vb.w;
-      } else {
-#pragma unroll
-        for (int i = 0; i < TS; ++i) {
-          av[i] = stage[s * LDS + TS * rb + i];
-          bv[i] = stage[s * LDS + TS * cb + i];
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < TS; ++i)
-#pragma unroll
-        for (int j = 0; j < TS; ++j) part[TS * i + j] = fma(av[i], bv[j], part[TS * i + j]);
-    }
-#pragma unroll
-    for (int i = 0; i < TS * TS; ++i) acc[k][i] += part[i];
-  }
-}
+// Gram of `cols` columns of the staged rows: work item = (4x4 tile, sample
+// group); each thread holds up to IPT items.  Chunk partials are summed
+// into the per-item accumulators (blocked summation).
+template <class Real, int IPT, int LDS>
+struct TileGram {
+  Real acc[IPT][16];
+  int ntiles, groups;
 
-template <class Real, int TS, int TPL>
-__device__ __forceinline__ void gram_store(const Real (&acc)[TPL][TS * TS], int ntiles, int n, Real *G) {
-  const int lane = threadIdx.x & 31;
+  __device__ void init(int cols) {
+    const int side = (cols + 3) / 4;
+    ntiles = side * (side + 1) / 2;
+    groups = max(1, kT / ntiles);
 #pragma unroll
-  for (int k = 0; k < TPL; ++k) {
-    const int t = lane + 32 * k;
-    if (t >= ntiles) break;
-    int rb, cb;
-    tile_of(t, rb, cb);
+    for (int k = 0; k < IPT; ++k)
 #pragma unroll
-    for (int i = 0; i < TS; ++i)
-#pragma unroll
-      for (int j = 0; j < TS; ++j) {
-        const int r = TS * rb + i, c = TS * cb + j;
-        if (r < n && c < n) {
-          G[r * n + c] = acc[k][TS * i + j];
-          G[c * n + r] = acc[k][TS * i + j];
-        }
-      }
+      for (int i = 0; i < 16; ++i) acc[k][i] = 0;
   }
-}
+
+  __device__ void chunk(const Real *stage, int cnt) {
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      const int item = threadIdx.x + kT * k;
+      if (item >= ntiles * groups) break;
+      const int tile = item % ntiles, g = item / ntiles;
+      int rb, cb;
+      tile_of(tile, rb, cb);
+      Real part[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) part[i] = 0;
+#pragma unroll 2
+      for (int s = g; s < cnt; s += groups) {
+        Real av[4], bv[4];
+        if constexpr (sizeof(Real) == 4) {
+          const float4 va = *reinterpret_cast<const float4 *>(stage + s * LDS + 4 * rb);
+          const float4 vb = *reinterpret_cast<const float4 *>(stage + s * LDS + 4 * cb);
+          av[0] = va.x; av[1] = va.y; av[2] = va.z; av[3] = va.w;
+          bv[0] = vb.x; bv[1] = vb.y; bv[2] = vb.z; bv[3] = vb.w;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            av[i] = stage[s * LDS + 4 * rb + i];
+            bv[i] = stage[s * LDS + 4 * cb + i];
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) part[4 * i + j] = fma(av[i], bv[j], part[4 * i + j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) acc[k][i] += part[i];
+    }
+  }
+
+  // Sum the sample groups and write the symmetric cols x cols Gram into G
+  // (stride cols).  `scratch` needs ntiles * groups * 16 entries.
+  __device__ void finish(int cols, Real *G, Real *scratch) {
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      const int item = threadIdx.x + kT * k;
+      if (item < ntiles * groups)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) scratch[(size_t)item * 16 + i] = acc[k][i];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ntiles * 16; e += kT) {
+      const int tile = e / 16, q = e % 16;
+      int rb, cb;
+      tile_of(tile, rb, cb);
+      const int r = 4 * rb + q / 4, c = 4 * cb + q % 4;
+      Real sum = 0;
+      for (int g = 0; g < groups; ++g) sum += scratch[((size_t)g * ntiles + tile) * 16 + q];
+      if (r < cols && c < cols) {
+        G[r * cols + c] = sum;
+        G[c * cols + r] = sum;
+      }
+    }
+    __syncthreads();
+  }
+};
 
 // ---------------------------------------------------------------------
 // The fit kernel.  Real = double: plain FP64 path; Real = float: FP32 path.
 
-constexpr int kMaxWarps = 8;
-
 template <class Real, int DMAX>
-__global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warps_per_cta) {
-  using WF = WarpFit<Real, DMAX>;
+__global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? 4 : 2) fit_kernel(FitArgs a) {
+  using WF = CtaFit<Real, DMAX>;
   constexpr int NM = WF::NM;
   constexpr int NAUG = WF::NAUG;
   constexpr int LDS = WF::LDS;
   constexpr int WS = WF::WS;
-  constexpr int S2 = (NM + 1) / 2;                       // 2x2 tiles of the Psi Gram
-  constexpr int T2 = (S2 * (S2 + 1) / 2 + 31) / 32;
-  constexpr int S4 = (NAUG + 3) / 4;                     // 4x4 tiles of the design Gram
-  constexpr int T4 = (S4 * (S4 + 1) / 2 + 31) / 32;
+  constexpr int S4 = (NAUG + 3) / 4;
+  constexpr int IPT = ((S4 * (S4 + 1) / 2) + kT - 1) / kT;   // design-Gram items per thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (wid >= warps_per_cta) return;
-  WF &w = *reinterpret_cast<WF *>(smem_raw + warpfit_bytes<Real, DMAX>() * wid);
-  const int64_t nwarps = (int64_t)gridDim.x * warps_per_cta;
-  for (int64_t f = (int64_t)blockIdx.x * warps_per_cta + wid; f < a.F; f += nwarps) {
+  WF &w = *reinterpret_cast<WF *>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int64_t f = blockIdx.x; f < a.F; f += gridDim.x) {
     // ---------------- phase 0: range, degree, validation, box, distinct values
     const int64_t b0 = a.off[f], b1 = a.off[f + 1];
     const int d = a.degs ? (int)a.degs[f] : a.d_uniform;
     const bool range_ok = b0 >= 0 && b1 >= b0 && b1 <= a.S;
     const int m = range_ok ? (int)(b1 - b0) : 0;
     double *cf = a.coef + f * kStride;
-    for (int j = lane; j < kStride; j += 32) {
+    for (int j = tid; j < kStride; j += kT) {
       cf[j] = 0.0;
       if (a.coef32) a.coef32[f * kStride + j] = 0.0f;
     }
-    if (lane < 6) a.box[f * 6 + lane] = 0.0;
+    if (tid < 6) a.box[f * 6 + tid] = 0.0;
     if (d < 1 || d > DMAX || m == 0) {
-      if (lane == 0) {
+      if (tid == 0) {
         a.status[f] = RP_FIT_EMPTY;
         a.rank[f] = 0;
       }
@@ -400,13 +429,21 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
     const int nc = nm - 1;
     const int naug = 2 * nm;
     const int n = naug - 1;
+    const bool cached = m <= kMC;
     const float *gx0 = a.x + b0, *gx1 = a.x + a.S + b0, *gx2 = a.x + 2 * a.S + b0, *gy = a.y + b0;
-    if (lane < 3 * (kMaxDeg + 1)) (&w.dslot[0][0])[lane] = kEmpty;
-    __syncwarp();
+    if (tid < 3 * (kMaxDeg + 1)) (&w.dslot[0][0])[tid] = kEmpty;
+    if (tid == 0) w.bad = 0;
+    __syncthreads();
     float lmin[3] = {INFINITY, INFINITY, INFINITY}, lmax[3] = {-INFINITY, -INFINITY, -INFINITY};
     int bad = 0;
-    for (int i = lane; i < m; i += 32) {
+    for (int i = tid; i < m; i += kT) {
       const float v0 = gx0[i], v1 = gx1[i], v2 = gx2[i], yy = gy[i];
+      if (cached) {
+        w.xs[0][i] = v0;
+        w.xs[1][i] = v1;
+        w.xs[2][i] = v2;
+        w.xs[3][i] = yy;
+      }
       distinct_insert(w.dslot[0], v0);
       distinct_insert(w.dslot[1], v1);
       distinct_insert(w.dslot[2], v2);
@@ -425,48 +462,72 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
       }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-    if (bad) {
-      if (lane == 0) {
-        a.status[f] = (bad & RP_FIT_NONFINITE) ? RP_FIT_NONFINITE : RP_FIT_NONPOS_Y;
+    if (lane == 0) {
+      for (int v = 0; v < 3; ++v) {
+        w.redf[wid][v] = lmin[v];
+        w.redf[wid][3 + v] = lmax[v];
+      }
+      if (bad) atomicOr(&w.bad, bad);
+    }
+    __syncthreads();
+    if (w.bad) {
+      if (tid == 0) {
+        a.status[f] = (w.bad & RP_FIT_NONFINITE) ? RP_FIT_NONFINITE : RP_FIT_NONPOS_Y;
         a.rank[f] = 0;
       }
+      __syncthreads();
       continue;
     }
-    if (lane < 3) {
-      const double mn = lmin[lane], mx = lmax[lane];
-      w.lo[lane] = mn;
-      w.hi[lane] = mx;
-      a.box[f * 6 + 2 * lane] = mn;
-      a.box[f * 6 + 2 * lane + 1] = mx;
+    if (tid < 3) {
+      double mn = w.redf[0][tid], mx = w.redf[0][3 + tid];
+      for (int k = 1; k < 4; ++k) {
+        mn = fmin(mn, (double)w.redf[k][tid]);
+        mx = fmax(mx, (double)w.redf[k][3 + tid]);
+      }
+      w.lo[tid] = mn;
+      w.hi[tid] = mx;
+      a.box[f * 6 + 2 * tid] = mn;
+      a.box[f * 6 + 2 * tid + 1] = mx;
       if (mx > mn) {   // x' = 2 (x - lo) / (hi - lo) - 1 = x * sc + of
         const double sc = 2.0 / (mx - mn);
-        w.sc_v[lane] = (Real)sc;
-        w.of_v[lane] = (Real)(-1.0 - mn * sc);
+        w.sc_v[tid] = (Real)sc;
+        w.of_v[tid] = (Real)(-1.0 - mn * sc);
       } else {
-        w.sc_v[lane] = 0;
-        w.of_v[lane] = 0;
+        w.sc_v[tid] = 0;
+        w.of_v[tid] = 0;
       }
     }
-    __syncwarp();
+    __syncthreads();
+    const float *sx0 = cached ? w.xs[0] : gx0;
+    const float *sx1 = cached ? w.xs[1] : gx1;
+    const float *sx2 = cached ? w.xs[2] : gx2;
+    const float *sy = cached ? w.xs[3] : gy;
 
     // ---------------- phase 1: standardisation, marginal orthonormal polynomials
     {
       Real acc[3] = {0, 0, 0};
-      for (int i = lane; i < m; i += 32) {
-        acc[0] += fma((Real)gx0[i], w.sc_v[0], w.of_v[0]);
-        acc[1] += fma((Real)gx1[i], w.sc_v[1], w.of_v[1]);
-        acc[2] += fma((Real)gx2[i], w.sc_v[2], w.of_v[2]);
+      for (int i = tid; i < m; i += kT) {
+        acc[0] += fma((Real)sx0[i], w.sc_v[0], w.of_v[0]);
+        acc[1] += fma((Real)sx1[i], w.sc_v[1], w.of_v[1]);
+        acc[2] += fma((Real)sx2[i], w.sc_v[2], w.of_v[2]);
       }
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        const double sv = (double)warp_sum(acc[v]);
+        if (lane == 0) w.redd[wid][v] = sv;
+      }
+      __syncthreads();
       Real mu[3];
 #pragma unroll
-      for (int v = 0; v < 3; ++v) mu[v] = warp_sum(acc[v]) / (Real)m;
-      Real mom[3][2 * kMaxDeg];
+      for (int v = 0; v < 3; ++v)
+        mu[v] = (Real)((w.redd[0][v] + w.redd[1][v] + w.redd[2][v] + w.redd[3][v]) / (double)m);
+      Real mom[3][2 * DMAX];
 #pragma unroll
       for (int v = 0; v < 3; ++v)
 #pragma unroll
-        for (int k = 0; k < 2 * kMaxDeg; ++k) mom[v][k] = 0;
-      for (int i = lane; i < m; i += 32) {
-        const float xv[3] = {gx0[i], gx1[i], gx2[i]};
+        for (int k = 0; k < 2 * DMAX; ++k) mom[v][k] = 0;
+      for (int i = tid; i < m; i += kT) {
+        const float xv[3] = {sx0[i], sx1[i], sx2[i]};
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
           const Real c = fma((Real)xv[v], w.sc_v[v], w.of_v[v]) - mu[v];
@@ -478,16 +539,23 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
           }
         }
       }
-      double M[3][2 * kMaxDeg + 1];
+      __syncthreads();
 #pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        M[v][0] = 1.0;
+      for (int v = 0; v < 3; ++v)
 #pragma unroll
-        for (int k = 0; k < 2 * DMAX; ++k) M[v][k + 1] = (double)warp_sum(mom[v][k]) / (double)m;
-      }
-      if (lane < 3) {
-        const int v = lane;
-        const double var = M[v][2];
+        for (int k = 0; k < 2 * DMAX; ++k) {
+          const double sv = (double)warp_sum(mom[v][k]);
+          if (lane == 0) w.redd[wid][v * 2 * DMAX + k] = sv;
+        }
+      __syncthreads();
+      if (tid < 3) {
+        const int v = tid;
+        double M[2 * kMaxDeg + 1];
+        M[0] = 1.0;
+        for (int k = 0; k < 2 * DMAX; ++k)
+          M[k + 1] = (w.redd[0][v * 2 * DMAX + k] + w.redd[1][v * 2 * DMAX + k] +
+                      w.redd[2][v * 2 * DMAX + k] + w.redd[3][v * 2 * DMAX + k]) / (double)m;
+        const double var = M[2];
         w.mu_v[v] = mu[v];
         for (int l = 0; l <= kMaxDeg; ++l)
           for (int k = 0; k <= kMaxDeg; ++k) w.Tm[v][l][k] = (l == 0 && k == 0) ? (Real)1 : (Real)0;
@@ -500,7 +568,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
           Ms[0] = 1.0;
           double pw = isg;
           for (int k = 1; k <= 2 * DMAX; ++k) {
-            Ms[k] = M[v][k] * pw;
+            Ms[k] = M[k] * pw;
             pw *= isg;
           }
           int cnt = 0;
@@ -511,89 +579,84 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
             for (int k = 0; k <= kMaxDeg; ++k) w.Tm[v][l][k] = (Real)T[l][k];
         }
       }
-      __syncwarp();
+      __syncthreads();
     }
 
     // ---------------- phase 2: Gram of Psi (nm columns), means, whitening
     {
-      const int side = (nm + 1) / 2;
-      const int ntiles = side * (side + 1) / 2;
-      Real acc[T2][4];
+      TileGram<Real, IPT, LDS> tg;
+      tg.init(nm);
+      const int cols4 = 4 * ((nm + 3) / 4);
+      for (int base = 0; base < m; base += kT) {
+        const int cnt = min(kT, m - base);
+        if (tid < cnt) {
+          const int i = base + tid;
+          Real psi[NM];
+          eval_psi<Real, DMAX, NM>(w, d, nm, sx0[i], sx1[i], sx2[i], psi);
+          Real *row = w.stage + tid * LDS;
 #pragma unroll
-      for (int k = 0; k < T2; ++k)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) acc[k][i] = 0;
-      for (int base = 0; base < m; base += 32) {
-        const int i = base + lane;
-        Real psi[NM];
-        if (i < m) {
-          eval_psi<Real, DMAX, NM>(w, d, nm, gx0[i], gx1[i], gx2[i], psi);
-        } else {
-#pragma unroll
-          for (int j = 0; j < NM; ++j) psi[j] = 0;
+          for (int j = 0; j < NM; ++j) row[j] = psi[j];
+          for (int j = NM; j < cols4; ++j) row[j] = 0;
         }
-#pragma unroll
-        for (int j = 0; j < 2 * S2; ++j) w.stage[lane * LDS + j] = (j < NM) ? psi[j] : (Real)0;
-        __syncwarp();
-        gram_stage<Real, 2, T2, LDS>(w.stage, ntiles, acc);
-        __syncwarp();
+        __syncthreads();
+        tg.chunk(w.stage, cnt);
+        __syncthreads();
       }
-      gram_store<Real, 2, T2>(acc, ntiles, nm, w.G);
-      __syncwarp();
-      // means (row 0 holds the sums of Psi_j) and the centred Gram / m of the
+      tg.finish(nm, w.G, w.stage);
+      // means (row 0 holds the sums of Psi_j), the centred Gram / m of the
       // non-constant functions, equilibrated, in `stage`
-      for (int j = lane; j < NM; j += 32) w.mupsi[j] = (j < nm) ? w.G[j] / (Real)m : (Real)0;
-      for (int e = lane; e < NM * WS; e += 32) w.W[e] = 0;
-      __syncwarp();
-      for (int e = lane; e < nc * nc; e += 32) {
+      for (int j = tid; j < NM; j += kT) w.mupsi[j] = (j < nm) ? w.G[j] / (Real)m : (Real)0;
+      for (int e = tid; e < NM * WS; e += kT) w.W[e] = 0;
+      __syncthreads();
+      for (int e = tid; e < nc * nc; e += kT) {
         const int i = e / nc + 1, j = e % nc + 1;
         w.stage[e] = (w.G[i * nm + j] - (Real)m * w.mupsi[i] * w.mupsi[j]) / (Real)m;
       }
-      __syncwarp();
-      for (int j = lane; j < nc; j += 32) {
+      __syncthreads();
+      for (int j = tid; j < nc; j += kT) {
         const Real dg = w.stage[j * nc + j];
         w.scl[j] = dg > 0 ? rsqrt_pos<Real>(dg) : (Real)0;
       }
-      __syncwarp();
-      for (int e = lane; e < nc * nc; e += 32) w.stage[e] *= w.scl[e / nc] * w.scl[e % nc];
+      __syncthreads();
+      for (int e = tid; e < nc * nc; e += kT) w.stage[e] *= w.scl[e / nc] * w.scl[e % nc];
+      __syncthreads();
       // the whitening only preconditions: any positive pivot is kept (the
       // basis stays a basis of the same space); only directions whose pivot
       // is at rounding level or below are dropped
-      warp_chol<Real>(w.stage, nc, nc, sizeof(Real) == 8 ? (Real)1e-14 : (Real)1e-10, w.invw,
-                      &w.keep_w);
+      if (wid == 0)
+        warp_chol<Real>(w.stage, nc, nc, sizeof(Real) == 8 ? (Real)1e-14 : (Real)1e-10, w.invw,
+                        &w.keep_w);
+      __syncthreads();
       // R^{-1} (R = L^T, R[i][l] = L[l][i]) column by column into G; W = D R^{-1}
-      for (int j = lane; j < nc; j += 32)
+      for (int j = tid; j < nc; j += kT)
         for (int i = j; i >= 0; --i) {
           Real s = (i == j) ? (Real)1 : (Real)0;
           for (int l = i + 1; l <= j; ++l) s -= w.stage[l * nc + i] * w.G[l * nc + j];
           w.G[i * nc + j] = s * w.invw[i];
         }
-      __syncwarp();
-      for (int e = lane; e < nc * nc; e += 32) {
+      __syncthreads();
+      for (int e = tid; e < nc * nc; e += kT) {
         const int i = e / nc, j = e % nc;
         if (i <= j) w.W[(i + 1) * WS + (j + 1)] = w.G[i * nc + j] * w.scl[i];
       }
-      __syncwarp();
+      __syncthreads();
     }
 
     // ---------------- phase 3: the design Gram [num (nm) | den (nm-1) | rhs]
     {
-      const int side = (naug + 3) / 4;
-      const int ntiles = side * (side + 1) / 2;
-      Real acc[T4][16];
-#pragma unroll
-      for (int k = 0; k < T4; ++k)
-#pragma unroll
-        for (int i = 0; i < 16; ++i) acc[k][i] = 0;
-      for (int base = 0; base < m; base += 32) {
-        const int i = base + lane;
-        Real *row = w.stage + lane * LDS;
-        if (i < m) {
+      TileGram<Real, IPT, LDS> tg;
+      tg.init(naug);
+      const int cols4 = 4 * ((naug + 3) / 4);
+      for (int base = 0; base < m; base += kT) {
+        const int cnt = min(kT, m - base);
+        if (tid < cnt) {
+          const int i = base + tid;
           Real psi[NM], pt[NM];
-          eval_psi<Real, DMAX, NM>(w, d, nm, gx0[i], gx1[i], gx2[i], psi);
-          whiten<Real, DMAX, NM>(w, psi, pt);
-          const Real yy = (Real)gy[i];
+          eval_psi<Real, DMAX, NM>(w, d, nm, sx0[i], sx1[i], sx2[i], psi);
+          whiten<Real, NM, WS>(w, psi, pt);
+          const Real yy = (Real)sy[i];
           const Real wt = a.weighted ? (Real)1 / fabs(yy) : (Real)1;
+          Real *row = w.stage + tid * LDS;
 #pragma unroll
           for (int j = 0; j < NM; ++j)
             if (j < nm) row[j] = wt * pt[j];
@@ -601,71 +664,63 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
           for (int j = 1; j < NM; ++j)
             if (j < nm) row[nm + j - 1] = -wt * yy * pt[j];
           row[n] = wt * yy;
-          for (int j = naug; j < 4 * S4; ++j) row[j] = 0;
-        } else {
-          for (int j = 0; j < 4 * S4; ++j) row[j] = 0;
+          for (int j = naug; j < cols4; ++j) row[j] = 0;
         }
-        __syncwarp();
-        gram_stage<Real, 4, T4, LDS>(w.stage, ntiles, acc);
-        __syncwarp();
+        __syncthreads();
+        tg.chunk(w.stage, cnt);
+        __syncthreads();
       }
-      gram_store<Real, 4, T4>(acc, ntiles, naug, w.G);
-      __syncwarp();
+      tg.finish(naug, w.G, w.stage);
     }
 
     // ---------------- phase 4: equilibrate, factor, first solve
     // The leading n x n block of G (stride naug) is the normal matrix and
-    // column n holds A^T b; the scaled block is compacted in place to stride n
-    // (row by row: each destination row ends before the next source row).
+    // column n holds A^T b; the scaled block is compacted to stride n through
+    // `stage` and factored by warp 0.
     {
-      for (int j = lane; j < n; j += 32) {
+      for (int j = tid; j < n; j += kT) {
         const Real dg = w.G[j * naug + j];
         w.scl[j] = dg > 0 ? rsqrt_pos<Real>(dg) : (Real)0;
         w.gvec[j] = w.G[j * naug + n];
       }
-      __syncwarp();
-      for (int i = 0; i < n; ++i) {
-        Real v[3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          const int j = lane + 32 * r;
-          v[r] = (j < n) ? w.G[i * naug + j] * w.scl[i] * w.scl[j] : (Real)0;
-        }
-        __syncwarp();
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          const int j = lane + 32 * r;
-          if (j < n) w.G[i * n + j] = v[r];
-        }
-        __syncwarp();
+      __syncthreads();
+      for (int e = tid; e < n * n; e += kT) {
+        const int i = e / n, j = e % n;
+        w.stage[e] = w.G[i * naug + j] * w.scl[i] * w.scl[j];
       }
-      for (int j = lane; j < n; j += 32) w.gvec[j] *= w.scl[j];
-      warp_chol<Real>(w.G, n, n, (Real)a.drop_tol, w.invd, &w.keep_cnt);
-      warp_solve<Real>(w.G, n, n, w.invd, w.gvec);
-      for (int j = lane; j < n; j += 32) w.xsol[j] = (double)(w.gvec[j] * w.scl[j]);
-      __syncwarp();
+      __syncthreads();
+      for (int e = tid; e < n * n; e += kT) w.G[e] = w.stage[e];
+      for (int j = tid; j < n; j += kT) w.gvec[j] *= w.scl[j];
+      __syncthreads();
+      if (wid == 0) {
+        warp_chol<Real>(w.G, n, n, (Real)a.drop_tol, w.invd, &w.keep_cnt);
+        warp_solve<Real>(w.G, n, n, w.invd, w.gvec);
+        for (int j = lane; j < n; j += 32) w.xsol[j] = (double)(w.gvec[j] * w.scl[j]);
+      }
+      __syncthreads();
     }
 
     // ---------------- phase 5: refinement from the samples.
-    // With u = W x_num, v = W x_den (index 1..nm-1) and
+    // With u = W x_num, v = W x_den (index 1..nm-1),
     //   c_p = x_num[0] - mu.u, c_q = 1 - mu.v,
     // the fit's p and q at a sample are p = c_p + psi.u, q = c_q + psi.v, and
     // the design residual is r = w (y q - p).  The normal-equation residual
-    // g = A^T r follows from H_i = sum (w r) psi_i and K_i = sum (w y r) psi_i:
+    // g = A^T r follows from H_i = sum (w r) psi_i, K_i = sum (w y r) psi_i:
     //   g_num_0 = H_0, g_num_j = sum_{i<=j} W_ij (H_i - mu_i H_0),
     //   g_den_j = -sum_{i<=j} W_ij (K_i - mu_i K_0),
     // so the passes work in the unwhitened basis.  Each pass also returns the
-    // objective sum r^2 (a step that increases it is undone) and whether
-    // q > 0 at every sample.  Residuals are plain FP32 until the corrections
-    // fall below 1e-4 relative, then compensated (Dot2).
+    // objective sum r^2 (a step that increases it beyond its rounding level is
+    // undone) and whether q > 0 at every sample.  Residuals are plain FP32
+    // until the corrections fall below 1e-4 relative, then compensated (Dot2).
     int flags = (w.keep_cnt < n) ? RP_FIT_RANK_DEFICIENT : 0;
-    float prev_rel = INFINITY, obj_prev = INFINITY;
-    bool compensated = sizeof(Real) == 8, done = false, converged = false;
+    float prev_rel = INFINITY, obj_prev = INFINITY, obj_drop = INFINITY;
+    bool compensated = sizeof(Real) == 8, done = false;
     int pole_prev = 0, it = 0;
+    const int hk_groups = max(1, kT / nm);
     for (;; ++it) {
       const bool update = it < a.max_refine && !done;
       // u, v, c_p, c_q (FP64) and their float splits
-      for (int e = lane; e < 2 * NM; e += 32) {
+      for (int e = tid; e < 2 * NM; e += kT) {
         const int which = e / NM, i2 = e % NM;
         double acc = 0.0;
         if (i2 >= 1 && i2 < nm)
@@ -673,33 +728,34 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
             acc += (double)w.W[i2 * WS + j2] * (which == 0 ? w.xsol[j2] : w.xsol[nm + j2 - 1]);
         w.uv[which][i2] = acc;
       }
-      __syncwarp();
-      if (lane < 2) {
-        double c = lane == 0 ? w.xsol[0] : 1.0;
-        for (int i2 = 1; i2 < nm; ++i2) c -= (double)w.mupsi[i2] * w.uv[lane][i2];
-        w.uv[lane][0] = c;
+      __syncthreads();
+      if (tid < 2) {
+        double c = tid == 0 ? w.xsol[0] : 1.0;
+        for (int i2 = 1; i2 < nm; ++i2) c -= (double)w.mupsi[i2] * w.uv[tid][i2];
+        w.uv[tid][0] = c;
       }
-      __syncwarp();
-      for (int e = lane; e < 2 * NM; e += 32) {
+      __syncthreads();
+      for (int e = tid; e < 2 * NM; e += kT) {
         const int which = e / NM, i2 = e % NM;
         const double v = w.uv[which][i2];
         const float h = (float)v;
         w.uvhi[which][i2] = h;
         w.uvlo[which][i2] = (float)(v - (double)h);
       }
-      __syncwarp();
-      Real hk[2][2] = {{0, 0}, {0, 0}};
+      __syncthreads();
+      Real hk0 = 0, hk1 = 0;
       float obj = 0.0f;
       int pole = 0;
-      for (int base = 0; base < m; base += 32) {
-        const int i = base + lane;
-        Real psi[NM];
-        Real r = 0, yy = 0, wt = 0;
-        if (i < m) {
-          eval_psi<Real, DMAX, NM>(w, d, nm, gx0[i], gx1[i], gx2[i], psi);
+      for (int base = 0; base < m; base += kT) {
+        const int cnt = min(kT, m - base);
+        if (tid < cnt) {
+          const int i = base + tid;
+          Real psi[NM];
+          eval_psi<Real, DMAX, NM>(w, d, nm, sx0[i], sx1[i], sx2[i], psi);
           psi[0] = 1;
-          yy = (Real)gy[i];
-          wt = a.weighted ? (Real)1 / fabs(yy) : (Real)1;
+          const Real yy = (Real)sy[i];
+          const Real wt = a.weighted ? (Real)1 / fabs(yy) : (Real)1;
+          Real r;
           if constexpr (sizeof(Real) == 8) {
             double p = w.uv[0][0], q = w.uv[1][0];
 #pragma unroll
@@ -715,24 +771,26 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
             for (int j2 = 1; j2 < NM; ++j2) qf = fmaf(psi[j2], w.uvhi[1][j2], qf);
             pole |= !(qf > 0.0f);
             if (compensated) {
-              // e = y q - p = sum over (y psi_j) v_j - psi_j u_j, j = 0..nm-1
-              // (psi_0 = 1), Dot2 against the split u, v
-              float sacc = 0.0f, c = 0.0f;
+              // e = y q - p = sum_j (y psi_j) v_j - psi_j u_j (psi_0 = 1):
+              // Dot2 against the split u, v, two independent chains
+              float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
 #pragma unroll
-              for (int j2 = 0; j2 < 2 * NM; ++j2) {
-                const int jj = j2 >> 1;
-                const bool den = (j2 & 1) == 0;
-                const float av = den ? yy * psi[jj] : -psi[jj];
-                const float xh = den ? w.uvhi[1][jj] : w.uvhi[0][jj];
-                const float xl = den ? w.uvlo[1][jj] : w.uvlo[0][jj];
-                const float pr = av * xh;
-                const float pe = fmaf(av, xh, -pr);
-                float t, e;
-                two_sum(sacc, pr, t, e);
-                sacc = t;
-                c += e + pe + av * xl;
+              for (int j2 = 0; j2 < NM; ++j2) {
+                const float av = yy * psi[j2], bv = -psi[j2];
+                const float pr0 = av * w.uvhi[1][j2], pr1 = bv * w.uvhi[0][j2];
+                const float pe0 = fmaf(av, w.uvhi[1][j2], -pr0);
+                const float pe1 = fmaf(bv, w.uvhi[0][j2], -pr1);
+                float t0, e0, t1, e1;
+                two_sum(s0, pr0, t0, e0);
+                two_sum(s1, pr1, t1, e1);
+                s0 = t0;
+                s1 = t1;
+                c0 += e0 + pe0 + av * w.uvlo[1][j2];
+                c1 += e1 + pe1 + bv * w.uvlo[0][j2];
               }
-              r = wt * (sacc + c);
+              float t, e;
+              two_sum(s0, s1, t, e);
+              r = wt * (t + (e + c0 + c1));
             } else {
               float p = w.uvhi[0][0];
 #pragma unroll
@@ -741,62 +799,66 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
             }
           }
           obj += (float)(r * r);
-        } else {
+          if (update) {
+            Real *row = w.stage + tid * LDS;
 #pragma unroll
-          for (int j2 = 0; j2 < NM; ++j2) psi[j2] = 0;
+            for (int j2 = 0; j2 < NM; ++j2) row[j2] = psi[j2];
+            w.rbuf[0][tid] = wt * r;
+            w.rbuf[1][tid] = wt * yy * r;
+          }
         }
         if (update) {
-#pragma unroll
-          for (int j2 = 0; j2 < NM; ++j2) w.stage[lane * LDS + j2] = psi[j2];
-          w.rbuf[0][lane] = wt * r;
-          w.rbuf[1][lane] = wt * yy * r;
-          __syncwarp();
-#pragma unroll
-          for (int rr = 0; rr < 2; ++rr) {
-            const int j2 = lane + 32 * rr;
-            if (j2 < nm) {
-              Real pn = 0, pd = 0;
-#pragma unroll 8
-              for (int s2 = 0; s2 < 32; ++s2) {
-                const Real bv = w.stage[s2 * LDS + j2];
-                pn = fma(bv, w.rbuf[0][s2], pn);
-                pd = fma(bv, w.rbuf[1][s2], pd);
-              }
-              hk[rr][0] += pn;
-              hk[rr][1] += pd;
+          __syncthreads();
+          if (tid < nm * hk_groups) {
+            const int j2 = tid % nm, g = tid / nm;
+            Real pn = 0, pd = 0;
+            for (int s2 = g; s2 < cnt; s2 += hk_groups) {
+              const Real bv = w.stage[s2 * LDS + j2];
+              pn = fma(bv, w.rbuf[0][s2], pn);
+              pd = fma(bv, w.rbuf[1][s2], pd);
             }
+            hk0 += pn;
+            hk1 += pd;
           }
-          __syncwarp();
+          __syncthreads();
         }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) pole |= __shfl_xor_sync(0xffffffffu, pole, o);
-      obj = warp_sum(obj);
-      // a step that increases the objective by more than the objective's own
-      // rounding level (plain FP32 residuals: ~1e-4 relative) is undone
-      if (it > 0 && obj > obj_prev * (compensated ? 1.00001f : 1.0001f)) {
-        for (int j2 = lane; j2 < n; j2 += 32) w.xsol[j2] = w.xprev[j2];
+      pole = __syncthreads_or(pole);
+      obj = block_sum_f(w, obj, 8);
+      __syncthreads();
+      const bool worse = it > 0 && obj > obj_prev * (compensated ? 1.00001f : 1.0001f);
+      if (worse) {
+        // the last step increased the objective: undo it
+        for (int j2 = tid; j2 < n; j2 += kT) w.xsol[j2] = w.xprev[j2];
         pole = pole_prev;
-        converged = converged || prev_rel <= 1e-4f;
-        __syncwarp();
+        obj_drop = 0.0f;
+        __syncthreads();
         break;
       }
-      for (int j2 = lane; j2 < n; j2 += 32) w.xprev[j2] = w.xsol[j2];
+      if (it > 0) obj_drop = (obj_prev - obj) / fmaxf(obj_prev, 1e-30f);
+      for (int j2 = tid; j2 < n; j2 += kT) w.xprev[j2] = w.xsol[j2];
       obj_prev = obj;
       pole_prev = pole;
-      __syncwarp();
+      __syncthreads();
       if (!update) break;
-      // g from H, K; scaled for the factored (equilibrated) system
-#pragma unroll
-      for (int rr = 0; rr < 2; ++rr) {
-        const int j2 = lane + 32 * rr;
-        if (j2 < nm) {
-          w.HK[0][j2] = hk[rr][0];
-          w.HK[1][j2] = hk[rr][1];
-        }
+      // H, K: sum the sample groups
+      if (tid < nm * hk_groups) {
+        w.stage[tid] = hk0;
+        w.stage[kT + tid] = hk1;
       }
-      __syncwarp();
-      for (int e = lane; e < n; e += 32) {
+      __syncthreads();
+      if (tid < nm) {
+        Real h = 0, k2 = 0;
+        for (int g = 0; g < hk_groups; ++g) {
+          h += w.stage[g * nm + tid];
+          k2 += w.stage[kT + g * nm + tid];
+        }
+        w.HK[0][tid] = h;
+        w.HK[1][tid] = k2;
+      }
+      __syncthreads();
+      // g, scaled for the factored (equilibrated) system
+      for (int e = tid; e < n; e += kT) {
         Real g;
         if (e < nm) {
           if (e == 0) {
@@ -812,40 +874,41 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
         }
         w.gvec[e] = g * w.scl[e];
       }
-      __syncwarp();
-      warp_solve<Real>(w.G, n, n, w.invd, w.gvec);
-      float dn = 0, xn = 0;
-      for (int j2 = lane; j2 < n; j2 += 32) {
-        const double dx = (double)(w.gvec[j2] * w.scl[j2]);
-        const double xv = w.xsol[j2] + dx;
-        w.xsol[j2] = xv;
-        dn += (float)(dx * dx);
-        xn += (float)(xv * xv);
+      __syncthreads();
+      if (wid == 0) {
+        warp_solve<Real>(w.G, n, n, w.invd, w.gvec);
+        float dn = 0, xn = 0;
+        for (int j2 = lane; j2 < n; j2 += 32) {
+          const double dx = (double)(w.gvec[j2] * w.scl[j2]);
+          const double xv = w.xsol[j2] + dx;
+          w.xsol[j2] = xv;
+          dn += (float)(dx * dx);
+          xn += (float)(xv * xv);
+        }
+        dn = warp_sum(dn);
+        xn = warp_sum(xn);
+        if (lane == 0) w.fscal[0] = xn > 0.0f ? sqrtf(dn / xn) : 0.0f;
       }
-      dn = warp_sum(dn);
-      xn = warp_sum(xn);
-      __syncwarp();
-      const float rel = xn > 0.0f ? sqrtf(dn / xn) : 0.0f;
+      __syncthreads();
+      const float rel = w.fscal[0];
       const bool was_compensated = compensated;
       if (!compensated && rel < 1e-4f) compensated = true;
-      if (rel <= (float)a.tol) {
-        done = converged = true;
-      } else if (was_compensated && rel > 0.9f * prev_rel) {
-        // corrections stopped shrinking: at the noise floor of the residuals
-        done = true;
-        converged = rel <= 1e-4f;
-      }
+      // stop at tol, or once compensated corrections stop shrinking (the
+      // residuals' noise floor)
+      if (rel <= (float)a.tol || (was_compensated && rel > 0.9f * prev_rel)) done = true;
       prev_rel = rel;
     }
     flags |= (pole_prev ? RP_FIT_POLE : 0);
-    if (a.max_refine > 0 && !converged && !(prev_rel <= 1e-4f)) flags |= RP_FIT_NOT_CONVERGED;
+    // not converged: the iteration cap was hit while the objective was still
+    // falling by more than 1e-5 per step
+    if (a.max_refine > 0 && !done && !(obj_drop <= 1e-5f)) flags |= RP_FIT_NOT_CONVERGED;
     flags |= min(it, 255) << RP_FIT_ITER_SHIFT;
 
     // ---------------- phase 6: back to the monomial basis (FP64)
     {
       double *cpsi = reinterpret_cast<double *>(w.stage);   // [2][kMaxNm]
       double *P = cpsi + 2 * kMaxNm;                          // [3][5][5]
-      for (int e = lane; e < 2 * nm; e += 32) {
+      for (int e = tid; e < 2 * nm; e += kT) {
         const int which = e / nm, i = e % nm;   // 0 numerator, 1 denominator
         if (i >= 1) {
           double u = 0;
@@ -856,9 +919,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
           cpsi[which * kMaxNm + i] = u;
         }
       }
-      if (lane < 3 * (kMaxDeg + 1)) {
+      if (tid >= 96 && tid < 96 + 3 * (kMaxDeg + 1)) {
         // Q_k(u), u = (x' - mu) isg, as a polynomial in x'
-        const int v = lane / (kMaxDeg + 1), k = lane % (kMaxDeg + 1);
+        const int v = (tid - 96) / (kMaxDeg + 1), k = (tid - 96) % (kMaxDeg + 1);
         const double mu = w.mu_v[v], isg = w.isg_v[v];
         double out[kMaxDeg + 1] = {0, 0, 0, 0, 0};
         if (k <= d) {
@@ -879,14 +942,14 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
         }
         for (int i2 = 0; i2 <= kMaxDeg; ++i2) P[(v * (kMaxDeg + 1) + k) * (kMaxDeg + 1) + i2] = out[i2];
       }
-      __syncwarp();
-      if (lane < 2) {
-        double c0 = lane == 0 ? w.xsol[0] : 1.0;
-        for (int i = 1; i < nm; ++i) c0 -= (double)w.mupsi[i] * cpsi[lane * kMaxNm + i];
-        cpsi[lane * kMaxNm] = c0;
+      __syncthreads();
+      if (tid < 2) {
+        double c0 = tid == 0 ? w.xsol[0] : 1.0;
+        for (int i = 1; i < nm; ++i) c0 -= (double)w.mupsi[i] * cpsi[tid * kMaxNm + i];
+        cpsi[tid * kMaxNm] = c0;
       }
-      __syncwarp();
-      for (int e = lane; e < 2 * nm; e += 32) {
+      __syncthreads();
+      for (int e = tid; e < 2 * nm; e += kT) {
         const int which = e / nm, t = e % nm;
         const int i0 = c_exp[t][0], i1 = c_exp[t][1], i2 = c_exp[t][2];
         double s = 0;
@@ -901,11 +964,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32) fit_kernel(FitArgs a, int warp
         cf[o] = s;
         if (a.coef32) a.coef32[f * kStride + o] = (float)s;
       }
-      if (lane == 0) {
+      if (tid == 0) {
         a.status[f] = flags;
         a.rank[f] = w.keep_cnt;
       }
-      __syncwarp();
+      __syncthreads();
     }
   }
 }
@@ -929,36 +992,19 @@ void set_tables() {
   done = true;
 }
 
-// Choose warps per CTA (1..8) to maximise resident warps per SM under the
-// per-warp shared-memory slice, then launch a persistent grid.
 template <class Real, int DMAX>
 cudaError_t launch_t(const FitArgs &a, cudaStream_t s) {
-  const size_t per_warp = warpfit_bytes<Real, DMAX>();
-  int best_w = 1, best_total = 0, best_ctas = 1;
-  for (int wpc = kMaxWarps; wpc >= 1; wpc /= 2) {
-    const size_t smem = per_warp * wpc;
-    if (smem > 227 * 1024) continue;
-    cudaError_t e = cudaFuncSetAttribute(fit_kernel<Real, DMAX>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fit_kernel<Real, DMAX>, wpc * 32, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm * wpc > best_total) {
-      best_total = per_sm * wpc;
-      best_w = wpc;
-      best_ctas = per_sm;
-    }
-  }
-  if (best_total == 0) return cudaErrorInvalidConfiguration;
-  const size_t smem = per_warp * best_w;
+  const size_t smem = ctafit_bytes<Real, DMAX>();
   cudaError_t e = cudaFuncSetAttribute(fit_kernel<Real, DMAX>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int64_t grid = (int64_t)num_sms() * best_ctas;
-  const int64_t need = (a.F + best_w - 1) / best_w;
-  if (grid > need) grid = need;
-  fit_kernel<Real, DMAX><<<(unsigned)grid, best_w * 32, smem, s>>>(a, best_w);
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fit_kernel<Real, DMAX>, kT, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)num_sms() * per_sm;
+  if (grid > a.F) grid = a.F;
+  fit_kernel<Real, DMAX><<<(unsigned)grid, kT, smem, s>>>(a);
   return cudaGetLastError();
 }
 

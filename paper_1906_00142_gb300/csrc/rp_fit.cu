@@ -134,40 +134,83 @@ __device__ void warp_solve(const SR *L, int n, int ld, const SR *invd, SR *b) {
   __syncwarp();
 }
 
-// FP64 Cholesky of the (d+1) x (d+1) Hankel moment matrix of a standardised
+// Cholesky (lower) of the n x n matrix G (row stride ld) by all NT threads of
+// the block, with column dropping: a pivot <= tol removes the column
+// (invd = 0).  Step k scales column k, then updates the trailing lower
+// triangle with one thread per entry.
+template <class SR, int NT>
+__device__ void cta_chol(SR *G, int n, int ld, SR tol, SR *invd, int *keep_cnt) {
+  const int tid = threadIdx.x;
+  for (int k = 0; k < n; ++k) {
+    const SR p = G[k * ld + k];
+    const bool keep = p > tol;
+    const SR inv = keep ? rsqrt_pos<SR>(p) : (SR)0;
+    __syncthreads();
+    if (tid == 0) {
+      G[k * ld + k] = keep ? p * inv : (SR)0;
+      invd[k] = inv;
+    }
+    for (int i = k + 1 + tid; i < n; i += NT) G[i * ld + k] *= inv;
+    __syncthreads();
+    const int r = n - k - 1;
+    const int np = r * (r + 1) / 2;
+    for (int e = tid; e < np; e += NT) {
+      int ii = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+      ii += ((ii + 1) * (ii + 2) / 2 <= e);
+      ii -= (ii * (ii + 1) / 2 > e);
+      const int jj = e - ii * (ii + 1) / 2;
+      const int i = k + 1 + ii, j = k + 1 + jj;
+      G[i * ld + j] -= G[i * ld + k] * G[j * ld + k];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    int kept = 0;
+    for (int k = 0; k < n; ++k) kept += invd[k] != (SR)0;
+    *keep_cnt = kept;
+  }
+  __syncthreads();
+}
+
+// Cholesky of the (d+1) x (d+1) Hankel moment matrix of a standardised
 // variable -> coefficients of the orthonormal polynomials (columns of the
 // inverse factor).  A variable with only q distinct sample values supports
 // polynomials of degree < q on the samples: Q_k for k > deg_eff (= q - 1) is
-// set to 0, as is any Q_k whose pivot is not positive.  Single thread.
-__device__ void marginal_transform(const double *M, int d, int deg_eff, float T[][kMaxDeg + 1]) {
-  double R[kMaxDeg + 1][kMaxDeg + 1], Ti[kMaxDeg + 1][kMaxDeg + 1];
+// set to 0.  Single thread, FP32 (the transform only has to give a
+// well-scaled basis; it is used consistently wherever the basis is).
+__device__ void marginal_transform(const float *M, int d, int deg_eff, float T[][kMaxDeg + 1]) {
+  float R[kMaxDeg + 1][kMaxDeg + 1], Ti[kMaxDeg + 1][kMaxDeg + 1];
   bool ok[kMaxDeg + 1];
   for (int i = 0; i <= kMaxDeg; ++i)
-    for (int j = 0; j <= kMaxDeg; ++j) R[i][j] = Ti[i][j] = 0.0;
+    for (int j = 0; j <= kMaxDeg; ++j) R[i][j] = Ti[i][j] = 0.0f;
   for (int k = 0; k <= d; ++k) {
-    double p = M[2 * k];
+    float p = M[2 * k];
     for (int l = 0; l < k; ++l) p -= R[l][k] * R[l][k];
-    ok[k] = k <= deg_eff && M[2 * k] > 0.0 && p > 1e-12 * M[2 * k];
+    ok[k] = k <= deg_eff && M[2 * k] > 0.0f;
     if (!ok[k]) continue;
-    R[k][k] = sqrt(p);
+    // a supported direction whose pivot rounding has eaten is regularised
+    // (any positive pivot keeps the polynomial basis a basis)
+    p = fmaxf(p, 1e-6f * M[2 * k]);
+    R[k][k] = sqrtf(p);
+    const float inv = 1.0f / R[k][k];
     for (int j = k + 1; j <= d; ++j) {
-      double s = M[k + j];
+      float s = M[k + j];
       for (int l = 0; l < k; ++l) s -= R[l][k] * R[l][j];
-      R[k][j] = s / R[k][k];
+      R[k][j] = s * inv;
     }
   }
   for (int k = 0; k <= d; ++k) {
     if (!ok[k]) continue;
-    Ti[k][k] = 1.0 / R[k][k];
+    Ti[k][k] = 1.0f / R[k][k];
     for (int i = k - 1; i >= 0; --i) {
       if (!ok[i]) continue;
-      double s = 0;
+      float s = 0;
       for (int l = i + 1; l <= k; ++l) s += R[i][l] * Ti[l][k];
       Ti[i][k] = -s / R[i][i];
     }
   }
   for (int l = 0; l <= kMaxDeg; ++l)
-    for (int k = 0; k <= kMaxDeg; ++k) T[l][k] = (l <= d && k <= d) ? (float)Ti[l][k] : 0.0f;
+    for (int k = 0; k <= kMaxDeg; ++k) T[l][k] = (l <= d && k <= d) ? Ti[l][k] : 0.0f;
   T[0][0] = 1.0f;  // Q_0 = 1 (M_0 = 1)
 }
 
@@ -564,11 +607,11 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? 4 : 2) 
         } else {
           const double isg = 1.0 / sqrt(var);
           w.isg_v[v] = (Real)isg;
-          double Ms[2 * kMaxDeg + 1];
-          Ms[0] = 1.0;
+          float Ms[2 * kMaxDeg + 1];
+          Ms[0] = 1.0f;
           double pw = isg;
           for (int k = 1; k <= 2 * DMAX; ++k) {
-            Ms[k] = M[k] * pw;
+            Ms[k] = (float)(M[k] * pw);
             pw *= isg;
           }
           int cnt = 0;
@@ -623,10 +666,8 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? 4 : 2) 
       // the whitening only preconditions: any positive pivot is kept (the
       // basis stays a basis of the same space); only directions whose pivot
       // is at rounding level or below are dropped
-      if (wid == 0)
-        warp_chol<Real>(w.stage, nc, nc, sizeof(Real) == 8 ? (Real)1e-14 : (Real)1e-10, w.invw,
-                        &w.keep_w);
-      __syncthreads();
+      cta_chol<Real, kT>(w.stage, nc, nc, sizeof(Real) == 8 ? (Real)1e-14 : (Real)1e-10, w.invw,
+                         &w.keep_w);
       // R^{-1} (R = L^T, R[i][l] = L[l][i]) column by column into G; W = D R^{-1}
       for (int j = tid; j < nc; j += kT)
         for (int i = j; i >= 0; --i) {
@@ -692,8 +733,8 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? 4 : 2) 
       for (int e = tid; e < n * n; e += kT) w.G[e] = w.stage[e];
       for (int j = tid; j < n; j += kT) w.gvec[j] *= w.scl[j];
       __syncthreads();
+      cta_chol<Real, kT>(w.G, n, n, (Real)a.drop_tol, w.invd, &w.keep_cnt);
       if (wid == 0) {
-        warp_chol<Real>(w.G, n, n, (Real)a.drop_tol, w.invd, &w.keep_cnt);
         warp_solve<Real>(w.G, n, n, w.invd, w.gvec);
         for (int j = lane; j < n; j += 32) w.xsol[j] = (double)(w.gvec[j] * w.scl[j]);
       }
@@ -897,6 +938,12 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? 4 : 2) 
       // residuals' noise floor)
       if (rel <= (float)a.tol || (was_compensated && rel > 0.9f * prev_rel)) done = true;
       prev_rel = rel;
+      if (done) {
+        // converged: the last correction is below tol (or at the residuals'
+        // noise floor); it is kept without another evaluation pass
+        ++it;
+        break;
+      }
     }
     flags |= (pole_prev ? RP_FIT_POLE : 0);
     // not converged: the iteration cap was hit while the objective was still

@@ -11,8 +11,9 @@ Two checks per fit:
     perturbed by one FP32 rounding (the oracle's sensitivity check), no
     FP32-data method can do better than ~sens.  A GPU design entry carries
     ~10 roundings (normalisation, marginal polynomials, products,
-    whitening), so the gate there is max(1e-4, 30 sens).  The number of
-    fits with sens >= 1e-5 is reported.
+    whitening), so the gate there is max(1e-4, 30 sens); fits with
+    sens >= 1e-2 are compared on the objective only.  The number of fits
+    with sens >= 1e-5 is reported.
 """
 import numpy as np
 import pytest
@@ -63,10 +64,15 @@ def compare(inst, g, ref=None, sens=None, all_fits=False):
     rel = np.abs(p_g - p_o) / np.abs(p_o)
     err = per_fit_max(rel, off)
     gate = np.full(len(err), TOL) if all_fits else np.maximum(TOL, 30.0 * sens)
-    bad = np.where(ok & ~(err <= gate))[0]
+    # a fit whose own predictions move by more than 1% under one FP32 rounding
+    # of its data has no FP32-determined predictions: only its objective
+    # (checked above) is compared
+    checked = ok if all_fits else ok & (sens < 1e-2)
+    bad = np.where(checked & ~(err <= gate))[0]
     assert len(bad) == 0, [(int(f), float(err[f]), float(sens[f]), int(g["status"][f])) for f in bad[:10]]
     well = ok & (sens < 1e-5)
     print(f"fits {ok.sum()}: well-posed at FP32 data precision {well.sum()}, "
+          f"objective-only {(ok & ~checked).sum()}, "
           f"median err {np.median(err[ok]):.2e}, max err on well-posed "
           f"{(err[well].max() if well.any() else 0):.2e}")
     # coef32 is coef rounded to float

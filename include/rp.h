@@ -64,6 +64,7 @@ typedef enum rp_status {
 #define RP_FIT_NONFINITE 8        /* NaN/Inf in the fit's samples: no fit */
 #define RP_FIT_NONPOS_Y 16        /* y <= 0 with relative weighting: no fit */
 #define RP_FIT_EMPTY 32           /* no samples: no fit */
+#define RP_FIT_TIMEOUT 64         /* a bounded wait of the tensor-core path ran out: no fit */
 #define RP_FIT_ITER_SHIFT 8       /* bits 8..15: refinement iterations performed */
 #define RP_FIT_ITER_MASK 0xFF00
 
@@ -74,12 +75,13 @@ typedef enum rp_status {
 
 /* Arithmetic used by rp_fit for the Gram product of the design matrix. */
 typedef enum rp_precision {
-  RP_PREC_FP64 = 0,    /* plain form: FP64 design, FP64 Gram on CUDA cores */
-  RP_PREC_FP32 = 1,    /* FP32 design, FP32 Gram on CUDA cores */
-  RP_PREC_TF32 = 2,    /* FP32 design, TF32 tensor-core Gram (tcgen05) */
-  RP_PREC_TF32X3 = 3,  /* split TF32 (hi*hi + hi*lo + lo*hi) tensor-core Gram */
-  RP_PREC_BF16 = 4,    /* BF16 tensor-core Gram (tcgen05) */
-  RP_PREC_BF16X3 = 5   /* split BF16 (three terms) tensor-core Gram */
+  RP_PREC_FP64 = 0,    /* plain form: FP64 design, Gram, factor and residuals on CUDA cores */
+  RP_PREC_FP32 = 1,    /* FP32 design, Gram products and factor on CUDA cores */
+  RP_PREC_TF32 = 2,    /* FP32 design; design Gram in one TF32 tensor-core pass (tcgen05),
+                          basis Gram in split TF32; FP32 factor; residuals from the samples */
+  RP_PREC_TF32X3 = 3,  /* as TF32 with both Grams in split TF32 (hi*hi + hi*lo + lo*hi) */
+  RP_PREC_BF16 = 4,    /* reserved: rp_fit returns RP_ERR_UNSUPPORTED */
+  RP_PREC_BF16X3 = 5   /* reserved: rp_fit returns RP_ERR_UNSUPPORTED */
 } rp_precision;
 
 /* rp_fit flags */

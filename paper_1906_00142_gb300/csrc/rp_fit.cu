@@ -36,6 +36,7 @@
 #include <stdint.h>
 
 #include "rp_internal.cuh"
+#include "rp_tc.cuh"
 
 namespace rpk {
 namespace {
@@ -241,7 +242,27 @@ __device__ __forceinline__ void distinct_insert(unsigned *slots, float x) {
 constexpr int kT = 128;       // threads per CTA (one fit at a time)
 constexpr int kMC = 512;      // samples per fit kept in shared memory
 
-template <class Real, int DMAX>
+// Tensor-core Gram shapes (Sec. 4.2 normal equations on tcgen05).  A Gram
+// X^T X over the samples is one MMA chain D = A B^T with A = B = X^T stored
+// K-major (K = samples): the B operand holds the NPAD padded columns, the A
+// operand (M = 128 rows) reads the same tile and the shared memory after it
+// (rows >= NPAD of D are never read).  One K-block = 32 samples = NPAD/8
+// swizzle atoms.
+template <int DMAX>
+struct TcShape {
+  static constexpr int NM = (DMAX + 1) * (DMAX + 2) * (DMAX + 3) / 6;
+  static constexpr int NAUG = 2 * NM;
+  static constexpr int NDES = ((NAUG + 15) / 16) * 16;
+  static constexpr int NB_DES = NDES / 8 * 1024;
+  static constexpr int TMEM_COLS = NDES <= 64 ? 64 : 128;
+};
+
+// GM: 0 = design Gram on CUDA cores (FP32 or FP64), 1 = design Gram on the
+// tensor cores in one TF32 pass, 2 = in three TF32 passes (hi.hi + hi.lo +
+// lo.hi).  The basis Gram (whitening) is always formed on CUDA cores: its
+// condition number (~1e6 for the correlated B0, B1 of the 66 formats) needs
+// round-to-nearest FP32 accumulation.
+template <class Real, int DMAX, int GM>
 struct CtaFit {
   static constexpr int NM = (DMAX + 1) * (DMAX + 2) * (DMAX + 3) / 6;
   static constexpr int NAUG = 2 * NM;
@@ -249,14 +270,21 @@ struct CtaFit {
   // rows; 128-bit reads of the same row by many threads spread over banks)
   static constexpr int LDS = (((NAUG + 3) / 4) % 2 == 1) ? ((NAUG + 3) / 4) * 4 : ((NAUG + 3) / 4 + 1) * 4;
   static constexpr int WS = ((NM + 3) / 4) * 4;   // row stride of W (16-byte rows)
+  using TS = TcShape<DMAX>;
+  static constexpr int ROWS_BYTES = kT * LDS * (int)sizeof(Real);
+  static constexpr int TC_BYTES = GM == 0 ? 0 : (GM == 2 ? 8 : 4) * TS::NB_DES;
+  static constexpr int STAGE_BYTES = ROWS_BYTES > TC_BYTES ? ROWS_BYTES : TC_BYTES;
+  // furthest byte the M = 128 A operand reads, from the start of `stage`
+  static constexpr int TC_REACH = GM == 0 ? 0 : (GM == 2 ? 7 : 3) * TS::NB_DES + 16384;
+  alignas(16) Real stage[STAGE_BYTES / sizeof(Real)];   // first member: 1024-byte aligned
   double xsol[NAUG];                  // solution (design basis, unscaled)
   double xprev[NAUG];                 // best solution so far (refinement)
   double uv[2][NM];                   // solution in the unwhitened basis
   double lo[3], hi[3];
   double redd[4][32];
-  Real G[NAUG * NAUG];                // Gram, then factor (stride n)
-  Real stage[kT * LDS];               // staged rows / reduction scratch
-  Real W[NM * WS];                    // whitening, upper triangular on 1..nm-1
+  uint64_t mbar;                      // tensor-core completion barrier
+  alignas(16) Real G[NAUG * NAUG];    // Gram, then factor (stride n)
+  alignas(16) Real W[NM * WS];        // whitening, upper triangular on 1..nm-1 (128-bit loads)
   Real mupsi[NM];
   Real gvec[NAUG], scl[NAUG], invd[NAUG], invw[NM];
   Real HK[2][NM];
@@ -267,13 +295,17 @@ struct CtaFit {
   float xs[4][kMC];                   // sample cache (N, B0, B1, y)
   float redf[4][32];
   unsigned dslot[3][kMaxDeg + 1];
+  uint32_t tmem_base;
   int keep_cnt, keep_w, bad;
   float fscal[4];
 };
 
-template <class Real, int DMAX>
+// Dynamic shared memory of one CTA: the state, at least TC_REACH bytes from
+// its start, plus 1 KB to align the start to 1024 bytes.
+template <class Real, int DMAX, int GM>
 __host__ __device__ constexpr size_t ctafit_bytes() {
-  return (sizeof(CtaFit<Real, DMAX>) + 15) & ~size_t(15);
+  using WF = CtaFit<Real, DMAX, GM>;
+  return ((sizeof(WF) > (size_t)WF::TC_REACH ? sizeof(WF) : (size_t)WF::TC_REACH) + 15 & ~size_t(15)) + 1024;
 }
 
 // Block-wide sum of one float per thread; result returned to every thread.
@@ -434,12 +466,102 @@ struct TileGram {
   }
 };
 
+// Tensor-core Gram X^T X of up to NPAD columns over 128-sample chunks: each
+// thread stages its sample's row (column j at row j of the K-major tile,
+// K slot = the thread), one thread issues the MMAs of the chunk's K-blocks
+// and commits them to an mbarrier.  X3: the staged values are split into a
+// TF32 head and tail and D accumulates hi.hi + hi.lo + lo.hi.
+constexpr uint32_t kTcWaitLimit = 1u << 22;   // mbarrier polls before giving up
+
+template <int NPAD, bool X3>
+struct TcGram {
+  static constexpr int NB = NPAD / 8 * 1024;   // bytes per K-block of 32 samples
+  uint32_t base;                               // this thread's K slot in K-block 0
+  uint32_t xo[8];                              // swizzled chunk offset per row % 8
+
+  __device__ __forceinline__ void init() {
+    const int t = threadIdx.x;
+    base = (uint32_t)((t >> 5) * NB + (t & 3) * 4);
+    const int c = (t & 31) >> 2;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) xo[r] = (uint32_t)(((c ^ r) & 7) << 4);
+  }
+  // column j (a compile-time index after unrolling) of this thread's sample
+  __device__ __forceinline__ void put(unsigned char *st, int j, float v) const {
+    const uint32_t o = base + (uint32_t)((j >> 3) * 1024 + (j & 7) * 128) + xo[j & 7];
+    float h, l;
+    tc::split_tf32(v, h, l);
+    *reinterpret_cast<float *>(st + o) = h;
+    if (X3) *reinterpret_cast<float *>(st + 4 * NB + o) = l;
+  }
+  // one thread: D = (first ? 0 : D) + X^T X over nkb K-blocks
+  __device__ static void issue(const unsigned char *st, uint32_t tmem, int nkb, bool first) {
+    constexpr uint32_t id = tc::idesc(tc::kFmtTF32, 128, NPAD);
+    const uint32_t b = tc::smem_u32(st);
+    for (int kb = 0; kb < nkb; ++kb)
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const uint32_t off = (uint32_t)(kb * NB + 32 * s);
+        const uint64_t ah = tc::sw128_desc(b + off);
+        tc::mma_tf32(tmem, ah, ah, id, (first && kb == 0 && s == 0) ? 0u : 1u);
+        if (X3) {
+          const uint64_t al = tc::sw128_desc(b + 4 * NB + off);
+          tc::mma_tf32(tmem, ah, al, id, 1u);
+          tc::mma_tf32(tmem, al, ah, id, 1u);
+        }
+      }
+  }
+  // Warps holding padded rows < rows copy D into G: padded index j maps to
+  // map(j) (< 0: unused), G[map(r) * ld + map(c)].
+  template <class Real, class Map>
+  __device__ static void read(uint32_t tmem, int rows, Real *G, int ld, Map map) {
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (32 * wid < rows) {
+      const int r = 32 * wid + lane;
+      const int rc = r < rows ? map(r) : -1;
+#pragma unroll
+      for (int c0 = 0; c0 < NPAD; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(32 * wid) << 16) + (uint32_t)c0, v);
+        if (rc >= 0)
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int cc = map(c0 + q);
+            if (cc >= 0) G[rc * ld + cc] = (Real)v[q];
+          }
+      }
+    }
+    tc::fence_before_sync();
+  }
+};
+
+// Staged values visible to the tensor core, MMAs of one chunk issued by
+// thread 0 and committed, completion awaited by every thread (bounded).
+template <class TG>
+__device__ __forceinline__ bool tc_chunk(const unsigned char *st, uint32_t tmem, uint64_t *mbar,
+                                         int nkb, bool first, uint32_t &phase) {
+  tc::fence_proxy_async_smem();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc::fence_after_sync();
+    TG::issue(st, tmem, nkb, first);
+    tc::mma_commit(mbar);
+  }
+  const bool ok = tc::mbar_wait(mbar, phase, kTcWaitLimit);
+  tc::fence_after_sync();
+  const bool all = __syncthreads_and(ok);
+  if (all) phase ^= 1u;
+  return all;
+}
+
 // ---------------------------------------------------------------------
 // The fit kernel.  Real = double: plain FP64 path; Real = float: FP32 path.
 
-template <class Real, int DMAX>
-__global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? 4 : 2) fit_kernel(FitArgs a) {
-  using WF = CtaFit<Real, DMAX>;
+template <class Real, int DMAX, int GM>
+__global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 2 ? 3 : 4) : (DMAX <= 3 ? 2 : 1))
+    fit_kernel(FitArgs a) {
+  using WF = CtaFit<Real, DMAX, GM>;
+  using TS = TcShape<DMAX>;
   constexpr int NM = WF::NM;
   constexpr int NAUG = WF::NAUG;
   constexpr int LDS = WF::LDS;
@@ -447,8 +569,24 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? 4 : 2) 
   constexpr int S4 = (NAUG + 3) / 4;
   constexpr int IPT = ((S4 * (S4 + 1) / 2) + kT - 1) / kT;   // design-Gram items per thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  WF &w = *reinterpret_cast<WF *>(smem_raw);
+  // the state starts at the first 1024-byte boundary (swizzle atoms)
+  const uint32_t raw_s = tc::smem_u32(smem_raw);
+  WF &w = *reinterpret_cast<WF *>(smem_raw + (((raw_s + 1023u) & ~1023u) - raw_s));
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // tensor memory for the Gram accumulators, held for the whole launch
+  uint32_t tmem = 0, tc_phase = 0;
+  bool tc_dead = false;
+  if constexpr (GM > 0) {
+    if (wid == 0) {
+      tc::tmem_alloc(&w.tmem_base, TS::TMEM_COLS);
+      tc::tmem_relinquish();
+    }
+    if (tid == 0) tc::mbar_init(&w.mbar, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    tmem = w.tmem_base;
+  }
   for (int64_t f = blockIdx.x; f < a.F; f += gridDim.x) {
     // ---------------- phase 0: range, degree, validation, box, distinct values
     const int64_t b0 = a.off[f], b1 = a.off[f + 1];
@@ -646,6 +784,7 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? 4 : 2) 
         __syncthreads();
       }
       tg.finish(nm, w.G, w.stage);
+
       // means (row 0 holds the sums of Psi_j), the centred Gram / m of the
       // non-constant functions, equilibrated, in `stage`
       for (int j = tid; j < NM; j += kT) w.mupsi[j] = (j < nm) ? w.G[j] / (Real)m : (Real)0;
@@ -684,7 +823,52 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? 4 : 2) 
     }
 
     // ---------------- phase 3: the design Gram [num (nm) | den (nm-1) | rhs]
-    {
+    if constexpr (GM > 0) {
+      // staged in the padded layout num [0, NM), den [NM, 2 NM - 1), rhs
+      // 2 NM - 1 (compile-time columns); read back compacted to stride naug
+      using TG = TcGram<TS::NDES, GM == 2>;
+      TG tg;
+      tg.init();
+      unsigned char *st = reinterpret_cast<unsigned char *>(w.stage);
+      for (int base = 0; base < m && !tc_dead; base += kT) {
+        const int cnt = min(kT, m - base);
+        const int nkb = (cnt + 31) >> 5;
+        if (tid < nkb * 32) {
+          Real pt[NM];
+          Real wt = 0, yy = 0;
+          if (tid < cnt) {
+            const int i = base + tid;
+            Real psi[NM];
+            eval_psi<Real, DMAX, NM>(w, d, nm, sx0[i], sx1[i], sx2[i], psi);
+            whiten<Real, NM, WS>(w, psi, pt);
+            yy = (Real)sy[i];
+            wt = a.weighted ? (Real)1 / fabs(yy) : (Real)1;
+          } else {
+#pragma unroll
+            for (int j = 0; j < NM; ++j) pt[j] = 0;
+          }
+#pragma unroll
+          for (int j = 0; j < NM; ++j) tg.put(st, j, j < nm ? (float)(wt * pt[j]) : 0.0f);
+#pragma unroll
+          for (int j = 1; j < NM; ++j) tg.put(st, NM + j - 1, j < nm ? (float)(-wt * yy * pt[j]) : 0.0f);
+          tg.put(st, 2 * NM - 1, (float)(wt * yy));
+#pragma unroll
+          for (int j = 2 * NM; j < TS::NDES; ++j) tg.put(st, j, 0.0f);
+        }
+        tc_dead = !tc_chunk<TG>(st, tmem, &w.mbar, nkb, base == 0, tc_phase);
+      }
+      if (tc_dead) {
+        if (tid == 0) {
+          a.status[f] = RP_FIT_TIMEOUT;
+          a.rank[f] = 0;
+        }
+        continue;
+      }
+      TG::read(tmem, 2 * NM, w.G, naug, [nm](int j) {
+        return j < nm ? j : (j < NM ? -1 : (j < NM + nm - 1 ? nm + (j - NM) : (j == 2 * NM - 1 ? 2 * nm - 1 : -1)));
+      });
+      __syncthreads();
+    } else {
       TileGram<Real, IPT, LDS> tg;
       tg.init(naug);
       const int cols4 = 4 * ((naug + 3) / 4);
@@ -1018,6 +1202,15 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? 4 : 2) 
       __syncthreads();
     }
   }
+  if constexpr (GM > 0) {
+    // after a wait that gave up, wait (bounded) once more for the MMAs still
+    // in flight before the tensor memory is released
+    if (tc_dead && tid == 0) (void)tc::mbar_wait(&w.mbar, tc_phase, kTcWaitLimit);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (wid == 0) tc::tmem_dealloc(tmem, TS::TMEM_COLS);
+  }
 }
 
 // ---------------------------------------------------------------------
@@ -1039,20 +1232,47 @@ void set_tables() {
   done = true;
 }
 
-template <class Real, int DMAX>
+template <class Real, int DMAX, int GM>
 cudaError_t launch_t(const FitArgs &a, cudaStream_t s) {
-  const size_t smem = ctafit_bytes<Real, DMAX>();
-  cudaError_t e = cudaFuncSetAttribute(fit_kernel<Real, DMAX>,
+  using WF = CtaFit<Real, DMAX, GM>;
+  // 128-bit shared-memory loads of the staged rows and of W; 8-byte mbarrier
+  static_assert(offsetof(WF, stage) == 0, "stage must start the state");
+  static_assert(offsetof(WF, W) % 16 == 0 && offsetof(WF, G) % 16 == 0, "W, G: 16-byte aligned");
+  static_assert(offsetof(WF, mbar) % 8 == 0, "mbarrier: 8-byte aligned");
+  const size_t smem = ctafit_bytes<Real, DMAX, GM>();
+  cudaError_t e = cudaFuncSetAttribute(fit_kernel<Real, DMAX, GM>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fit_kernel<Real, DMAX>, kT, smem);
+  // resident CTAs per SM from registers, shared memory and (tensor-core
+  // path) tensor-memory columns
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, fit_kernel<Real, DMAX, GM>);
   if (e != cudaSuccess) return e;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int smem_sm = 0, smem_rsv = 0, regs_sm = 0;
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  const int regs_cta = ((fa.numRegs * 32 + 255) / 256 * 256) * (kT / 32);
+  int per_sm = smem_sm / (int)(smem + smem_rsv);
+  per_sm = min(per_sm, regs_sm / max(regs_cta, 1));
+  per_sm = min(per_sm, 2048 / kT);
+  if (GM > 0) per_sm = min(per_sm, 512 / TcShape<DMAX>::TMEM_COLS);
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)num_sms() * per_sm;
   if (grid > a.F) grid = a.F;
-  fit_kernel<Real, DMAX><<<(unsigned)grid, kT, smem, s>>>(a);
+  fit_kernel<Real, DMAX, GM><<<(unsigned)grid, kT, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int GM>
+cudaError_t launch_f32(const FitArgs &a, int dmax, cudaStream_t s) {
+  switch (dmax) {
+    case 1: case 2: return launch_t<float, 2, GM>(a, s);
+    case 3: return launch_t<float, 3, GM>(a, s);
+    default: return launch_t<float, 4, GM>(a, s);
+  }
 }
 
 }  // namespace
@@ -1060,7 +1280,8 @@ cudaError_t launch_t(const FitArgs &a, cudaStream_t s) {
 size_t fit_workspace_bytes(const rp_fit_desc &) { return 0; }
 
 bool fit_precision_supported(int precision) {
-  return precision == RP_PREC_FP64 || precision == RP_PREC_FP32;
+  return precision == RP_PREC_FP64 || precision == RP_PREC_FP32 || precision == RP_PREC_TF32 ||
+         precision == RP_PREC_TF32X3;
 }
 
 cudaError_t launch_fit(const rp_fit_desc &desc, const float *x, const float *y,
@@ -1088,17 +1309,15 @@ cudaError_t launch_fit(const rp_fit_desc &desc, const float *x, const float *y,
   if (desc.precision == RP_PREC_FP64) {
     a.drop_tol = 1e-13;
     switch (dmax) {
-      case 1: case 2: return launch_t<double, 2>(a, s);
-      case 3: return launch_t<double, 3>(a, s);
-      default: return launch_t<double, 4>(a, s);
+      case 1: case 2: return launch_t<double, 2, 0>(a, s);
+      case 3: return launch_t<double, 3, 0>(a, s);
+      default: return launch_t<double, 4, 0>(a, s);
     }
   }
   a.drop_tol = 1e-7;
-  switch (dmax) {
-    case 1: case 2: return launch_t<float, 2>(a, s);
-    case 3: return launch_t<float, 3>(a, s);
-    default: return launch_t<float, 4>(a, s);
-  }
+  if (desc.precision == RP_PREC_TF32) return launch_f32<1>(a, dmax, s);
+  if (desc.precision == RP_PREC_TF32X3) return launch_f32<2>(a, dmax, s);
+  return launch_f32<0>(a, dmax, s);
 }
 
 }  // namespace rpk

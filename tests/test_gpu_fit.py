@@ -88,13 +88,18 @@ def batched():
     return inst, ref, sens
 
 
-def test_fit_fp32_batched(batched):
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "tf32x3"])
+def test_fit_fp32_data_batched(batched, precision):
+    """FP32 design; Gram products on CUDA cores (fp32) or on the tensor
+    cores (tf32: one TF32 pass for the design Gram; tf32x3: split TF32,
+    three passes)."""
     need_gpu()
     inst, ref, sens = batched
-    g = gpu_fit(inst, "fp32")
+    g = gpu_fit(inst, precision)
+    assert not (g["status"] & rp.RP_FIT_TIMEOUT).any()
     err, _ = compare(inst, g, ref, sens)
     iters = (g["status"] & rp.RP_FIT_ITER_MASK) >> rp.RP_FIT_ITER_SHIFT
-    print("refinement iterations: median", np.median(iters), "max", iters.max())
+    print(precision, "refinement iterations: median", np.median(iters), "max", iters.max())
     assert ((g["status"] & rp.RP_FIT_NOT_CONVERGED) == 0).mean() > 0.95, np.unique(g["status"])
 
 
@@ -113,7 +118,7 @@ def test_fit_uniform_degree_argument(batched):
     compare(inst, g, ref, sens)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "tf32x3", "fp64"])
 def test_fit_tiny_exact_data(precision):
     """Noise-free integer-coefficient rationals (plain FP64 tiny case)."""
     need_gpu()
@@ -122,7 +127,7 @@ def test_fit_tiny_exact_data(precision):
     compare(inst, g, all_fits=(precision == "fp64"))
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "fp64"])
 def test_fit_uneven_degrees_and_counts(precision):
     """Per-fit degree 2..4 and sample counts 64..2048 (some beyond the
     shared-memory sample cache)."""
@@ -150,7 +155,7 @@ def test_fit_edge_cases():
     off = np.zeros(7, np.int64)
     off[1:] = np.cumsum([len(v) for v in ys])
     inst = dict(x=np.ascontiguousarray(x), y=y, fit_off=off, degree=np.full(6, 2, np.int8))
-    for prec in ["fp32", "fp64"]:
+    for prec in ["fp32", "tf32", "tf32x3", "fp64"]:
         g = gpu_fit(inst, prec, degree=2)
         assert g["status"][1] & rp.RP_FIT_EMPTY
         assert g["status"][2] & rp.RP_FIT_NONFINITE
@@ -167,12 +172,14 @@ def test_fit_edge_cases():
             assert np.max(np.abs(pg[a:b] - po[a:b]) / po[a:b]) < TOL
 
 
-def test_fit_full_size_sampled():
+@pytest.mark.parametrize("precision", ["fp32", "tf32"])
+def test_fit_full_size_sampled(precision):
     """The benchmarked launch: 1024 kernels x 8 metrics, 512 samples, d=3;
     64 fits re-solved by the oracle."""
     need_gpu()
     inst = W.batched_instance(1024, seed=20190602, m=512, d=3)
-    g = gpu_fit(inst, "fp32")
+    g = gpu_fit(inst, precision)
+    assert not (g["status"] & rp.RP_FIT_TIMEOUT).any()
     F = len(inst["fit_off"]) - 1
     pick = np.sort(np.random.default_rng(1).choice(F, 64, replace=False))
     xs, ys, offs = [], [], [0]

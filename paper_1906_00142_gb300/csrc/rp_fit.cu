@@ -84,57 +84,6 @@ __device__ __forceinline__ float rsqrt_pos<float>(float v) { return 1.0f / sqrtf
 template <>
 __device__ __forceinline__ double rsqrt_pos<double>(double v) { return 1.0 / sqrt(v); }
 
-// Warp-synchronous Cholesky (lower) of the n x n matrix G (row stride ld) in
-// place, with column dropping: a pivot <= tol removes the column (invd = 0).
-// Called by one full warp.
-template <class SR>
-__device__ void warp_chol(SR *G, int n, int ld, SR tol, SR *invd, int *keep_cnt) {
-  const int lane = threadIdx.x & 31;
-  int kept = 0;
-  for (int k = 0; k < n; ++k) {
-    __syncwarp();
-    const SR p = G[k * ld + k];
-    const bool keep = p > tol;
-    const SR inv = keep ? rsqrt_pos<SR>(p) : (SR)0;
-    kept += keep;
-    __syncwarp();
-    if (lane == 0) {
-      G[k * ld + k] = keep ? p * inv : (SR)0;
-      invd[k] = inv;
-    }
-    for (int i = k + 1 + lane; i < n; i += 32) G[i * ld + k] *= inv;
-    __syncwarp();
-    for (int i = k + 1 + lane; i < n; i += 32) {
-      const SR lik = G[i * ld + k];
-      for (int j = k + 1; j <= i; ++j) G[i * ld + j] -= lik * G[j * ld + k];
-    }
-  }
-  __syncwarp();
-  if (lane == 0) *keep_cnt = kept;
-  __syncwarp();
-}
-
-// Solve (L L^T) z = b in place (one warp; dropped columns give z = 0).
-template <class SR>
-__device__ void warp_solve(const SR *L, int n, int ld, const SR *invd, SR *b) {
-  const int lane = threadIdx.x & 31;
-  for (int k = 0; k < n; ++k) {
-    __syncwarp();
-    const SR yk = b[k] * invd[k];
-    __syncwarp();
-    if (lane == 0) b[k] = yk;
-    for (int i = k + 1 + lane; i < n; i += 32) b[i] -= L[i * ld + k] * yk;
-  }
-  for (int k = n - 1; k >= 0; --k) {
-    __syncwarp();
-    const SR xk = b[k] * invd[k];
-    __syncwarp();
-    if (lane == 0) b[k] = xk;
-    for (int i = lane; i < k; i += 32) b[i] -= L[k * ld + i] * xk;
-  }
-  __syncwarp();
-}
-
 // Cholesky (lower) of the n x n matrix G (row stride ld) by all NT threads of
 // the block, with column dropping: a pivot <= tol removes the column
 // (invd = 0).  Step k scales column k, then updates the trailing lower
@@ -277,9 +226,7 @@ struct CtaFit {
   // furthest byte the M = 128 A operand reads, from the start of `stage`
   static constexpr int TC_REACH = GM == 0 ? 0 : (GM == 2 ? 7 : 3) * TS::NB_DES + 16384;
   alignas(16) Real stage[STAGE_BYTES / sizeof(Real)];   // first member: 1024-byte aligned
-  double xsol[NAUG];                  // solution (design basis, unscaled)
-  double xprev[NAUG];                 // best solution so far (refinement)
-  double uv[2][NM];                   // solution in the unwhitened basis
+  double uv[2][NM], uvp[2][NM];       // FP64 path: (c, u) and (c, v) of p and q; previous
   double lo[3], hi[3];
   double redd[4][32];
   uint64_t mbar;                      // tensor-core completion barrier
@@ -287,11 +234,16 @@ struct CtaFit {
   alignas(16) Real W[NM * WS];        // whitening, upper triangular on 1..nm-1 (128-bit loads)
   Real mupsi[NM];
   Real gvec[NAUG], scl[NAUG], invd[NAUG], invw[NM];
+  Real xw[NAUG], xwp[NAUG], dxw[NAUG];  // iterate in the design basis (norms), previous, step
+  Real rowb[2][NAUG];                 // pivot rows of the sweep
+  Real duv[2][NM];                    // step of (c, u), (c, v)
   Real HK[2][NM];
   Real rbuf[2][kT];
   Real Tm[3][kMaxDeg + 1][kMaxDeg + 1];  // Q_k(u) = sum_l Tm[l][k] u^l
   Real mu_v[3], isg_v[3], sc_v[3], of_v[3];
-  float uvhi[2][NM], uvlo[2][NM];
+  float uvhi[2][NM], uvlo[2][NM];     // FP32 path: (c, u), (c, v) as head + tail
+  float uvphi[2][NM], uvplo[2][NM];   // previous
+  float redv[4][((2 * NM + 2 + 15) / 16) * 16];
   float xs[4][kMC];                   // sample cache (N, B0, B1, y)
   float redf[4][32];
   unsigned dslot[3][kMaxDeg + 1];
@@ -465,6 +417,93 @@ struct TileGram {
     __syncthreads();
   }
 };
+
+// Warp reduce-scatter of V values per lane (V a multiple of 16): four
+// halving exchanges (offsets 16, 8, 4, 2) and one full exchange (offset 1).
+// Afterwards lane l holds, in v[0 .. V/16), the warp totals of the original
+// indices rs_base<V>(l) + q (lanes l and l ^ 1 hold the same totals).
+template <int V>
+__device__ __forceinline__ void warp_reduce_scatter(float (&v)[V]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int step = 0; step < 4; ++step) {
+    const int o = 16 >> step;
+    const int half = V >> (step + 1);
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      const float send = up ? v[j] : v[j + half];
+      const float keep = up ? v[j + half] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < V / 16; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], 1);
+}
+template <int V>
+__device__ __forceinline__ int rs_base(int lane) {
+  return ((lane >> 4) & 1) * (V / 2) + ((lane >> 3) & 1) * (V / 4) + ((lane >> 2) & 1) * (V / 8) +
+         ((lane >> 1) & 1) * (V / 16);
+}
+
+// x += dx in head + tail form (FP32 pairs carrying ~46 bits)
+__device__ __forceinline__ void df_add(float &h, float &l, float d) {
+  float s, e;
+  two_sum(h, d, s, e);
+  const float t = l + e;
+  h = s + t;
+  l = t - (h - s);
+}
+
+// Apply the design-basis step dxw (n entries: numerator 0..nm-1, denominator
+// 1..nm-1 at nm..2nm-2) to the fitted function: with u = W x_num and
+// v = W x_den on the non-constant basis functions, du = W dx_num,
+// dv = W dx_den, dc_p = dx_num_0 - mu.du, dc_q = -mu.dv.  The iterate
+// (c_p, u), (c_q, v) is kept in FP64 (FP64 path) or as FP32 head + tail
+// pairs (FP32 paths); dxw itself is FP32 there.  Returns ||dx|| / ||x||
+// for the updated x (block-wide; contains barriers).
+template <class Real, int NM, int WS, class S>
+__device__ float apply_step(S &w, int nm, int n) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int e = tid; e < 2 * NM; e += kT) {
+    const int which = e / NM, i = e % NM;
+    Real acc = 0;
+    if (i >= 1 && i < nm)
+      for (int j = i; j < nm; ++j)
+        acc = fma(w.W[i * WS + j], which == 0 ? w.dxw[j] : w.dxw[nm + j - 1], acc);
+    w.duv[which][i] = acc;
+  }
+  __syncthreads();
+  if (wid < 2) {
+    Real c = 0;
+    for (int i = 1 + lane; i < nm; i += 32) c = fma(-w.mupsi[i], w.duv[wid][i], c);
+    c = warp_sum(c);
+    if (lane == 0) w.duv[wid][0] = c + (wid == 0 ? w.dxw[0] : (Real)0);
+  } else if (wid == 2) {
+    // norms of the step and of the updated iterate
+    float dn = 0.0f, xn = 0.0f;
+    for (int j = lane; j < n; j += 32) {
+      const Real xv = w.xw[j] + w.dxw[j];
+      w.xw[j] = xv;
+      dn += (float)(w.dxw[j] * w.dxw[j]);
+      xn += (float)(xv * xv);
+    }
+    dn = warp_sum(dn);
+    xn = warp_sum(xn);
+    if (lane == 0) w.fscal[0] = xn > 0.0f ? sqrtf(dn / xn) : 0.0f;
+  }
+  __syncthreads();
+  for (int e = tid; e < 2 * NM; e += kT) {
+    const int which = e / NM, i = e % NM;
+    if (sizeof(Real) == 8) {
+      w.uv[which][i] += (double)w.duv[which][i];
+    } else {
+      df_add(w.uvhi[which][i], w.uvlo[which][i], (float)w.duv[which][i]);
+    }
+  }
+  __syncthreads();
+  return w.fscal[0];
+}
 
 // Tensor-core Gram X^T X of up to NPAD columns over 128-sample chunks: each
 // thread stages its sample's row (column j at row j of the K-major tile,
@@ -898,79 +937,144 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
       tg.finish(naug, w.G, w.stage);
     }
 
-    // ---------------- phase 4: equilibrate, factor, first solve
-    // The leading n x n block of G (stride naug) is the normal matrix and
-    // column n holds A^T b; the scaled block is compacted to stride n through
-    // `stage` and factored by warp 0.
+    // ---------------- phase 4: equilibrate and sweep
+    // S = D G D (D = diag(G_jj^-1/2) on the n normal columns, 1 on the
+    // right-hand side), in place in G (stride naug).  Sweeping the pivots
+    // 0..n-1 (the sweep operator of least-squares regression: Gauss-Jordan
+    // on the SPD normal matrix) leaves -S^-1 in the n x n block and the
+    // least-squares solution in column n.  A pivot <= drop_tol (relative to
+    // the unit equilibrated diagonal) is not swept: its column is dropped
+    // (rank deficiency).  Afterwards G holds Q = D S^-1 D on the kept columns
+    // (0 elsewhere), the refinement's preconditioner, and dxw the first step.
     {
-      for (int j = tid; j < n; j += kT) {
-        const Real dg = w.G[j * naug + j];
-        w.scl[j] = dg > 0 ? rsqrt_pos<Real>(dg) : (Real)0;
-        w.gvec[j] = w.G[j * naug + n];
+      const int N1 = naug;
+      for (int j = tid; j < N1; j += kT) {
+        const Real dg = w.G[j * N1 + j];
+        w.scl[j] = (j == n) ? (Real)1 : (dg > 0 ? rsqrt_pos<Real>(dg) : (Real)0);
       }
       __syncthreads();
-      for (int e = tid; e < n * n; e += kT) {
-        const int i = e / n, j = e % n;
-        w.stage[e] = w.G[i * naug + j] * w.scl[i] * w.scl[j];
+      // the upper triangle (i <= j), EPT entries per thread, decoded once
+      constexpr int EPT = (NAUG * (NAUG + 1) / 2 + kT - 1) / kT;
+      const int ntri = N1 * (N1 + 1) / 2;
+      int ent[EPT];   // i << 16 | j, or -1
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        const int e = tid + kT * q;
+        if (e < ntri) {
+          // e = i N1 - i (i - 1) / 2 + (j - i): row i holds N1 - i entries
+          int i = (int)((2.0f * N1 + 1.0f - sqrtf((2.0f * N1 + 1.0f) * (2.0f * N1 + 1.0f) - 8.0f * e)) * 0.5f);
+          while (i > 0 && i * N1 - i * (i - 1) / 2 > e) --i;
+          while ((i + 1) * N1 - (i + 1) * i / 2 <= e) ++i;
+          const int j = i + (e - (i * N1 - i * (i - 1) / 2));
+          ent[q] = (i << 16) | j;
+        } else {
+          ent[q] = -1;
+        }
       }
+#pragma unroll
+      for (int q = 0; q < EPT; ++q)
+        if (ent[q] >= 0) {
+          const int i = ent[q] >> 16, j = ent[q] & 0xFFFF;
+          const Real v = w.G[i * N1 + j] * w.scl[i] * w.scl[j];
+          w.G[i * N1 + j] = v;
+          if (i == 0) w.rowb[0][j] = v;
+        }
       __syncthreads();
-      for (int e = tid; e < n * n; e += kT) w.G[e] = w.stage[e];
-      for (int j = tid; j < n; j += kT) w.gvec[j] *= w.scl[j];
-      __syncthreads();
-      cta_chol<Real, kT>(w.G, n, n, (Real)a.drop_tol, w.invd, &w.keep_cnt);
-      if (wid == 0) {
-        warp_solve<Real>(w.G, n, n, w.invd, w.gvec);
-        for (int j = lane; j < n; j += 32) w.xsol[j] = (double)(w.gvec[j] * w.scl[j]);
+      int kept = 0;
+      for (int k = 0; k < n; ++k) {
+        const Real *rk = w.rowb[k & 1];
+        Real *rn = w.rowb[(k + 1) & 1];
+        const Real piv = rk[k];
+        const bool keep = piv > (Real)a.drop_tol;
+        kept += keep;
+        const Real ip = keep ? (Real)1 / piv : (Real)0;
+        Real v[EPT];
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+          const int i = ent[q] >> 16, j = ent[q] & 0xFFFF;
+          v[q] = ent[q] >= 0 ? w.G[i * N1 + j] : (Real)0;
+        }
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+          if (ent[q] < 0) continue;
+          const int i = ent[q] >> 16, j = ent[q] & 0xFFFF;
+          const bool on_k = (i == k) || (j == k);
+          if (keep && !on_k) {
+            v[q] = fma(-rk[i] * ip, rk[j], v[q]);
+            w.G[i * N1 + j] = v[q];
+          }
+          if (!(keep && on_k)) {
+            if (i == k + 1) rn[j] = v[q];
+            if (j == k + 1) rn[i] = v[q];
+          }
+        }
+        // row and column k: S'_kx = rk[x] / piv, S'_kk = -1 / piv
+        if (keep && tid < N1) {
+          const int x = tid;
+          const Real vk = (x == k) ? -ip : rk[x] * ip;
+          w.G[min(x, k) * N1 + max(x, k)] = vk;
+          if (x == k + 1) rn[k] = vk;
+        }
+        if (tid == 0) w.invd[k] = keep ? (Real)1 : (Real)0;
+        __syncthreads();
       }
+      // Q = -D S D on the kept columns, both triangles; the first step
+#pragma unroll
+      for (int q = 0; q < EPT; ++q)
+        if (ent[q] >= 0) {
+          const int i = ent[q] >> 16, j = ent[q] & 0xFFFF;
+          const Real vv = w.G[i * N1 + j];
+          const Real si = w.invd[i] * w.scl[i];
+          if (j < n) {
+            const Real qv = -vv * si * w.invd[j] * w.scl[j];
+            w.G[i * N1 + j] = qv;
+            w.G[j * N1 + i] = qv;
+          } else if (j == n && i < n) {
+            w.dxw[i] = vv * si;
+          }
+        }
+      if (tid == 0) w.keep_cnt = kept;
+      // the iterate starts at 0: (c_p, u) = 0, (c_q, v) = (1, 0)
+      for (int e = tid; e < 2 * NM; e += kT) {
+        const int which = e / NM, i = e % NM;
+        const float c = (which == 1 && i == 0) ? 1.0f : 0.0f;
+        w.uvhi[which][i] = c;
+        w.uvlo[which][i] = 0.0f;
+        w.uv[which][i] = c;
+      }
+      for (int j = tid; j < NAUG; j += kT) w.xw[j] = 0;
       __syncthreads();
+      (void)apply_step<Real, NM, WS>(w, nm, n);
     }
 
     // ---------------- phase 5: refinement from the samples.
-    // With u = W x_num, v = W x_den (index 1..nm-1),
-    //   c_p = x_num[0] - mu.u, c_q = 1 - mu.v,
-    // the fit's p and q at a sample are p = c_p + psi.u, q = c_q + psi.v, and
-    // the design residual is r = w (y q - p).  The normal-equation residual
-    // g = A^T r follows from H_i = sum (w r) psi_i, K_i = sum (w y r) psi_i:
+    // The iterate is the function pair p = c_p + psi.u, q = c_q + psi.v in
+    // the unwhitened basis; each pass computes at every sample the design
+    // residual r = w (y q - p) (plain FP32, then Ogita-Rump-Oishi Dot2
+    // against the head + tail iterate once the steps fall below 1e-4
+    // relative; FP64 on the FP64 path), the objective sum r^2, whether
+    // q > 0, and H_i = sum (w r) psi_i, K_i = sum (w y r) psi_i.  The
+    // normal-equation residual in the design basis is
     //   g_num_0 = H_0, g_num_j = sum_{i<=j} W_ij (H_i - mu_i H_0),
     //   g_den_j = -sum_{i<=j} W_ij (K_i - mu_i K_0),
-    // so the passes work in the unwhitened basis.  Each pass also returns the
-    // objective sum r^2 (a step that increases it beyond its rounding level is
-    // undone) and whether q > 0 at every sample.  Residuals are plain FP32
-    // until the corrections fall below 1e-4 relative, then compensated (Dot2).
+    // and the step dx = Q g.  A step that raises the objective beyond its
+    // rounding level is undone and the refinement stops.
     int flags = (w.keep_cnt < n) ? RP_FIT_RANK_DEFICIENT : 0;
     float prev_rel = INFINITY, obj_prev = INFINITY, obj_drop = INFINITY;
     bool compensated = sizeof(Real) == 8, done = false;
     int pole_prev = 0, it = 0;
+    float omega = 1.0f;   // step length (halved after an objective increase)
+    constexpr bool kRegAcc = sizeof(Real) == 4 && DMAX <= 3;
+    constexpr int VP = ((2 * NM + 2 + 15) / 16) * 16;   // register accumulators
     const int hk_groups = max(1, kT / nm);
     for (;; ++it) {
       const bool update = it < a.max_refine && !done;
-      // u, v, c_p, c_q (FP64) and their float splits
-      for (int e = tid; e < 2 * NM; e += kT) {
-        const int which = e / NM, i2 = e % NM;
-        double acc = 0.0;
-        if (i2 >= 1 && i2 < nm)
-          for (int j2 = i2; j2 < nm; ++j2)
-            acc += (double)w.W[i2 * WS + j2] * (which == 0 ? w.xsol[j2] : w.xsol[nm + j2 - 1]);
-        w.uv[which][i2] = acc;
-      }
-      __syncthreads();
-      if (tid < 2) {
-        double c = tid == 0 ? w.xsol[0] : 1.0;
-        for (int i2 = 1; i2 < nm; ++i2) c -= (double)w.mupsi[i2] * w.uv[tid][i2];
-        w.uv[tid][0] = c;
-      }
-      __syncthreads();
-      for (int e = tid; e < 2 * NM; e += kT) {
-        const int which = e / NM, i2 = e % NM;
-        const double v = w.uv[which][i2];
-        const float h = (float)v;
-        w.uvhi[which][i2] = h;
-        w.uvlo[which][i2] = (float)(v - (double)h);
-      }
-      __syncthreads();
-      Real hk0 = 0, hk1 = 0;
+      Real hk0 = 0, hk1 = 0;    // staged path: this thread's column partials
       float obj = 0.0f;
       int pole = 0;
+      float acc[kRegAcc ? VP : 1];
+#pragma unroll
+      for (int j = 0; j < (kRegAcc ? VP : 1); ++j) acc[j] = 0.0f;
       for (int base = 0; base < m; base += kT) {
         const int cnt = min(kT, m - base);
         if (tid < cnt) {
@@ -997,7 +1101,7 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
             pole |= !(qf > 0.0f);
             if (compensated) {
               // e = y q - p = sum_j (y psi_j) v_j - psi_j u_j (psi_0 = 1):
-              // Dot2 against the split u, v, two independent chains
+              // Dot2 against the head + tail iterate, two independent chains
               float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
 #pragma unroll
               for (int j2 = 0; j2 < NM; ++j2) {
@@ -1024,7 +1128,16 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
             }
           }
           obj += (float)(r * r);
-          if (update) {
+          if constexpr (kRegAcc) {
+            if (update) {
+              const float rn = (float)(wt * r), rd = (float)(wt * yy * r);
+#pragma unroll
+              for (int j2 = 0; j2 < NM; ++j2) {
+                acc[j2] = fmaf(rn, (float)psi[j2], acc[j2]);
+                acc[NM + j2] = fmaf(rd, (float)psi[j2], acc[NM + j2]);
+              }
+            }
+          } else if (update) {
             Real *row = w.stage + tid * LDS;
 #pragma unroll
             for (int j2 = 0; j2 < NM; ++j2) row[j2] = psi[j2];
@@ -1032,57 +1145,106 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
             w.rbuf[1][tid] = wt * yy * r;
           }
         }
-        if (update) {
-          __syncthreads();
-          if (tid < nm * hk_groups) {
-            const int j2 = tid % nm, g = tid / nm;
-            Real pn = 0, pd = 0;
-            for (int s2 = g; s2 < cnt; s2 += hk_groups) {
-              const Real bv = w.stage[s2 * LDS + j2];
-              pn = fma(bv, w.rbuf[0][s2], pn);
-              pd = fma(bv, w.rbuf[1][s2], pd);
+        if constexpr (!kRegAcc) {
+          if (update) {
+            __syncthreads();
+            if (tid < nm * hk_groups) {
+              const int j2 = tid % nm, g = tid / nm;
+              Real pn = 0, pd = 0;
+              for (int s2 = g; s2 < cnt; s2 += hk_groups) {
+                const Real bv = w.stage[s2 * LDS + j2];
+                pn = fma(bv, w.rbuf[0][s2], pn);
+                pd = fma(bv, w.rbuf[1][s2], pd);
+              }
+              hk0 += pn;
+              hk1 += pd;
             }
-            hk0 += pn;
-            hk1 += pd;
+            __syncthreads();
           }
-          __syncthreads();
         }
       }
-      pole = __syncthreads_or(pole);
-      obj = block_sum_f(w, obj, 8);
+      // block totals: objective, pole, and (when stepping) H and K
+      if constexpr (kRegAcc) {
+        acc[2 * NM] = obj;
+        acc[2 * NM + 1] = pole ? 1.0f : 0.0f;
+        warp_reduce_scatter<VP>(acc);
+        if ((lane & 1) == 0) {
+          const int b = rs_base<VP>(lane);
+#pragma unroll
+          for (int q = 0; q < VP / 16; ++q) w.redv[wid][b + q] = acc[q];
+        }
+        __syncthreads();
+        obj = w.redv[0][2 * NM] + w.redv[1][2 * NM] + w.redv[2][2 * NM] + w.redv[3][2 * NM];
+        pole = (w.redv[0][2 * NM + 1] + w.redv[1][2 * NM + 1] + w.redv[2][2 * NM + 1] +
+                w.redv[3][2 * NM + 1]) > 0.0f;
+      } else {
+        pole = __syncthreads_or(pole);
+        obj = block_sum_f(w, obj, 8);
+      }
       __syncthreads();
       const bool worse = it > 0 && obj > obj_prev * (compensated ? 1.00001f : 1.0001f);
       if (worse) {
-        // the last step increased the objective: undo it
-        for (int j2 = tid; j2 < n; j2 += kT) w.xsol[j2] = w.xprev[j2];
-        pole = pole_prev;
-        obj_drop = 0.0f;
+        // the last step increased the objective: undo it, then retry it at
+        // half length (a preconditioner that overestimates curvature in some
+        // direction makes the full step overshoot); the halving persists
+        // for the fit's later steps; below 1/16 the refinement stops
+        for (int e = tid; e < 2 * NM; e += kT) {
+          const int which = e / NM, i2 = e % NM;
+          w.uv[which][i2] = w.uvp[which][i2];
+          w.uvhi[which][i2] = w.uvphi[which][i2];
+          w.uvlo[which][i2] = w.uvplo[which][i2];
+        }
+        for (int j2 = tid; j2 < n; j2 += kT) w.xw[j2] = w.xwp[j2];
+        omega *= 0.5f;
+        if (omega < 0.0625f || it >= a.max_refine) {
+          pole = pole_prev;
+          obj_drop = 0.0f;
+          __syncthreads();
+          break;
+        }
+        for (int j2 = tid; j2 < n; j2 += kT) w.dxw[j2] *= (Real)0.5;
+        __syncthreads();
+        (void)apply_step<Real, NM, WS>(w, nm, n);
+        continue;
+      }
+      if (it > 0) obj_drop = (obj_prev - obj) / fmaxf(obj_prev, 1e-30f);
+      for (int e = tid; e < 2 * NM; e += kT) {
+        const int which = e / NM, i2 = e % NM;
+        w.uvp[which][i2] = w.uv[which][i2];
+        w.uvphi[which][i2] = w.uvhi[which][i2];
+        w.uvplo[which][i2] = w.uvlo[which][i2];
+      }
+      for (int j2 = tid; j2 < n; j2 += kT) w.xwp[j2] = w.xw[j2];
+      obj_prev = obj;
+      pole_prev = pole;
+      if (!update) {
         __syncthreads();
         break;
       }
-      if (it > 0) obj_drop = (obj_prev - obj) / fmaxf(obj_prev, 1e-30f);
-      for (int j2 = tid; j2 < n; j2 += kT) w.xprev[j2] = w.xsol[j2];
-      obj_prev = obj;
-      pole_prev = pole;
-      __syncthreads();
-      if (!update) break;
-      // H, K: sum the sample groups
-      if (tid < nm * hk_groups) {
-        w.stage[tid] = hk0;
-        w.stage[kT + tid] = hk1;
-      }
-      __syncthreads();
-      if (tid < nm) {
-        Real h = 0, k2 = 0;
-        for (int g = 0; g < hk_groups; ++g) {
-          h += w.stage[g * nm + tid];
-          k2 += w.stage[kT + g * nm + tid];
+      // H, K
+      if constexpr (kRegAcc) {
+        if (tid < 2 * NM) {
+          const Real v = w.redv[0][tid] + w.redv[1][tid] + w.redv[2][tid] + w.redv[3][tid];
+          w.HK[tid / NM][tid % NM] = v;
         }
-        w.HK[0][tid] = h;
-        w.HK[1][tid] = k2;
+      } else {
+        if (tid < nm * hk_groups) {
+          w.stage[tid] = hk0;
+          w.stage[kT + tid] = hk1;
+        }
+        __syncthreads();
+        if (tid < nm) {
+          Real h = 0, k2 = 0;
+          for (int g = 0; g < hk_groups; ++g) {
+            h += w.stage[g * nm + tid];
+            k2 += w.stage[kT + g * nm + tid];
+          }
+          w.HK[0][tid] = h;
+          w.HK[1][tid] = k2;
+        }
       }
       __syncthreads();
-      // g, scaled for the factored (equilibrated) system
+      // g, then the step dx = Q g
       for (int e = tid; e < n; e += kT) {
         Real g;
         if (e < nm) {
@@ -1090,32 +1252,24 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
             g = w.HK[0][0];
           } else {
             g = 0;
-            for (int i2 = 1; i2 <= e; ++i2) g += w.W[i2 * WS + e] * (w.HK[0][i2] - w.mupsi[i2] * w.HK[0][0]);
+            for (int i2 = 1; i2 <= e; ++i2) g = fma(w.W[i2 * WS + e], w.HK[0][i2] - w.mupsi[i2] * w.HK[0][0], g);
           }
         } else {
           const int jd = e - nm + 1;
           g = 0;
-          for (int i2 = 1; i2 <= jd; ++i2) g -= w.W[i2 * WS + jd] * (w.HK[1][i2] - w.mupsi[i2] * w.HK[1][0]);
+          for (int i2 = 1; i2 <= jd; ++i2) g = fma(-w.W[i2 * WS + jd], w.HK[1][i2] - w.mupsi[i2] * w.HK[1][0], g);
         }
-        w.gvec[e] = g * w.scl[e];
+        w.gvec[e] = g;
       }
       __syncthreads();
-      if (wid == 0) {
-        warp_solve<Real>(w.G, n, n, w.invd, w.gvec);
-        float dn = 0, xn = 0;
-        for (int j2 = lane; j2 < n; j2 += 32) {
-          const double dx = (double)(w.gvec[j2] * w.scl[j2]);
-          const double xv = w.xsol[j2] + dx;
-          w.xsol[j2] = xv;
-          dn += (float)(dx * dx);
-          xn += (float)(xv * xv);
-        }
-        dn = warp_sum(dn);
-        xn = warp_sum(xn);
-        if (lane == 0) w.fscal[0] = xn > 0.0f ? sqrtf(dn / xn) : 0.0f;
+      for (int e = tid; e < n; e += kT) {
+        Real z = 0;
+        const Real *qrow = w.G + e * naug;
+        for (int k2 = 0; k2 < n; ++k2) z = fma(qrow[k2], w.gvec[k2], z);
+        w.dxw[e] = z * (Real)omega;
       }
       __syncthreads();
-      const float rel = w.fscal[0];
+      const float rel = apply_step<Real, NM, WS>(w, nm, n);
       const bool was_compensated = compensated;
       if (!compensated && rel < 1e-4f) compensated = true;
       // stop at tol, or once compensated corrections stop shrinking (the
@@ -1139,16 +1293,12 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
     {
       double *cpsi = reinterpret_cast<double *>(w.stage);   // [2][kMaxNm]
       double *P = cpsi + 2 * kMaxNm;                          // [3][5][5]
+      // the iterate's coefficients on Psi (index 0: the constants c_p, c_q)
       for (int e = tid; e < 2 * nm; e += kT) {
         const int which = e / nm, i = e % nm;   // 0 numerator, 1 denominator
-        if (i >= 1) {
-          double u = 0;
-          for (int j = i; j < nm; ++j) {
-            const double cj = which == 0 ? w.xsol[j] : w.xsol[nm + j - 1];
-            u += (double)w.W[i * WS + j] * cj;
-          }
-          cpsi[which * kMaxNm + i] = u;
-        }
+        cpsi[which * kMaxNm + i] = sizeof(Real) == 8
+                                       ? w.uv[which][i]
+                                       : (double)w.uvhi[which][i] + (double)w.uvlo[which][i];
       }
       if (tid >= 96 && tid < 96 + 3 * (kMaxDeg + 1)) {
         // Q_k(u), u = (x' - mu) isg, as a polynomial in x'
@@ -1172,12 +1322,6 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
           }
         }
         for (int i2 = 0; i2 <= kMaxDeg; ++i2) P[(v * (kMaxDeg + 1) + k) * (kMaxDeg + 1) + i2] = out[i2];
-      }
-      __syncthreads();
-      if (tid < 2) {
-        double c0 = tid == 0 ? w.xsol[0] : 1.0;
-        for (int i = 1; i < nm; ++i) c0 -= (double)w.mupsi[i] * cpsi[tid * kMaxNm + i];
-        cpsi[tid * kMaxNm] = c0;
       }
       __syncthreads();
       for (int e = tid; e < 2 * nm; e += kT) {

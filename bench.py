@@ -34,6 +34,23 @@ WORKLOAD = ("batched fit 1024 kernels x 8 metrics, 512 samples, deg<=3 (TF32-cla
             "path: fp32), then MWP-CWP search 1e6 queries x 66 configs")
 
 
+# DRAM bytes per fit of the fit kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of fit_kernel<float, 3, 0>,
+# 2048 fits of 512 samples; traffic scales with the fit count), valid only
+# for the kernel sources they were taken on (SHA-256 of the files below).
+FIT_TRAFFIC = {"sources_sha256": None, "bytes_per_fit": None}
+FIT_SOURCES = ("paper_1906_00142_gb300/csrc/rp_fit.cu", "paper_1906_00142_gb300/csrc/rp_tc.cuh",
+               "paper_1906_00142_gb300/csrc/rp_internal.cuh")
+
+
+def fit_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in FIT_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -215,6 +232,80 @@ def run_reference(args):
 
 # --------------------------------------------------------------------------
 
+def _timed(fn, reps, flush, stream):
+    """Mean device time (ms) of fn() over reps calls, L2 flushed before each."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.mean(ts)
+
+
+def extra_measurements(rp, args, inst, x, y, off, deg, mm, gd, q, fit_out, prog, s_out, flush,
+                       stream, step, fit_ms, search_ms, step_ms):
+    """Fit-only rates per precision; the plain form (FP64 fits and single
+    queries, one per launch, no tensor cores) on a sample, and the batched
+    form's speedup over it; the step replayed from a CUDA graph."""
+    import torch
+    F = N_KERNELS * N_METRICS
+    out = {}
+    rates = {}
+    for prec in ("fp32", "tf32", "tf32x3", "fp64"):
+        fn = lambda: rp.rp_fit(x, y, off, DEGREE, precision=prec, max_refine=8, tol=args.tol,
+                               degrees=deg, out=fit_out, stream=stream)
+        fn()
+        rates[prec] = F / (_timed(fn, 3, flush, stream) / 1e3)
+    out["fit_only_fits_per_s"] = rates
+    # plain form: one FP64 fit per launch over 64 fits, one query per launch
+    # over 2000 queries (launch-bound; rates scale to any count)
+    n_pf, n_pq = 64, 2000
+    offs = torch.stack([off[:-1], off[1:]], 1).contiguous()
+    pf_out = {k: v for k, v in fit_out.items()}
+
+    def plain_fits():
+        for f in range(n_pf):
+            rp.rp_fit(x, y, offs[f], DEGREE, precision="fp64", max_refine=8, tol=args.tol,
+                      degrees=deg[f:f + 1], stream=stream,
+                      out={k: v[f:f + 1] for k, v in pf_out.items()})
+
+    def plain_queries():
+        for i in range(n_pq):
+            rp.rp_eval_search(prog, N_KERNELS, DEGREE, q[i:i + 1], stream=stream,
+                              out={k: v[i:i + 1] for k, v in s_out.items()})
+    plain_fits()
+    plain_queries()
+    t_pf = _timed(plain_fits, 2, flush, stream)
+    t_pq = _timed(plain_queries, 2, flush, stream)
+    plain = {"fits_per_s": n_pf / (t_pf / 1e3), "queries_per_s": n_pq / (t_pq / 1e3),
+             "sample": f"{n_pf} FP64 fits and {n_pq} queries, one per launch"}
+    out["plain"] = plain
+    out["speedup_vs_plain"] = {"fit": rates["fp32"] / plain["fits_per_s"],
+                               "search": (N_QUERIES / (search_ms / 1e3)) / plain["queries_per_s"]}
+    # the whole step captured in one CUDA graph
+    try:
+        s2 = torch.cuda.Stream()
+        s2.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s2):
+            step(st=s2)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s2):
+            step(st=s2)
+        g.replay()
+        torch.cuda.synchronize()
+        out["graph_ms_per_step"] = _timed(lambda: g.replay(), 5, flush, torch.cuda.current_stream())
+    except Exception as e:   # reported, never silently replaced
+        out["graph_ms_per_step"] = None
+        out["graph_error"] = str(e).splitlines()[0]
+    return out
+
+
 def main():
     global N_KERNELS, N_QUERIES
     ap = argparse.ArgumentParser()
@@ -231,6 +322,8 @@ def main():
     ap.add_argument("--queries", type=int, default=N_QUERIES)
     ap.add_argument("--only", default="all", choices=["all", "fit", "search"],
                     help="profiling captures: launch only one phase per step")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the per-precision, plain-form and graph measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -269,23 +362,24 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(ev=None):
+    def step(ev=None, st=None):
+        st = stream if st is None else st
         if ev:
-            ev[0].record(stream)
+            ev[0].record(st)
         if args.only in ("all", "fit"):
             rp.rp_fit(x, y, off, DEGREE, precision=args.precision, max_refine=8, tol=args.tol,
-                      degrees=deg, out=fit_out, stream=stream)
+                      degrees=deg, out=fit_out, stream=st)
         if ev:
-            ev[1].record(stream)
+            ev[1].record(st)
         if args.only in ("all", "fit"):
             rp.rp_program_pack(fit_out["coef"], fit_out["box"], deg, mm, gd, DEGREE, program=prog,
-                               stream=stream)
+                               stream=st)
         if ev:
-            ev[2].record(stream)
+            ev[2].record(st)
         if args.only in ("all", "search"):
-            rp.rp_eval_search(prog, N_KERNELS, DEGREE, q, out=s_out, stream=stream)
+            rp.rp_eval_search(prog, N_KERNELS, DEGREE, q, out=s_out, stream=st)
         if ev:
-            ev[3].record(stream)
+            ev[3].record(st)
 
     if args.only == "search":   # program from one fit + pack, outside the timed steps
         rp.rp_fit(x, y, off, DEGREE, precision=args.precision, max_refine=8, tol=args.tol,
@@ -367,6 +461,12 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = float(t.item())
 
+    extra = {}
+    if args.only == "all" and not args.no_extras:
+        extra = extra_measurements(rp, args, inst, x, y, off, deg, mm, gd, q, fit_out, prog, s_out,
+                                   flush, stream, step, statistics.mean(fit_ms),
+                                   statistics.mean(search_ms), ms_per_step)
+
     if rank == 0:
         pk, src = peaks()
         sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -374,8 +474,13 @@ def main():
         alu_peak = fp32_peak_tflops(sm_count, pk.get("sm_max_mhz", 2070.0))
         if fit_avg >= search_avg:
             ach = F * fit_flops_per_fit(M_SAMPLES, DEGREE) / (fit_avg / 1e3) / 1e12
+            traffic = None
+            if (FIT_TRAFFIC["bytes_per_fit"] is not None and args.precision == "fp32"
+                    and FIT_TRAFFIC["sources_sha256"] == fit_sources_sha256()):
+                traffic = FIT_TRAFFIC["bytes_per_fit"] * F
             roof = {"kernel": "rp_fit", "bound": "alu", "achieved": ach, "peak": alu_peak,
-                    "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
+                    "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": traffic,
+                    "algorithmic_bytes": F * (16 * M_SAMPLES + 896),
                     "peak_source": f"FP32 lanes x SM clock ({src} sm_max_mhz)"}
         else:
             ach = N_QUERIES * search_flops_per_query(DEGREE) / (search_avg / 1e3) / 1e12
@@ -397,6 +502,7 @@ def main():
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
                 "gpu_launches": (3 if args.only == "all" else 2 if args.only == "fit" else 1) * args.steps,
                 "clocks": clk}
+        line.update(extra)
         if ws == 1 and not args.no_cpu_baseline and args.only == "all":
             r = oracle_rates(inst, q_np, gd_np, budget_s=20.0)
             line["cpu_baseline"] = {"value": F / r["step_s"], "unit": "fits/s", "cores": r["cores"],

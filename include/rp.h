@@ -200,33 +200,37 @@ int rp_eval_search(const void *program, int64_t num_kernels, int32_t degree,
 /*
  * rp_relmse_fwd -- per-fit mean squared relative error
  *   L_f = (1/m) sum_i ((p(x_i)/q(x_i) - y_i) / y_i)^2
- * of float coefficients coef32 [F][70] (layout as rp_fit) with the fits'
- * boxes (double[F][6]) on the fits' samples (x, y, fit_off as rp_fit),
- * written to loss float[F].  FP32 arithmetic.  degrees: int8[F] device.
+ * of the coefficients coef double[F][70] (layout and precision of rp_fit's
+ * output) with the fits' boxes (double[F][6]) on the fits' samples (x, y,
+ * fit_off as rp_fit), written to loss float[F].  p and q are evaluated in
+ * FP64 (fitted monomial coefficients cancel by up to ~1e9); residuals and
+ * sums in FP32.  degrees: int8[F] device.
  */
 int rp_relmse_fwd(int64_t num_fits, int64_t num_samples, const float *x, const float *y,
-                  const int64_t *fit_off, const int8_t *degrees, const float *coef32,
+                  const int64_t *fit_off, const int8_t *degrees, const double *coef,
                   const double *box, float *loss, void *stream);
 
 /*
- * rp_relmse_bwd -- gradient of sum_f g_f L_f with respect to coef32, given
+ * rp_relmse_bwd -- gradient of sum_f g_f L_f with respect to coef, given
  * g = grad_loss float[F]; written to grad float[F][70]:
  *   dL/dalpha_j = (2/m) sum r_i phi_j(x_i) / (y_i q_i)
  *   dL/dbeta_j  = -(2/m) sum r_i p_i phi_j(x_i) / (y_i q_i^2)   (j >= 1)
  * with beta_0 held fixed (its gradient is written as 0).
  */
 int rp_relmse_bwd(int64_t num_fits, int64_t num_samples, const float *x, const float *y,
-                  const int64_t *fit_off, const int8_t *degrees, const float *coef32,
+                  const int64_t *fit_off, const int8_t *degrees, const double *coef,
                   const double *box, const float *grad_loss, float *grad, void *stream);
 
 /*
  * rp_adam_step -- one Adam update (Kingma & Ba 2015) of n parameters in
  * place: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
  * p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).  Entries with
- * mask[i] == 0 are left unchanged.  All arrays float[n] on the device;
- * mask uint8[n] (may be NULL = all).  t >= 1.
+ * mask[i] == 0 are left unchanged.  param double[n] (the fitted
+ * coefficients; an FP32 copy could not hold steps below its rounding),
+ * grad, m, v float[n], mask uint8[n] (may be NULL = all), all on the device.
+ * t >= 1.
  */
-int rp_adam_step(int64_t n, float *param, const float *grad, float *m, float *v,
+int rp_adam_step(int64_t n, double *param, const float *grad, float *m, float *v,
                  const uint8_t *mask, int32_t t, float lr, float beta1, float beta2, float eps,
                  void *stream);
 

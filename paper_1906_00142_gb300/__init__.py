@@ -228,37 +228,37 @@ def rp_eval_search(program, num_kernels: int, degree: int, queries: torch.Tensor
     return out
 
 
-def rp_relmse_fwd(x, y, fit_off, degrees, coef32, box, loss=None, stream=None):
+def rp_relmse_fwd(x, y, fit_off, degrees, coef, box, loss=None, stream=None):
     lib = load_library()
     F = fit_off.numel() - 1
     if loss is None:
         loss = torch.empty(F, dtype=torch.float32, device=y.device)
     rc = lib.rp_relmse_fwd(F, y.numel(), _dev(x, torch.float32, "x"), _dev(y, torch.float32, "y"),
                            _dev(fit_off, torch.int64, "fit_off"), _dev(degrees, torch.int8, "degrees"),
-                           _dev(coef32, torch.float32, "coef32"), _dev(box, torch.float64, "box"),
+                           _dev(coef, torch.float64, "coef"), _dev(box, torch.float64, "box"),
                            _dev(loss, torch.float32, "loss"), _stream(stream))
     _check(rc, "rp_relmse_fwd")
     return loss
 
 
-def rp_relmse_bwd(x, y, fit_off, degrees, coef32, box, grad_loss, grad=None, stream=None):
+def rp_relmse_bwd(x, y, fit_off, degrees, coef, box, grad_loss, grad=None, stream=None):
     lib = load_library()
     F = fit_off.numel() - 1
     if grad is None:
         grad = torch.empty((F, RP_COEF_STRIDE), dtype=torch.float32, device=y.device)
     rc = lib.rp_relmse_bwd(F, y.numel(), _dev(x, torch.float32, "x"), _dev(y, torch.float32, "y"),
                            _dev(fit_off, torch.int64, "fit_off"), _dev(degrees, torch.int8, "degrees"),
-                           _dev(coef32, torch.float32, "coef32"), _dev(box, torch.float64, "box"),
+                           _dev(coef, torch.float64, "coef"), _dev(box, torch.float64, "box"),
                            _dev(grad_loss, torch.float32, "grad_loss"),
                            _dev(grad, torch.float32, "grad"), _stream(stream))
     _check(rc, "rp_relmse_bwd")
     return grad
 
 
-def rp_adam_step(param, grad, m, v, t: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, mask=None,
+def rp_adam_step(param, grad, m, v, t: int, lr=1e-6, beta1=0.9, beta2=0.999, eps=1e-8, mask=None,
                  stream=None):
     lib = load_library()
-    rc = lib.rp_adam_step(param.numel(), _dev(param, torch.float32, "param"),
+    rc = lib.rp_adam_step(param.numel(), _dev(param, torch.float64, "param"),
                           _dev(grad, torch.float32, "grad"), _dev(m, torch.float32, "m"),
                           _dev(v, torch.float32, "v"), _ptr_or_null(mask, torch.uint8, "mask"),
                           int(t), float(lr), float(beta1), float(beta2), float(eps), _stream(stream))
@@ -266,20 +266,21 @@ def rp_adam_step(param, grad, m, v, t: int, lr=1e-3, beta1=0.9, beta2=0.999, eps
 
 
 class RelMSE(torch.autograd.Function):
-    """Per-fit mean squared relative error of coef32 with a hand-written
-    CUDA backward (rp_relmse_fwd / rp_relmse_bwd)."""
+    """Per-fit mean squared relative error of the FP64 coefficients coef
+    [F, 70] with a hand-written CUDA backward (rp_relmse_fwd /
+    rp_relmse_bwd); the gradient is computed in FP32 and returned as FP64."""
 
     @staticmethod
-    def forward(ctx, coef32, x, y, fit_off, degrees, box):
-        ctx.save_for_backward(coef32, x, y, fit_off, degrees, box)
-        return rp_relmse_fwd(x, y, fit_off, degrees, coef32.contiguous(), box)
+    def forward(ctx, coef, x, y, fit_off, degrees, box):
+        ctx.save_for_backward(coef, x, y, fit_off, degrees, box)
+        return rp_relmse_fwd(x, y, fit_off, degrees, coef.contiguous(), box)
 
     @staticmethod
     def backward(ctx, grad_loss):
-        coef32, x, y, fit_off, degrees, box = ctx.saved_tensors
-        g = rp_relmse_bwd(x, y, fit_off, degrees, coef32.contiguous(), box,
+        coef, x, y, fit_off, degrees, box = ctx.saved_tensors
+        g = rp_relmse_bwd(x, y, fit_off, degrees, coef.contiguous(), box,
                           grad_loss.contiguous().float())
-        return g, None, None, None, None, None
+        return g.double(), None, None, None, None, None
 
 
 def refine_mask(degrees: torch.Tensor) -> torch.Tensor:
@@ -293,21 +294,23 @@ def refine_mask(degrees: torch.Tensor) -> torch.Tensor:
     return torch.cat([num, den], 1).to(torch.uint8).contiguous()
 
 
-def refine_relmse(coef32, x, y, fit_off, degrees, box, steps=20, lr=1e-3, beta1=0.9,
+def refine_relmse(coef, x, y, fit_off, degrees, box, steps=20, lr=1e-6, beta1=0.9,
                   beta2=0.999, eps=1e-8, stream=None):
     """Adam on the mean squared relative error, using the CUDA forward and
-    backward kernels and the CUDA Adam update.  Updates coef32 in place and
-    returns the per-fit losses before and after."""
+    backward kernels and the CUDA Adam update.  Updates the FP64 coefficients
+    coef [F, 70] in place and returns the per-fit losses before and after.
+    The default step suits the fitted monomial coefficients, which cancel
+    heavily: Adam moves every coefficient by ~lr per step."""
     F = fit_off.numel() - 1
-    dev = coef32.device
-    m = torch.zeros_like(coef32)
-    v = torch.zeros_like(coef32)
+    dev = coef.device
+    m = torch.zeros(coef.shape, dtype=torch.float32, device=dev)
+    v = torch.zeros(coef.shape, dtype=torch.float32, device=dev)
     mask = refine_mask(degrees)
     ones = torch.ones(F, dtype=torch.float32, device=dev)
-    grad = torch.empty_like(coef32)
-    loss0 = rp_relmse_fwd(x, y, fit_off, degrees, coef32, box, stream=stream).clone()
+    grad = torch.empty(coef.shape, dtype=torch.float32, device=dev)
+    loss0 = rp_relmse_fwd(x, y, fit_off, degrees, coef, box, stream=stream).clone()
     for t in range(1, steps + 1):
-        rp_relmse_bwd(x, y, fit_off, degrees, coef32, box, ones, grad=grad, stream=stream)
-        rp_adam_step(coef32, grad, m, v, t, lr, beta1, beta2, eps, mask=mask, stream=stream)
-    loss1 = rp_relmse_fwd(x, y, fit_off, degrees, coef32, box, stream=stream)
+        rp_relmse_bwd(x, y, fit_off, degrees, coef, box, ones, grad=grad, stream=stream)
+        rp_adam_step(coef, grad, m, v, t, lr, beta1, beta2, eps, mask=mask, stream=stream)
+    loss1 = rp_relmse_fwd(x, y, fit_off, degrees, coef, box, stream=stream)
     return loss0, loss1

@@ -98,29 +98,29 @@ int rp_eval_search(const void *program, int64_t num_kernels, int32_t degree,
 }
 
 int rp_relmse_fwd(int64_t num_fits, int64_t num_samples, const float *x, const float *y,
-                  const int64_t *fit_off, const int8_t *degrees, const float *coef32,
+                  const int64_t *fit_off, const int8_t *degrees, const double *coef,
                   const double *box, float *loss, void *stream) {
   if (num_fits < 0 || num_samples < 0) return RP_ERR_INVALID_ARG;
   if (num_fits == 0) return RP_OK;
-  if (!x || !y || !fit_off || !degrees || !coef32 || !box || !loss) return RP_ERR_INVALID_ARG;
+  if (!x || !y || !fit_off || !degrees || !coef || !box || !loss) return RP_ERR_INVALID_ARG;
   if (!device_ok()) return RP_ERR_NO_DEVICE;
-  return from_cuda(rpk::launch_relmse(false, num_fits, num_samples, x, y, fit_off, degrees, coef32,
+  return from_cuda(rpk::launch_relmse(false, num_fits, num_samples, x, y, fit_off, degrees, coef,
                                       box, nullptr, loss, as_stream(stream)));
 }
 
 int rp_relmse_bwd(int64_t num_fits, int64_t num_samples, const float *x, const float *y,
-                  const int64_t *fit_off, const int8_t *degrees, const float *coef32,
+                  const int64_t *fit_off, const int8_t *degrees, const double *coef,
                   const double *box, const float *grad_loss, float *grad, void *stream) {
   if (num_fits < 0 || num_samples < 0) return RP_ERR_INVALID_ARG;
   if (num_fits == 0) return RP_OK;
-  if (!x || !y || !fit_off || !degrees || !coef32 || !box || !grad_loss || !grad)
+  if (!x || !y || !fit_off || !degrees || !coef || !box || !grad_loss || !grad)
     return RP_ERR_INVALID_ARG;
   if (!device_ok()) return RP_ERR_NO_DEVICE;
-  return from_cuda(rpk::launch_relmse(true, num_fits, num_samples, x, y, fit_off, degrees, coef32,
+  return from_cuda(rpk::launch_relmse(true, num_fits, num_samples, x, y, fit_off, degrees, coef,
                                       box, grad_loss, grad, as_stream(stream)));
 }
 
-int rp_adam_step(int64_t n, float *param, const float *grad, float *m, float *v,
+int rp_adam_step(int64_t n, double *param, const float *grad, float *m, float *v,
                  const uint8_t *mask, int32_t t, float lr, float beta1, float beta2, float eps,
                  void *stream) {
   if (n < 0 || t < 1 || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||

@@ -69,11 +69,11 @@ size_t fit_workspace_bytes(const rp_fit_desc &desc);
 bool fit_precision_supported(int precision);
 
 cudaError_t launch_relmse(bool backward, int64_t F, int64_t S, const float *x, const float *y,
-                          const int64_t *fit_off, const int8_t *degrees, const float *coef32,
+                          const int64_t *fit_off, const int8_t *degrees, const double *coef,
                           const double *box, const float *grad_loss, float *out,
                           cudaStream_t s);
 
-cudaError_t launch_adam(int64_t n, float *p, const float *g, float *m, float *v,
+cudaError_t launch_adam(int64_t n, double *p, const float *g, float *m, float *v,
                         const uint8_t *mask, int t, float lr, float b1, float b2, float eps,
                         cudaStream_t s);
 

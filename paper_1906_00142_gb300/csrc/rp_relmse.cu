@@ -5,9 +5,12 @@
 //   dL/dalpha_j = (2/m) sum_i r_i phi_j(x_i) / (y_i q_i)
 //   dL/dbeta_j  = -(2/m) sum_i r_i p_i phi_j(x_i) / (y_i q_i^2)   (j >= 1)
 // beta_0 is held fixed (it fixes the scale of the homogeneous pair p, q).
-// One CTA per fit, deterministic reductions.  p and q are evaluated in FP64
-// (the fitted monomial coefficients can cancel by 1e3-1e9); the residual,
-// loss and gradient sums are FP32.
+// One CTA per fit, deterministic reductions.  The coefficients are the
+// fit's FP64 output and p and q are evaluated in FP64 (the fitted monomial
+// coefficients can cancel by 1e3-1e9, so neither an FP32 copy of them nor an
+// FP32 evaluation keeps the residual's leading digits); the residual, loss
+// and gradient sums are FP32.  Adam updates the FP64 coefficients with FP32
+// moments.
 #include <math.h>
 #include <stdint.h>
 
@@ -37,7 +40,7 @@ Exps exps_table() {
 }
 
 struct RelShared {
-  float cf[kStride];
+  double cf[kStride];
   double scd[3], ofd[3];
   float red[kT / 32];
   float xn[kT][3];
@@ -55,7 +58,7 @@ __global__ void __launch_bounds__(kT) relmse_kernel(bool backward, int64_t F, in
                                                     const float *__restrict__ y,
                                                     const int64_t *__restrict__ off,
                                                     const int8_t *__restrict__ degs,
-                                                    const float *__restrict__ coef32,
+                                                    const double *__restrict__ coef,
                                                     const double *__restrict__ box,
                                                     const float *__restrict__ grad_loss,
                                                     float *__restrict__ out, Exps et) {
@@ -66,7 +69,7 @@ __global__ void __launch_bounds__(kT) relmse_kernel(bool backward, int64_t F, in
     const int m = (int)(off[f + 1] - b0);
     const int d = degs[f];
     const int nm = (d >= 1 && d <= kMaxDeg) ? num_monomials(d) : 0;
-    if (tid < kStride) sh.cf[tid] = coef32[f * kStride + tid];
+    if (tid < kStride) sh.cf[tid] = coef[f * kStride + tid];
     if (tid < 3) {
       const double lo = box[f * 6 + 2 * tid], hi = box[f * 6 + 2 * tid + 1];
       if (hi > lo) {
@@ -104,8 +107,8 @@ __global__ void __launch_bounds__(kT) relmse_kernel(bool backward, int64_t F, in
         double p = 0.0, q = 0.0;
         for (int j = 0; j < nm; ++j) {
           const double ph = pw[0][et.e[j][0]] * pw[1][et.e[j][1]] * pw[2][et.e[j][2]];
-          p = fma((double)sh.cf[j], ph, p);
-          q = fma((double)sh.cf[kHalf + j], ph, q);
+          p = fma(sh.cf[j], ph, p);
+          q = fma(sh.cf[kHalf + j], ph, q);
         }
         const float yy = y[i];
         const float r = (float)((p / q - (double)yy) / (double)yy);
@@ -162,7 +165,7 @@ __global__ void __launch_bounds__(kT) relmse_kernel(bool backward, int64_t F, in
   }
 }
 
-__global__ void adam_kernel(int64_t n, float *__restrict__ p, const float *__restrict__ g,
+__global__ void adam_kernel(int64_t n, double *__restrict__ p, const float *__restrict__ g,
                             float *__restrict__ m, float *__restrict__ v,
                             const uint8_t *__restrict__ mask, float lr, float b1, float b2,
                             float eps, float c1, float c2) {
@@ -174,26 +177,26 @@ __global__ void adam_kernel(int64_t n, float *__restrict__ p, const float *__res
     const float vi = fmaf(b2, v[i], (1.0f - b2) * gi * gi);
     m[i] = mi;
     v[i] = vi;
-    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] -= (double)(lr * (mi / c1) / (sqrtf(vi / c2) + eps));
   }
 }
 
 }  // namespace
 
 cudaError_t launch_relmse(bool backward, int64_t F, int64_t S, const float *x, const float *y,
-                          const int64_t *fit_off, const int8_t *degrees, const float *coef32,
+                          const int64_t *fit_off, const int8_t *degrees, const double *coef,
                           const double *box, const float *grad_loss, float *out,
                           cudaStream_t s) {
   if (F == 0) return cudaSuccess;
   static const Exps et = exps_table();
   int64_t grid = (int64_t)num_sms() * 4;
   if (grid > F) grid = F;
-  relmse_kernel<<<(unsigned)grid, kT, 0, s>>>(backward, F, S, x, y, fit_off, degrees, coef32, box,
+  relmse_kernel<<<(unsigned)grid, kT, 0, s>>>(backward, F, S, x, y, fit_off, degrees, coef, box,
                                               grad_loss, out, et);
   return cudaGetLastError();
 }
 
-cudaError_t launch_adam(int64_t n, float *p, const float *g, float *m, float *v,
+cudaError_t launch_adam(int64_t n, double *p, const float *g, float *m, float *v,
                         const uint8_t *mask, int t, float lr, float b1, float b2, float eps,
                         cudaStream_t s) {
   if (n == 0) return cudaSuccess;

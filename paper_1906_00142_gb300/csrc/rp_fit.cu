@@ -43,6 +43,7 @@ namespace {
 
 
 __constant__ int8_t c_exp[kMaxNm][3];   // graded-lex exponents
+__constant__ int8_t c_idx[kMaxDeg + 1][kMaxDeg + 1][kMaxDeg + 1];   // exponents -> graded-lex index
 
 struct FitArgs {
   int64_t F, S;
@@ -1263,9 +1264,9 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
       }
       __syncthreads();
       for (int e = tid; e < n; e += kT) {
+        // Q is symmetric: read column e (consecutive threads, consecutive words)
         Real z = 0;
-        const Real *qrow = w.G + e * naug;
-        for (int k2 = 0; k2 < n; ++k2) z = fma(qrow[k2], w.gvec[k2], z);
+        for (int k2 = 0; k2 < n; ++k2) z = fma(w.G[k2 * naug + e], w.gvec[k2], z);
         w.dxw[e] = z * (Real)omega;
       }
       __syncthreads();
@@ -1324,17 +1325,31 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
         for (int i2 = 0; i2 <= kMaxDeg; ++i2) P[(v * (kMaxDeg + 1) + k) * (kMaxDeg + 1) + i2] = out[i2];
       }
       __syncthreads();
+      // the basis change is a tensor product: three 1-D passes, one per
+      // variable (N last), each summing <= d + 1 terms per coefficient
+      double *buf[2] = {cpsi, P + 3 * (kMaxDeg + 1) * (kMaxDeg + 1)};
+      int cur = 0;
+#pragma unroll
+      for (int v = 2; v >= 0; --v) {
+        for (int e = tid; e < 2 * nm; e += kT) {
+          const int which = e / nm, t = e % nm;
+          int ex[3] = {c_exp[t][0], c_exp[t][1], c_exp[t][2]};
+          const int ov = ex[v];
+          const int room = d - (ex[0] + ex[1] + ex[2] - ov);
+          double acc = 0.0;
+          for (int k = ov; k <= room; ++k) {
+            ex[v] = k;
+            acc = fma(buf[cur][which * kMaxNm + c_idx[ex[0]][ex[1]][ex[2]]],
+                      P[(v * (kMaxDeg + 1) + k) * (kMaxDeg + 1) + ov], acc);
+          }
+          buf[cur ^ 1][which * kMaxNm + t] = acc;
+        }
+        cur ^= 1;
+        __syncthreads();
+      }
       for (int e = tid; e < 2 * nm; e += kT) {
         const int which = e / nm, t = e % nm;
-        const int i0 = c_exp[t][0], i1 = c_exp[t][1], i2 = c_exp[t][2];
-        double s = 0;
-        for (int j = 0; j < nm; ++j) {
-          const int e0 = c_exp[j][0], e1 = c_exp[j][1], e2 = c_exp[j][2];
-          if (e0 < i0 || e1 < i1 || e2 < i2) continue;
-          s += cpsi[which * kMaxNm + j] * P[(0 * (kMaxDeg + 1) + e0) * (kMaxDeg + 1) + i0] *
-               P[(1 * (kMaxDeg + 1) + e1) * (kMaxDeg + 1) + i1] *
-               P[(2 * (kMaxDeg + 1) + e2) * (kMaxDeg + 1) + i2];
-        }
+        const double s = buf[cur][which * kMaxNm + t];
         const int o = which == 0 ? t : kHalf + t;
         cf[o] = s;
         if (a.coef32) a.coef32[f * kStride + o] = (float)s;
@@ -1373,6 +1388,12 @@ void set_tables() {
         ++k;
       }
   cudaMemcpyToSymbol(c_exp, e, sizeof(e));
+  int8_t idx[kMaxDeg + 1][kMaxDeg + 1][kMaxDeg + 1];
+  for (int i = 0; i <= kMaxDeg; ++i)
+    for (int j = 0; j <= kMaxDeg; ++j)
+      for (int l = 0; l <= kMaxDeg; ++l) idx[i][j][l] = -1;
+  for (int t = 0; t < kMaxNm; ++t) idx[e[t][0]][e[t][1]][e[t][2]] = (int8_t)t;
+  cudaMemcpyToSymbol(c_idx, idx, sizeof(idx));
   done = true;
 }
 

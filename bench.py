@@ -271,8 +271,8 @@ def extra_measurements(rp, args, inst, x, y, off, deg, mm, gd, q, fit_out, prog,
     def plain_fits():
         for f in range(n_pf):
             rp.rp_fit(x, y, offs[f], DEGREE, precision="fp64", max_refine=8, tol=args.tol,
-                      degrees=deg[f:f + 1], stream=stream,
-                      out={k: v[f:f + 1] for k, v in pf_out.items()})
+                      degrees=deg[f:f + 1], stream=stream, schedule="static",
+                      out={k: v[f:f + 1] for k, v in pf_out.items() if k != "workspace"})
 
     def plain_queries():
         for i in range(n_pq):
@@ -322,6 +322,7 @@ def main():
     ap.add_argument("--queries", type=int, default=N_QUERIES)
     ap.add_argument("--only", default="all", choices=["all", "fit", "search"],
                     help="profiling captures: launch only one phase per step")
+    ap.add_argument("--no-tune", action="store_true", help="built-in launch shapes")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the per-precision, plain-form and graph measurements")
     args = ap.parse_args()
@@ -353,7 +354,8 @@ def main():
                    coef32=torch.empty((F, 70), dtype=torch.float32, device=dev),
                    box=torch.empty((F, 6), dtype=torch.float64, device=dev),
                    status=torch.empty(F, dtype=torch.int32, device=dev),
-                   rank=torch.empty(F, dtype=torch.int32, device=dev))
+                   rank=torch.empty(F, dtype=torch.int32, device=dev),
+                   workspace=torch.zeros(16, dtype=torch.uint8, device=dev))
     prog = torch.empty(rp.rp_program_size(N_KERNELS, DEGREE), dtype=torch.uint8, device=dev)
     s_out = dict(argmin=torch.empty(N_QUERIES, dtype=torch.int32, device=dev),
                  best=torch.empty(N_QUERIES, dtype=torch.float32, device=dev),
@@ -386,6 +388,20 @@ def main():
                   degrees=deg, out=fit_out, stream=stream)
         rp.rp_program_pack(fit_out["coef"], fit_out["box"], deg, mm, gd, DEGREE, program=prog,
                            stream=stream)
+
+    # launch shapes chosen by the library's autotuner on this workload
+    # (outside the timed region; the tuned shapes are what the steps use)
+    tuned = {}
+    if not args.no_tune:
+        if args.only in ("all", "fit"):
+            tuned["fit_ctas_per_sm"] = rp.rp_tune_fit(x, y, off, DEGREE, precision=args.precision,
+                                                      max_refine=8, tol=args.tol, degrees=deg,
+                                                      out=fit_out, stream=stream)
+        rp.rp_program_pack(fit_out["coef"], fit_out["box"], deg, mm, gd, DEGREE, program=prog,
+                           stream=stream)
+        if args.only in ("all", "search"):
+            t, c = rp.rp_tune_search(prog, N_KERNELS, DEGREE, q, out=s_out, stream=stream)
+            tuned["search_threads"], tuned["search_ctas_per_sm"] = t, c
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -501,7 +517,7 @@ def main():
                 "e2e": {"value": ws * F / (e2e_ms / 1e3), "unit": "fits/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
                 "gpu_launches": (3 if args.only == "all" else 2 if args.only == "fit" else 1) * args.steps,
-                "clocks": clk}
+                "clocks": clk, "tuned": tuned}
         line.update(extra)
         if ws == 1 and not args.no_cpu_baseline and args.only == "all":
             r = oracle_rates(inst, q_np, gd_np, budget_s=20.0)

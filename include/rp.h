@@ -99,8 +99,9 @@ typedef struct rp_fit_desc {
 } rp_fit_desc;
 
 /*
- * rp_fit_workspace_size -- bytes of device workspace rp_fit needs for `desc`
- * (written to *bytes; may be 0).  Host-only, launches nothing.
+ * rp_fit_workspace_size -- bytes of the optional device workspace of rp_fit
+ * for `desc` (the dynamic fit schedule's counter: 16 for a non-empty batch,
+ * 0 otherwise), written to *bytes.  Host-only, launches nothing.
  */
 int rp_fit_workspace_size(const rp_fit_desc *desc, size_t *bytes);
 
@@ -125,10 +126,16 @@ int rp_fit_workspace_size(const rp_fit_desc *desc, size_t *bytes);
  *   factorisation; status[f] = RP_FIT_* bits.
  * Inputs: x float[3][S], y float[S], fit_off int64[F+1] non-decreasing with
  * fit_off[0] = 0 and fit_off[F] <= S (checked on the device: a fit with a
- * bad range gets RP_FIT_EMPTY).  workspace: device memory of at least
- * rp_fit_workspace_size bytes (may be NULL if that is 0).
+ * bad range gets RP_FIT_EMPTY).  workspace: NULL, or device memory of at
+ * least rp_fit_workspace_size bytes, 16-byte aligned, owned by the caller
+ * and used by one call at a time: with it, CTAs claim fits dynamically from
+ * a counter kept there (reset on the stream with cudaMemsetAsync before the
+ * launch), so CTAs that draw large fits take fewer; with NULL each CTA takes
+ * every (grid size)-th fit.  Results do not depend on the schedule.
  * Errors: RP_ERR_INVALID_ARG for null pointers, F < 0, degree or precision
- * out of range; RP_ERR_CUDA if a launch fails.
+ * out of range; RP_ERR_WORKSPACE / RP_ERR_ALIGNMENT for a workspace that is
+ * too small or misaligned; RP_ERR_UNSUPPORTED for the reserved BF16
+ * precisions; RP_ERR_CUDA if a launch fails.
  */
 int rp_fit(const rp_fit_desc *desc, const float *x, const float *y, const int64_t *fit_off,
            double *coef, float *coef32, double *box, int32_t *status, int32_t *rank,
@@ -233,6 +240,33 @@ int rp_relmse_bwd(int64_t num_fits, int64_t num_samples, const float *x, const f
 int rp_adam_step(int64_t n, double *param, const float *grad, float *m, float *v,
                  const uint8_t *mask, int32_t t, float lr, float beta1, float beta2, float eps,
                  void *stream);
+
+/*
+ * Launch-shape autotuning (no counterpart in the paper; the paper's search is
+ * the evaluation itself).  Each call runs its kernel several times on the
+ * caller's buffers (the outputs end holding a valid result of the call),
+ * synchronises the host with the stream, and records the fastest shape for
+ * the current device; later launches of that kind use it.  Results never
+ * depend on the shape.  Not capturable into a CUDA graph: call before
+ * capturing.  Not thread-safe against concurrent launches of the same kind.
+ *
+ * rp_tune_search -- arguments as rp_eval_search; times persistent grids of
+ * {256, 128, 64} threads per CTA and 2..32 CTAs per SM for `degree` and
+ * writes the chosen threads per CTA and CTAs per SM.
+ */
+int rp_tune_search(const void *program, int64_t num_kernels, int32_t degree,
+                   const rp_hw_fixed *hw, const float *queries, int64_t num_queries,
+                   int32_t *argmin, float *best, float *second, int32_t *status, void *stream,
+                   int32_t *threads, int32_t *ctas_per_sm);
+
+/*
+ * rp_tune_fit -- arguments as rp_fit; times persistent grids of 1 .. (the
+ * residency limit of the variant desc selects) CTAs per SM for desc's
+ * precision and degree and writes the chosen CTAs per SM.
+ */
+int rp_tune_fit(const rp_fit_desc *desc, const float *x, const float *y, const int64_t *fit_off,
+                double *coef, float *coef32, double *box, int32_t *status, int32_t *rank,
+                void *workspace, size_t workspace_bytes, void *stream, int32_t *ctas_per_sm);
 
 /* Message for an rp_status code (static string). */
 const char *rp_strerror(int code);

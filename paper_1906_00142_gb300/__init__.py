@@ -8,7 +8,7 @@ device is missing, calls raise.
 
 Entry points (same names as the C ABI):
     rp_fit, rp_fit_workspace_size, rp_program_size, rp_program_pack,
-    rp_eval_search, rp_relmse_fwd, rp_relmse_bwd, rp_adam_step,
+    rp_eval_search, rp_relmse_fwd, rp_relmse_bwd, rp_adam_step, rp_tune_fit, rp_tune_search,
     rp_strerror, rp_version
 plus ``RelMSE`` (a torch.autograd.Function over rp_relmse_fwd/bwd) and
 ``refine_relmse`` (Adam steps with the hand-written backward).
@@ -77,6 +77,10 @@ def load_library(path: str = LIB_PATH):
             lib.rp_relmse_bwd.argtypes = [i64, i64, P, P, P, P, P, P, P, P, P]
             lib.rp_adam_step.argtypes = [i64, P, P, P, P, P, i32, C.c_float, C.c_float, C.c_float,
                                          C.c_float, P]
+            lib.rp_tune_search.argtypes = [P, i64, i32, C.POINTER(HwFixed), P, i64, P, P, P, P, P,
+                                           C.POINTER(i32), C.POINTER(i32)]
+            lib.rp_tune_fit.argtypes = [C.POINTER(FitDesc), P, P, P, P, P, P, P, P, P, C.c_size_t, P,
+                                        C.POINTER(i32)]
             lib.rp_strerror.argtypes = [C.c_int]
             lib.rp_strerror.restype = C.c_char_p
             lib.rp_version.restype = C.c_int
@@ -123,14 +127,8 @@ def rp_fit_workspace_size(desc: FitDesc) -> int:
     return b.value
 
 
-def rp_fit(x: torch.Tensor, y: torch.Tensor, fit_off: torch.Tensor, degree: int,
-           precision: str = "fp32", max_refine: int = 8, tol: float = 1e-12,
-           degrees: torch.Tensor | None = None, weighted: bool = True, out=None, stream=None):
-    """Batched rational least-squares fits (see rp_fit in include/rp.h).
-    x: float32 [3, S], y: float32 [S], fit_off: int64 [F+1] (all CUDA).
-    Returns dict(coef float64 [F,70], coef32 float32 [F,70], box float64 [F,6],
-    status int32 [F], rank int32 [F])."""
-    lib = load_library()
+def _fit_args(x, y, fit_off, degree, precision, max_refine, tol, degrees, weighted, out,
+              stream, schedule):
     F = fit_off.numel() - 1
     S = y.numel()
     dev = y.device
@@ -143,19 +141,53 @@ def rp_fit(x: torch.Tensor, y: torch.Tensor, fit_off: torch.Tensor, degree: int,
     desc = FitDesc(F, S, int(degree), PREC[precision], int(max_refine),
                    0 if weighted else RP_FIT_UNWEIGHTED, float(tol),
                    _ptr_or_null(degrees, torch.int8, "degrees").value)
+    st = torch.cuda.current_stream() if stream is None else stream
     ws_bytes = rp_fit_workspace_size(desc)
-    ws = out.get("workspace")
-    if ws_bytes and (ws is None or ws.numel() < ws_bytes):
-        raise RPError(f"rp_fit needs a workspace of {ws_bytes} bytes (out['workspace'])")
-    rc = lib.rp_fit(C.byref(desc), _dev(x, torch.float32, "x"), _dev(y, torch.float32, "y"),
-                    _dev(fit_off, torch.int64, "fit_off"), _dev(out["coef"], torch.float64, "coef"),
-                    _ptr_or_null(out.get("coef32"), torch.float32, "coef32"),
-                    _dev(out["box"], torch.float64, "box"), _dev(out["status"], torch.int32, "status"),
-                    _dev(out["rank"], torch.int32, "rank"),
-                    C.c_void_p(0 if not ws_bytes else ws.data_ptr()), C.c_size_t(ws_bytes),
-                    _stream(stream))
-    _check(rc, "rp_fit")
+    ws = None
+    if schedule == "dynamic" and ws_bytes:
+        ws = out.get("workspace")
+        if ws is None or ws.numel() < ws_bytes:
+            with torch.cuda.stream(st):        # stream-ordered reuse of the buffer
+                ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    elif schedule not in ("dynamic", "static"):
+        raise RPError(f"unknown schedule {schedule!r}")
+    args = (C.byref(desc), _dev(x, torch.float32, "x"), _dev(y, torch.float32, "y"),
+            _dev(fit_off, torch.int64, "fit_off"), _dev(out["coef"], torch.float64, "coef"),
+            _ptr_or_null(out.get("coef32"), torch.float32, "coef32"),
+            _dev(out["box"], torch.float64, "box"), _dev(out["status"], torch.int32, "status"),
+            _dev(out["rank"], torch.int32, "rank"),
+            C.c_void_p(0 if ws is None else ws.data_ptr()),
+            C.c_size_t(0 if ws is None else ws.numel()), C.c_void_p(st.cuda_stream))
+    return out, args, ws
+
+
+def rp_fit(x: torch.Tensor, y: torch.Tensor, fit_off: torch.Tensor, degree: int,
+           precision: str = "fp32", max_refine: int = 8, tol: float = 1e-12,
+           degrees: torch.Tensor | None = None, weighted: bool = True, out=None, stream=None,
+           schedule: str = "dynamic"):
+    """Batched rational least-squares fits (see rp_fit in include/rp.h).
+    x: float32 [3, S], y: float32 [S], fit_off: int64 [F+1] (all CUDA).
+    schedule "dynamic" (CTAs claim fits from a counter in a 16-byte
+    workspace, out["workspace"] or allocated here) or "static".
+    Returns dict(coef float64 [F,70], coef32 float32 [F,70], box float64 [F,6],
+    status int32 [F], rank int32 [F])."""
+    out, args, _ws = _fit_args(x, y, fit_off, degree, precision, max_refine, tol, degrees,
+                               weighted, out, stream, schedule)
+    _check(load_library().rp_fit(*args), "rp_fit")
     return out
+
+
+def rp_tune_fit(x, y, fit_off, degree: int, precision: str = "fp32", max_refine: int = 8,
+                tol: float = 1e-12, degrees=None, weighted: bool = True, out=None, stream=None,
+                schedule: str = "dynamic") -> int:
+    """Time the fit kernel's grid sizes on these fits (see rp_tune_fit in
+    include/rp.h); returns the CTAs per SM now used for this precision and
+    degree.  Synchronises; call before any graph capture."""
+    out, args, _ws = _fit_args(x, y, fit_off, degree, precision, max_refine, tol, degrees,
+                               weighted, out, stream, schedule)
+    c = C.c_int32(0)
+    _check(load_library().rp_tune_fit(*args, C.byref(c)), "rp_tune_fit")
+    return c.value
 
 
 def rp_program_size(num_kernels: int, degree: int) -> int:
@@ -206,10 +238,7 @@ def hw_struct(hw=None) -> HwFixed:
                    float(h["issue_cycles"]), 0)
 
 
-def rp_eval_search(program, num_kernels: int, degree: int, queries: torch.Tensor, hw=None,
-                   out=None, stream=None):
-    """Evaluate-and-argmin for queries float32 [Q, 8] (CUDA)."""
-    lib = load_library()
+def _search_args(program, num_kernels, degree, queries, hw, out, stream):
     Q = queries.shape[0]
     dev = queries.device
     if out is None:
@@ -218,14 +247,30 @@ def rp_eval_search(program, num_kernels: int, degree: int, queries: torch.Tensor
                    second=torch.empty(Q, dtype=torch.float32, device=dev),
                    status=torch.empty(Q, dtype=torch.int32, device=dev))
     h = hw_struct(hw)
-    rc = lib.rp_eval_search(_dev(program, torch.uint8, "program"), int(num_kernels), int(degree),
-                            C.byref(h), _dev(queries, torch.float32, "queries"), Q,
-                            _dev(out["argmin"], torch.int32, "argmin"),
-                            _dev(out["best"], torch.float32, "best"),
-                            _dev(out["second"], torch.float32, "second"),
-                            _dev(out["status"], torch.int32, "status"), _stream(stream))
-    _check(rc, "rp_eval_search")
+    args = (_dev(program, torch.uint8, "program"), int(num_kernels), int(degree), C.byref(h),
+            _dev(queries, torch.float32, "queries"), Q, _dev(out["argmin"], torch.int32, "argmin"),
+            _dev(out["best"], torch.float32, "best"), _dev(out["second"], torch.float32, "second"),
+            _dev(out["status"], torch.int32, "status"), _stream(stream))
+    return out, args, h
+
+
+def rp_eval_search(program, num_kernels: int, degree: int, queries: torch.Tensor, hw=None,
+                   out=None, stream=None):
+    """Evaluate-and-argmin for queries float32 [Q, 8] (CUDA)."""
+    out, args, _h = _search_args(program, num_kernels, degree, queries, hw, out, stream)
+    _check(load_library().rp_eval_search(*args), "rp_eval_search")
     return out
+
+
+def rp_tune_search(program, num_kernels: int, degree: int, queries: torch.Tensor, hw=None,
+                   out=None, stream=None):
+    """Time the search kernel's launch shapes on these queries (see
+    rp_tune_search in include/rp.h); returns (threads per CTA, CTAs per SM)
+    now used for this degree.  Synchronises; call before any graph capture."""
+    out, args, _h = _search_args(program, num_kernels, degree, queries, hw, out, stream)
+    t, c = C.c_int32(0), C.c_int32(0)
+    _check(load_library().rp_tune_search(*args, C.byref(t), C.byref(c)), "rp_tune_search")
+    return t.value, c.value
 
 
 def rp_relmse_fwd(x, y, fit_off, degrees, coef, box, loss=None, stream=None):

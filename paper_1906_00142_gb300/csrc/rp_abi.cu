@@ -18,6 +18,27 @@ bool device_ok() {
   return cudaGetDeviceCount(&n) == cudaSuccess && n > 0;
 }
 
+// Mean device time (ms) of `reps` calls of fn on the stream, after one
+// untimed call; a negative value reports a launch or CUDA error.
+template <class Fn>
+float time_calls(Fn fn, int reps, cudaStream_t s) {
+  if (fn() != RP_OK) return -1.0f;
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return -1.0f;
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return -1.0f;
+  }
+  float ms = -1.0f;
+  bool ok = cudaEventRecord(a, s) == cudaSuccess;
+  for (int r = 0; r < reps && ok; ++r) ok = fn() == RP_OK;
+  ok = ok && cudaEventRecord(b, s) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
+       cudaEventElapsedTime(&ms, a, b) == cudaSuccess;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ok ? ms / (float)reps : -1.0f;
+}
+
 }  // namespace
 
 extern "C" {
@@ -53,7 +74,8 @@ int rp_fit(const rp_fit_desc *desc, const float *x, const float *y, const int64_
   if (desc->num_fits == 0) return RP_OK;
   if (!fit_off || !coef || !box || !status || !rank) return RP_ERR_INVALID_ARG;
   if (desc->num_samples > 0 && (!x || !y)) return RP_ERR_INVALID_ARG;
-  if (workspace_bytes < rpk::fit_workspace_bytes(*desc)) return RP_ERR_WORKSPACE;
+  if (workspace && workspace_bytes < rpk::fit_workspace_bytes(*desc)) return RP_ERR_WORKSPACE;
+  if (workspace && !aligned(workspace, 16)) return RP_ERR_ALIGNMENT;
   if (!rpk::fit_precision_supported(desc->precision)) return RP_ERR_UNSUPPORTED;
   if (!device_ok()) return RP_ERR_NO_DEVICE;
   return from_cuda(rpk::launch_fit(*desc, x, y, fit_off, coef, coef32, box, status, rank, workspace,
@@ -95,6 +117,81 @@ int rp_eval_search(const void *program, int64_t num_kernels, int32_t degree,
   auto pv = rpk::program_sections<rpk::ProgramView>(program, num_kernels);
   return from_cuda(rpk::launch_search(pv, num_kernels, degree, *hw, queries, num_queries, argmin,
                                       best, second, status, as_stream(stream)));
+}
+
+int rp_tune_search(const void *program, int64_t num_kernels, int32_t degree,
+                   const rp_hw_fixed *hw, const float *queries, int64_t num_queries,
+                   int32_t *argmin, float *best, float *second, int32_t *status, void *stream,
+                   int32_t *threads, int32_t *ctas_per_sm) {
+  if (!threads || !ctas_per_sm) return RP_ERR_INVALID_ARG;
+  // validates everything once (and is the first, untimed call)
+  int rc = rp_eval_search(program, num_kernels, degree, hw, queries, num_queries, argmin, best,
+                          second, status, stream);
+  if (rc != RP_OK) return rc;
+  static const rpk::SearchShape cand[] = {{256, 8}, {256, 4}, {256, 2}, {128, 16}, {128, 8},
+                                          {128, 4}, {64, 32}, {64, 16}};
+  const rpk::SearchShape keep = rpk::search_shape(degree);
+  rpk::SearchShape best_shape = keep;
+  float best_ms = 0.0f;
+  for (const auto &c : cand) {
+    rpk::set_search_shape(degree, c);
+    const float ms = time_calls(
+        [&] {
+          return rp_eval_search(program, num_kernels, degree, hw, queries, num_queries, argmin,
+                                best, second, status, stream);
+        },
+        3, as_stream(stream));
+    if (ms < 0.0f) {
+      rpk::set_search_shape(degree, keep);
+      return RP_ERR_CUDA;
+    }
+    if (best_ms == 0.0f || ms < best_ms) {
+      best_ms = ms;
+      best_shape = c;
+    }
+  }
+  rpk::set_search_shape(degree, best_shape);
+  *threads = best_shape.threads;
+  *ctas_per_sm = best_shape.ctas_per_sm;
+  return RP_OK;
+}
+
+int rp_tune_fit(const rp_fit_desc *desc, const float *x, const float *y, const int64_t *fit_off,
+                double *coef, float *coef32, double *box, int32_t *status, int32_t *rank,
+                void *workspace, size_t workspace_bytes, void *stream, int32_t *ctas_per_sm) {
+  if (!ctas_per_sm) return RP_ERR_INVALID_ARG;
+  int rc = rp_fit(desc, x, y, fit_off, coef, coef32, box, status, rank, workspace, workspace_bytes,
+                  stream);
+  if (rc != RP_OK) return rc;
+  if (desc->num_fits == 0) {
+    *ctas_per_sm = 0;
+    return RP_OK;
+  }
+  const int dmax = desc->degree;
+  const int keep = rpk::fit_ctas_cap(desc->precision, dmax);
+  const int top = rpk::fit_max_ctas_per_sm(*desc);
+  int best_cap = keep;
+  float best_ms = 0.0f;
+  for (int c = top; c >= 1; --c) {
+    rpk::set_fit_ctas_cap(desc->precision, dmax, c);
+    const float ms = time_calls(
+        [&] {
+          return rp_fit(desc, x, y, fit_off, coef, coef32, box, status, rank, workspace,
+                        workspace_bytes, stream);
+        },
+        2, as_stream(stream));
+    if (ms < 0.0f) {
+      rpk::set_fit_ctas_cap(desc->precision, dmax, keep);
+      return RP_ERR_CUDA;
+    }
+    if (best_ms == 0.0f || ms < best_ms) {
+      best_ms = ms;
+      best_cap = c;
+    }
+  }
+  rpk::set_fit_ctas_cap(desc->precision, dmax, best_cap);
+  *ctas_per_sm = best_cap;
+  return RP_OK;
 }
 
 int rp_relmse_fwd(int64_t num_fits, int64_t num_samples, const float *x, const float *y,

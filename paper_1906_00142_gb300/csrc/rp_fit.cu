@@ -60,6 +60,7 @@ struct FitArgs {
   double *box;
   int32_t *status;
   int32_t *rank;
+  unsigned long long *counter;   // dynamic fit schedule (workspace), or null
 };
 
 // ---------------------------------------------------------------------
@@ -249,6 +250,7 @@ struct CtaFit {
   float redf[4][32];
   unsigned dslot[3][kMaxDeg + 1];
   uint32_t tmem_base;
+  long long next_fit[2];              // claimed fit indices (alternating slots)
   int keep_cnt, keep_w, bad;
   float fscal[4];
 };
@@ -627,7 +629,18 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
     tc::fence_after_sync();
     tmem = w.tmem_base;
   }
-  for (int64_t f = blockIdx.x; f < a.F; f += gridDim.x) {
+  // fits are claimed from the workspace counter (CTAs that draw large fits
+  // take fewer), else every gridDim.x-th fit
+  int64_t f = blockIdx.x;
+  for (int claim = 0;; ++claim) {
+    if (a.counter) {
+      if (tid == 0) w.next_fit[claim & 1] = (long long)atomicAdd(a.counter, 1ull);
+      __syncthreads();
+      f = w.next_fit[claim & 1];
+    } else if (claim > 0) {
+      f += gridDim.x;
+    }
+    if (f >= a.F) break;
     // ---------------- phase 0: range, degree, validation, box, distinct values
     const int64_t b0 = a.off[f], b1 = a.off[f + 1];
     const int d = a.degs ? (int)a.degs[f] : a.d_uniform;
@@ -1301,28 +1314,26 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
                                        ? w.uv[which][i]
                                        : (double)w.uvhi[which][i] + (double)w.uvlo[which][i];
       }
-      if (tid >= 96 && tid < 96 + 3 * (kMaxDeg + 1)) {
-        // Q_k(u), u = (x' - mu) isg, as a polynomial in x'
-        const int v = (tid - 96) / (kMaxDeg + 1), k = (tid - 96) % (kMaxDeg + 1);
+      if (tid >= kT - 3 * (kMaxDeg + 1) * (kMaxDeg + 1) + 0 && tid < kT) {
+        // P[v][k][i]: coefficient of x'^i in Q_k(u), u = (x' - mu) isg, one
+        // entry per thread: sum_{l=i..k} Tm[l][k] C(l, i) isg^l (-mu)^(l-i)
+        const int e = tid - (kT - 3 * (kMaxDeg + 1) * (kMaxDeg + 1));
+        const int v = e / ((kMaxDeg + 1) * (kMaxDeg + 1));
+        const int k = (e / (kMaxDeg + 1)) % (kMaxDeg + 1), i = e % (kMaxDeg + 1);
         const double mu = w.mu_v[v], isg = w.isg_v[v];
-        double out[kMaxDeg + 1] = {0, 0, 0, 0, 0};
-        if (k <= d) {
-          double isgl = 1.0;
-          for (int l = 0; l <= k; ++l) {
-            const double t = w.Tm[v][l][k];
-            if (t != 0.0) {
-              double binom = 1.0;
-              for (int ii = 0; ii <= l; ++ii) {
-                double mpow = 1.0;
-                for (int q = 0; q < l - ii; ++q) mpow *= -mu;
-                out[ii] += t * isgl * binom * mpow;
-                binom = binom * (double)(l - ii) / (double)(ii + 1);
-              }
-            }
-            isgl *= isg;
+        double acc = 0.0;
+        if (k <= d && i <= k) {
+          double pw = 1.0;   // isg^l (-mu)^(l - i), starting at l = i
+          for (int l = 0; l < i; ++l) pw *= isg;
+          const double step = -mu * isg;
+          int binom = 1;     // C(l, i), starting at C(i, i)
+          for (int l = i; l <= k; ++l) {
+            acc = fma((double)w.Tm[v][l][k] * (double)binom, pw, acc);
+            pw *= step;
+            binom = binom * (l + 1) / (l + 1 - i);
           }
         }
-        for (int i2 = 0; i2 <= kMaxDeg; ++i2) P[(v * (kMaxDeg + 1) + k) * (kMaxDeg + 1) + i2] = out[i2];
+        P[(v * (kMaxDeg + 1) + k) * (kMaxDeg + 1) + i] = acc;
       }
       __syncthreads();
       // the basis change is a tensor product: three 1-D passes, one per
@@ -1397,22 +1408,14 @@ void set_tables() {
   done = true;
 }
 
+// Resident CTAs per SM of one fit-kernel variant: registers, shared memory,
+// threads and (tensor-core variants) tensor-memory columns.
 template <class Real, int DMAX, int GM>
-cudaError_t launch_t(const FitArgs &a, cudaStream_t s) {
+int residency() {
   using WF = CtaFit<Real, DMAX, GM>;
-  // 128-bit shared-memory loads of the staged rows and of W; 8-byte mbarrier
-  static_assert(offsetof(WF, stage) == 0, "stage must start the state");
-  static_assert(offsetof(WF, W) % 16 == 0 && offsetof(WF, G) % 16 == 0, "W, G: 16-byte aligned");
-  static_assert(offsetof(WF, mbar) % 8 == 0, "mbarrier: 8-byte aligned");
   const size_t smem = ctafit_bytes<Real, DMAX, GM>();
-  cudaError_t e = cudaFuncSetAttribute(fit_kernel<Real, DMAX, GM>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  // resident CTAs per SM from registers, shared memory and (tensor-core
-  // path) tensor-memory columns
   cudaFuncAttributes fa;
-  e = cudaFuncGetAttributes(&fa, fit_kernel<Real, DMAX, GM>);
-  if (e != cudaSuccess) return e;
+  if (cudaFuncGetAttributes(&fa, fit_kernel<Real, DMAX, GM>) != cudaSuccess) return 1;
   int dev = 0;
   cudaGetDevice(&dev);
   int smem_sm = 0, smem_rsv = 0, regs_sm = 0;
@@ -1424,25 +1427,59 @@ cudaError_t launch_t(const FitArgs &a, cudaStream_t s) {
   per_sm = min(per_sm, regs_sm / max(regs_cta, 1));
   per_sm = min(per_sm, 2048 / kT);
   if (GM > 0) per_sm = min(per_sm, 512 / TcShape<DMAX>::TMEM_COLS);
-  if (per_sm < 1) per_sm = 1;
+  (void)sizeof(WF);
+  return per_sm < 1 ? 1 : per_sm;
+}
+
+template <class Real, int DMAX, int GM>
+cudaError_t launch_t(const FitArgs &a, int precision, cudaStream_t s) {
+  using WF = CtaFit<Real, DMAX, GM>;
+  // 128-bit shared-memory loads of the staged rows and of W; 8-byte mbarrier
+  static_assert(offsetof(WF, stage) == 0, "stage must start the state");
+  static_assert(offsetof(WF, W) % 16 == 0 && offsetof(WF, G) % 16 == 0, "W, G: 16-byte aligned");
+  static_assert(offsetof(WF, mbar) % 8 == 0, "mbarrier: 8-byte aligned");
+  const size_t smem = ctafit_bytes<Real, DMAX, GM>();
+  cudaError_t e = cudaFuncSetAttribute(fit_kernel<Real, DMAX, GM>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = residency<Real, DMAX, GM>();
+  const int cap = fit_ctas_cap(precision, DMAX);
+  if (cap > 0 && cap < per_sm) per_sm = cap;
   int64_t grid = (int64_t)num_sms() * per_sm;
   if (grid > a.F) grid = a.F;
+  if (a.counter) {
+    e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+  }
   fit_kernel<Real, DMAX, GM><<<(unsigned)grid, kT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int GM>
-cudaError_t launch_f32(const FitArgs &a, int dmax, cudaStream_t s) {
+cudaError_t launch_f32(const FitArgs &a, int dmax, int precision, cudaStream_t s) {
   switch (dmax) {
-    case 1: case 2: return launch_t<float, 2, GM>(a, s);
-    case 3: return launch_t<float, 3, GM>(a, s);
-    default: return launch_t<float, 4, GM>(a, s);
+    case 1: case 2: return launch_t<float, 2, GM>(a, precision, s);
+    case 3: return launch_t<float, 3, GM>(a, precision, s);
+    default: return launch_t<float, 4, GM>(a, precision, s);
   }
 }
 
 }  // namespace
 
-size_t fit_workspace_bytes(const rp_fit_desc &) { return 0; }
+// One 64-bit counter for the dynamic fit schedule (16 bytes, aligned).
+size_t fit_workspace_bytes(const rp_fit_desc &desc) { return desc.num_fits > 0 ? 16 : 0; }
+
+int fit_max_ctas_per_sm(const rp_fit_desc &desc) {
+  const int dmax = desc.degree;
+  if (desc.precision == RP_PREC_FP64)
+    return dmax <= 2 ? residency<double, 2, 0>() : dmax == 3 ? residency<double, 3, 0>() : residency<double, 4, 0>();
+  const int gm = desc.precision == RP_PREC_TF32 ? 1 : desc.precision == RP_PREC_TF32X3 ? 2 : 0;
+  if (gm == 1)
+    return dmax <= 2 ? residency<float, 2, 1>() : dmax == 3 ? residency<float, 3, 1>() : residency<float, 4, 1>();
+  if (gm == 2)
+    return dmax <= 2 ? residency<float, 2, 2>() : dmax == 3 ? residency<float, 3, 2>() : residency<float, 4, 2>();
+  return dmax <= 2 ? residency<float, 2, 0>() : dmax == 3 ? residency<float, 3, 0>() : residency<float, 4, 0>();
+}
 
 bool fit_precision_supported(int precision) {
   return precision == RP_PREC_FP64 || precision == RP_PREC_FP32 || precision == RP_PREC_TF32 ||
@@ -1451,7 +1488,7 @@ bool fit_precision_supported(int precision) {
 
 cudaError_t launch_fit(const rp_fit_desc &desc, const float *x, const float *y,
                        const int64_t *fit_off, double *coef, float *coef32, double *box,
-                       int32_t *status, int32_t *rank, void *, cudaStream_t s) {
+                       int32_t *status, int32_t *rank, void *workspace, cudaStream_t s) {
   if (desc.num_fits == 0) return cudaSuccess;
   set_tables();
   FitArgs a;
@@ -1470,19 +1507,20 @@ cudaError_t launch_fit(const rp_fit_desc &desc, const float *x, const float *y,
   a.box = box;
   a.status = status;
   a.rank = rank;
+  a.counter = reinterpret_cast<unsigned long long *>(workspace);
   const int dmax = desc.degree;
   if (desc.precision == RP_PREC_FP64) {
     a.drop_tol = 1e-13;
     switch (dmax) {
-      case 1: case 2: return launch_t<double, 2, 0>(a, s);
-      case 3: return launch_t<double, 3, 0>(a, s);
-      default: return launch_t<double, 4, 0>(a, s);
+      case 1: case 2: return launch_t<double, 2, 0>(a, desc.precision, s);
+      case 3: return launch_t<double, 3, 0>(a, desc.precision, s);
+      default: return launch_t<double, 4, 0>(a, desc.precision, s);
     }
   }
   a.drop_tol = 1e-7;
-  if (desc.precision == RP_PREC_TF32) return launch_f32<1>(a, dmax, s);
-  if (desc.precision == RP_PREC_TF32X3) return launch_f32<2>(a, dmax, s);
-  return launch_f32<0>(a, dmax, s);
+  if (desc.precision == RP_PREC_TF32) return launch_f32<1>(a, dmax, desc.precision, s);
+  if (desc.precision == RP_PREC_TF32X3) return launch_f32<2>(a, dmax, desc.precision, s);
+  return launch_f32<0>(a, dmax, desc.precision, s);
 }
 
 }  // namespace rpk

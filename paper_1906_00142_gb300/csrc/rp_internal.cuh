@@ -67,6 +67,17 @@ cudaError_t launch_fit(const rp_fit_desc &desc, const float *x, const float *y,
                        int32_t *status, int32_t *rank, void *workspace, cudaStream_t s);
 size_t fit_workspace_bytes(const rp_fit_desc &desc);
 bool fit_precision_supported(int precision);
+int fit_max_ctas_per_sm(const rp_fit_desc &desc);   // residency limit of the launch desc selects
+
+// Launch shapes chosen by the autotuner, per device (0 = built-in default).
+struct SearchShape {
+  int threads;        // threads per CTA (<= 256)
+  int ctas_per_sm;    // persistent grid = SMs x this
+};
+SearchShape search_shape(int degree);
+void set_search_shape(int degree, SearchShape s);
+int fit_ctas_cap(int precision, int dmax);           // 0: the residency limit
+void set_fit_ctas_cap(int precision, int dmax, int cap);
 
 cudaError_t launch_relmse(bool backward, int64_t F, int64_t S, const float *x, const float *y,
                           const int64_t *fit_off, const int8_t *degrees, const double *coef,

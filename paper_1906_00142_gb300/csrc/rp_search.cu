@@ -314,6 +314,28 @@ int num_sms() {
   return n;
 }
 
+namespace {
+constexpr int kMaxDev = 16;
+SearchShape g_search_shape[kMaxDev][kMaxDeg + 1];
+int g_fit_cap[kMaxDev][RP_PREC_BF16X3 + 1][kMaxDeg + 1];
+int current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) dev = 0;
+  return dev;
+}
+}  // namespace
+
+SearchShape search_shape(int degree) {
+  SearchShape s = g_search_shape[current_device()][degree];
+  if (s.threads <= 0) s = SearchShape{256, 8};
+  return s;
+}
+void set_search_shape(int degree, SearchShape s) { g_search_shape[current_device()][degree] = s; }
+int fit_ctas_cap(int precision, int dmax) { return g_fit_cap[current_device()][precision][dmax]; }
+void set_fit_ctas_cap(int precision, int dmax, int cap) {
+  g_fit_cap[current_device()][precision][dmax] = cap;
+}
+
 cudaError_t launch_pack(int64_t K, int d, const double *coef, const double *box,
                         const int8_t *degrees, const int32_t *metric_map, const int32_t *grid_dims,
                         ProgramMut prog, cudaStream_t s) {
@@ -346,9 +368,10 @@ cudaError_t launch_search(ProgramView prog, int64_t K, int d, const rp_hw_fixed 
       cfg.bact_w[c] = (T > hw.t_max) ? 0 : bw;
     }
   HwC h{hw.warp_size, hw.w_max, hw.r_sm, hw.z_sm, hw.issue_cycles};
-  const int threads = 256;
+  const SearchShape shape = search_shape(d);
+  const int threads = shape.threads;
   int64_t blocks = (Q + threads - 1) / threads;
-  const int64_t cap = (int64_t)num_sms() * 8;
+  const int64_t cap = (int64_t)num_sms() * shape.ctas_per_sm;
   if (blocks > cap) blocks = cap;
   const float4 *q4 = reinterpret_cast<const float4 *>(queries);
   switch (d + 1) {

@@ -66,3 +66,20 @@ def test_argument_validation_without_launch(lib):
     assert lib.rp_program_pack(4, 0, None, None, None, None, None, None, 0, None) == -1
     assert lib.rp_adam_step(10, None, None, None, None, None, 0, 1e-3, 0.9, 0.999, 1e-8, None) == -1
     assert lib.rp_relmse_fwd(-1, 0, None, None, None, None, None, None, None, None) == -1
+
+
+def test_tuning_argument_validation_without_launch(lib):
+    d = rp.FitDesc(4, 100, 9, 1, 4, 0, 1e-12, None)          # degree 9: invalid
+    c = C.c_int32(0)
+    assert lib.rp_tune_fit(C.byref(d), None, None, None, None, None, None, None, None, None, 0,
+                           None, C.byref(c)) == -1
+    d = rp.FitDesc(4, 100, 3, 1, 4, 0, 1e-12, None)
+    assert lib.rp_tune_fit(C.byref(d), None, None, None, None, None, None, None, None, None, 0,
+                           None, None) == -1
+    h = rp.hw_struct()
+    t = C.c_int32(0)
+    assert lib.rp_tune_search(None, 1, 3, C.byref(h), None, 10, None, None, None, None, None,
+                              C.byref(t), None) == -1
+    ws = C.c_size_t(0)
+    d = rp.FitDesc(5, 100, 3, 1, 4, 0, 1e-12, None)
+    assert lib.rp_fit_workspace_size(C.byref(d), C.byref(ws)) == 0 and ws.value == 16

@@ -142,6 +142,24 @@ int rp_fit(const rp_fit_desc *desc, const float *x, const float *y, const int64_
            void *workspace, size_t workspace_bytes, void *stream);
 
 /*
+ * rp_fit_noalloc -- rp_fit (same arguments, results and errors) for callers
+ * that cannot provide device memory, e.g. a host thread on a latency path
+ * where cudaMalloc's implicit device synchronisation is not acceptable.  It
+ * allocates nothing: the dynamic schedule's scratch (one 64-bit counter, the
+ * whole of rp_fit_workspace_size) is a statically allocated 16-byte device
+ * array of the library, reset with cudaMemsetAsync on `stream` before each
+ * launch.  The paper has no counterpart (it describes no GPU fitting).
+ * Limit: scratch of 16 bytes, which covers any batch size; a larger need
+ * returns RP_ERR_WORKSPACE.  The first call on each device resolves the
+ * array's address (cudaGetSymbolAddress) with that device current: make it
+ * before capturing any stream.  Calls that overlap in time (any streams,
+ * any threads) share the counter and race: serialise them.
+ */
+int rp_fit_noalloc(const rp_fit_desc *desc, const float *x, const float *y,
+                   const int64_t *fit_off, double *coef, float *coef32, double *box,
+                   int32_t *status, int32_t *rank, void *stream);
+
+/*
  * rp_program_size -- bytes of the packed program for K kernels whose fitted
  * metrics have degree <= d.  Layout (all little-endian, 16-byte aligned
  * sections): aN float[K][8], bN float[K][8], grid_dims int32[K] (padded),

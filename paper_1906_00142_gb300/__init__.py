@@ -9,6 +9,7 @@ device is missing, calls raise.
 Entry points (same names as the C ABI):
     rp_fit, rp_fit_workspace_size, rp_program_size, rp_program_pack,
     rp_eval_search, rp_relmse_fwd, rp_relmse_bwd, rp_adam_step, rp_tune_fit, rp_tune_search,
+    rp_fit_noalloc,
     rp_strerror, rp_version
 plus ``RelMSE`` (a torch.autograd.Function over rp_relmse_fwd/bwd) and
 ``refine_relmse`` (Adam steps with the hand-written backward).
@@ -77,6 +78,7 @@ def load_library(path: str = LIB_PATH):
             lib.rp_relmse_bwd.argtypes = [i64, i64, P, P, P, P, P, P, P, P, P]
             lib.rp_adam_step.argtypes = [i64, P, P, P, P, P, i32, C.c_float, C.c_float, C.c_float,
                                          C.c_float, P]
+            lib.rp_fit_noalloc.argtypes = [C.POINTER(FitDesc), P, P, P, P, P, P, P, P, P]
             lib.rp_tune_search.argtypes = [P, i64, i32, C.POINTER(HwFixed), P, i64, P, P, P, P, P,
                                            C.POINTER(i32), C.POINTER(i32)]
             lib.rp_tune_fit.argtypes = [C.POINTER(FitDesc), P, P, P, P, P, P, P, P, P, C.c_size_t, P,
@@ -174,6 +176,17 @@ def rp_fit(x: torch.Tensor, y: torch.Tensor, fit_off: torch.Tensor, degree: int,
     out, args, _ws = _fit_args(x, y, fit_off, degree, precision, max_refine, tol, degrees,
                                weighted, out, stream, schedule)
     _check(load_library().rp_fit(*args), "rp_fit")
+    return out
+
+
+def rp_fit_noalloc(x, y, fit_off, degree: int, precision: str = "fp32", max_refine: int = 8,
+                   tol: float = 1e-12, degrees=None, weighted: bool = True, out=None,
+                   stream=None):
+    """rp_fit with the library's static scratch instead of a workspace (see
+    rp_fit_noalloc in include/rp.h); outputs as rp_fit."""
+    out, args, _ws = _fit_args(x, y, fit_off, degree, precision, max_refine, tol, degrees,
+                               weighted, out, stream, "static")
+    _check(load_library().rp_fit_noalloc(*args[:9], args[11]), "rp_fit_noalloc")
     return out
 
 

@@ -82,6 +82,21 @@ int rp_fit(const rp_fit_desc *desc, const float *x, const float *y, const int64_
                                    as_stream(stream)));
 }
 
+int rp_fit_noalloc(const rp_fit_desc *desc, const float *x, const float *y,
+                   const int64_t *fit_off, double *coef, float *coef32, double *box,
+                   int32_t *status, int32_t *rank, void *stream) {
+  if (!desc) return RP_ERR_INVALID_ARG;
+  if (desc->num_fits == 0)   // nothing to launch; arguments checked as rp_fit does
+    return rp_fit(desc, x, y, fit_off, coef, coef32, box, status, rank, nullptr, 0, stream);
+  if (!device_ok()) return RP_ERR_NO_DEVICE;
+  void *scratch = nullptr;
+  size_t scratch_bytes = 0;
+  if (rpk::fit_static_scratch(&scratch, &scratch_bytes) != cudaSuccess) return RP_ERR_CUDA;
+  if (rpk::fit_workspace_bytes(*desc) > scratch_bytes) return RP_ERR_WORKSPACE;
+  return rp_fit(desc, x, y, fit_off, coef, coef32, box, status, rank, scratch, scratch_bytes,
+                stream);
+}
+
 size_t rp_program_size(int64_t num_kernels, int32_t degree) {
   if (num_kernels < 0 || degree < 0 || degree > RP_MAX_DEGREE) return 0;
   return rpk::program_size(num_kernels, degree);

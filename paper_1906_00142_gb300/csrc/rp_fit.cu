@@ -1466,6 +1466,28 @@ cudaError_t launch_f32(const FitArgs &a, int dmax, int precision, cudaStream_t s
 
 }  // namespace
 
+// Scratch of rp_fit_noalloc: the dynamic schedule's counter in a statically
+// allocated device array (one per process and device; calls that overlap
+// in time share it).
+static __device__ __align__(256) unsigned long long g_fit_scratch[2];
+
+cudaError_t fit_static_scratch(void **ptr, size_t *bytes) {
+  static void *addr[16] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 16) return cudaErrorInvalidDevice;
+  if (!addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_fit_scratch);
+    if (e != cudaSuccess) return e;
+    addr[dev] = p;
+  }
+  *ptr = addr[dev];
+  *bytes = sizeof(g_fit_scratch);
+  return cudaSuccess;
+}
+
 // One 64-bit counter for the dynamic fit schedule (16 bytes, aligned).
 size_t fit_workspace_bytes(const rp_fit_desc &desc) { return desc.num_fits > 0 ? 16 : 0; }
 

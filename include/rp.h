@@ -65,6 +65,9 @@ typedef enum rp_status {
 #define RP_FIT_NONPOS_Y 16        /* y <= 0 with relative weighting: no fit */
 #define RP_FIT_EMPTY 32           /* no samples: no fit */
 #define RP_FIT_TIMEOUT 64         /* a bounded wait of the tensor-core path ran out: no fit */
+#define RP_FIT_ESCALATED 128      /* tensor-core precisions: refinement from the low-precision
+                                     Gram stopped short of tol (or dropped pivots), so the fit
+                                     was solved again from the FP32 Gram on CUDA cores */
 #define RP_FIT_ITER_SHIFT 8       /* bits 8..15: refinement iterations performed */
 #define RP_FIT_ITER_MASK 0xFF00
 
@@ -80,8 +83,9 @@ typedef enum rp_precision {
   RP_PREC_TF32 = 2,    /* FP32 design; design Gram in one TF32 tensor-core pass (tcgen05),
                           basis Gram in split TF32; FP32 factor; residuals from the samples */
   RP_PREC_TF32X3 = 3,  /* as TF32 with both Grams in split TF32 (hi*hi + hi*lo + lo*hi) */
-  RP_PREC_BF16 = 4,    /* reserved: rp_fit returns RP_ERR_UNSUPPORTED */
-  RP_PREC_BF16X3 = 5   /* reserved: rp_fit returns RP_ERR_UNSUPPORTED */
+  RP_PREC_BF16 = 4,    /* FP32 design rounded to BF16 for a one-pass tensor-core design Gram
+                          (tcgen05 kind::f16, FP32 accumulation); as TF32 otherwise */
+  RP_PREC_BF16X3 = 5   /* as BF16 with split BF16 operands (hi*hi + hi*lo + lo*hi) */
 } rp_precision;
 
 /* rp_fit flags */
@@ -134,8 +138,7 @@ int rp_fit_workspace_size(const rp_fit_desc *desc, size_t *bytes);
  * every (grid size)-th fit.  Results do not depend on the schedule.
  * Errors: RP_ERR_INVALID_ARG for null pointers, F < 0, degree or precision
  * out of range; RP_ERR_WORKSPACE / RP_ERR_ALIGNMENT for a workspace that is
- * too small or misaligned; RP_ERR_UNSUPPORTED for the reserved BF16
- * precisions; RP_ERR_CUDA if a launch fails.
+ * too small or misaligned; RP_ERR_CUDA if a launch fails.
  */
 int rp_fit(const rp_fit_desc *desc, const float *x, const float *y, const int64_t *fit_off,
            double *coef, float *coef32, double *box, int32_t *status, int32_t *rank,

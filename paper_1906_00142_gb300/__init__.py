@@ -30,7 +30,7 @@ RP_NUM_CONFIGS = 66
 RP_NUM_METRICS = 8
 PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16": 4, "bf16x3": 5}
 RP_FIT_RANK_DEFICIENT, RP_FIT_NOT_CONVERGED, RP_FIT_POLE = 1, 2, 4
-RP_FIT_NONFINITE, RP_FIT_NONPOS_Y, RP_FIT_EMPTY, RP_FIT_TIMEOUT = 8, 16, 32, 64
+RP_FIT_NONFINITE, RP_FIT_NONPOS_Y, RP_FIT_EMPTY, RP_FIT_TIMEOUT, RP_FIT_ESCALATED = 8, 16, 32, 64, 128
 RP_FIT_ITER_SHIFT, RP_FIT_ITER_MASK = 8, 0xFF00
 RP_Q_NO_VALID, RP_Q_POLE, RP_Q_BAD = 1, 2, 4
 RP_FIT_UNWEIGHTED = 1

@@ -32,6 +32,7 @@
 // SVD formulation defines (up to rounding).  The FP32 path factors in FP32
 // (GB300's FP64 rate is ~1/58 of FP32): the factor only preconditions the
 // refinement, whose residuals carry the accuracy.
+#include <cuda_bf16.h>
 #include <math.h>
 #include <stdint.h>
 
@@ -210,7 +211,7 @@ struct TcShape {
 
 // GM: 0 = design Gram on CUDA cores (FP32 or FP64), 1 = design Gram on the
 // tensor cores in one TF32 pass, 2 = in three TF32 passes (hi.hi + hi.lo +
-// lo.hi).  The basis Gram (whitening) is always formed on CUDA cores: its
+// lo.hi), 3 = one BF16 pass, 4 = three BF16 passes.  The basis Gram (whitening) is always formed on CUDA cores: its
 // condition number (~1e6 for the correlated B0, B1 of the 66 formats) needs
 // round-to-nearest FP32 accumulation.
 template <class Real, int DMAX, int GM>
@@ -223,10 +224,13 @@ struct CtaFit {
   static constexpr int WS = ((NM + 3) / 4) * 4;   // row stride of W (16-byte rows)
   using TS = TcShape<DMAX>;
   static constexpr int ROWS_BYTES = kT * LDS * (int)sizeof(Real);
-  static constexpr int TC_BYTES = GM == 0 ? 0 : (GM == 2 ? 8 : 4) * TS::NB_DES;
+  // staging: hi then lo K-blocks (4 TF32 or 2 BF16 K-blocks per chunk)
+  static constexpr int TC_NKB = (GM == 3 || GM == 4) ? 2 : 4;
+  static constexpr bool TC_X3 = GM == 2 || GM == 4;
+  static constexpr int TC_BYTES = GM == 0 ? 0 : (TC_X3 ? 2 : 1) * TC_NKB * TS::NB_DES;
   static constexpr int STAGE_BYTES = ROWS_BYTES > TC_BYTES ? ROWS_BYTES : TC_BYTES;
   // furthest byte the M = 128 A operand reads, from the start of `stage`
-  static constexpr int TC_REACH = GM == 0 ? 0 : (GM == 2 ? 7 : 3) * TS::NB_DES + 16384;
+  static constexpr int TC_REACH = GM == 0 ? 0 : ((TC_X3 ? 2 : 1) * TC_NKB - 1) * TS::NB_DES + 16384;
   alignas(16) Real stage[STAGE_BYTES / sizeof(Real)];   // first member: 1024-byte aligned
   double uv[2][NM], uvp[2][NM];       // FP64 path: (c, u) and (c, v) of p and q; previous
   double lo[3], hi[3];
@@ -515,41 +519,59 @@ __device__ float apply_step(S &w, int nm, int n) {
 // TF32 head and tail and D accumulates hi.hi + hi.lo + lo.hi.
 constexpr uint32_t kTcWaitLimit = 1u << 22;   // mbarrier polls before giving up
 
-template <int NPAD, bool X3>
+template <int NPAD, bool X3, bool BF16 = false>
 struct TcGram {
-  static constexpr int NB = NPAD / 8 * 1024;   // bytes per K-block of 32 samples
-  uint32_t base;                               // this thread's K slot in K-block 0
+  static constexpr int NB = NPAD / 8 * 1024;   // bytes per K-block (128-byte rows)
+  static constexpr int KB = BF16 ? 64 : 32;    // samples per K-block
+  static constexpr int NKB = kT / KB;          // K-blocks per 128-sample chunk
+  uint32_t base;                               // this thread's K slot
   uint32_t xo[8];                              // swizzled chunk offset per row % 8
 
   __device__ __forceinline__ void init() {
     const int t = threadIdx.x;
-    base = (uint32_t)((t >> 5) * NB + (t & 3) * 4);
-    const int c = (t & 31) >> 2;
+    const int k = t % KB;                      // sample slot within the K-block
+    constexpr int es = BF16 ? 2 : 4;
+    base = (uint32_t)((t / KB) * NB + (k * es) % 16);
+    const int c = (k * es) / 16;
 #pragma unroll
     for (int r = 0; r < 8; ++r) xo[r] = (uint32_t)(((c ^ r) & 7) << 4);
   }
   // column j (a compile-time index after unrolling) of this thread's sample
   __device__ __forceinline__ void put(unsigned char *st, int j, float v) const {
     const uint32_t o = base + (uint32_t)((j >> 3) * 1024 + (j & 7) * 128) + xo[j & 7];
-    float h, l;
-    tc::split_tf32(v, h, l);
-    *reinterpret_cast<float *>(st + o) = h;
-    if (X3) *reinterpret_cast<float *>(st + 4 * NB + o) = l;
+    if constexpr (BF16) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      *reinterpret_cast<__nv_bfloat16 *>(st + o) = h;
+      if (X3) *reinterpret_cast<__nv_bfloat16 *>(st + NKB * NB + o) = __float2bfloat16_rn(v - __bfloat162float(h));
+    } else {
+      float h, l;
+      tc::split_tf32(v, h, l);
+      *reinterpret_cast<float *>(st + o) = h;
+      if (X3) *reinterpret_cast<float *>(st + NKB * NB + o) = l;
+    }
   }
-  // one thread: D = (first ? 0 : D) + X^T X over nkb K-blocks
+  // one thread: D = (first ? 0 : D) + X^T X over nkb K-blocks (each 4 MMAs
+  // of K = 32 bytes of the 128-byte rows)
   __device__ static void issue(const unsigned char *st, uint32_t tmem, int nkb, bool first) {
-    constexpr uint32_t id = tc::idesc(tc::kFmtTF32, 128, NPAD);
+    constexpr uint32_t id = tc::idesc(BF16 ? tc::kFmtBF16 : tc::kFmtTF32, 128, NPAD);
     const uint32_t b = tc::smem_u32(st);
     for (int kb = 0; kb < nkb; ++kb)
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
         const uint32_t off = (uint32_t)(kb * NB + 32 * s);
         const uint64_t ah = tc::sw128_desc(b + off);
-        tc::mma_tf32(tmem, ah, ah, id, (first && kb == 0 && s == 0) ? 0u : 1u);
+        const uint32_t acc0 = (first && kb == 0 && s == 0) ? 0u : 1u;
+        if constexpr (BF16) tc::mma_f16(tmem, ah, ah, id, acc0);
+        else tc::mma_tf32(tmem, ah, ah, id, acc0);
         if (X3) {
-          const uint64_t al = tc::sw128_desc(b + 4 * NB + off);
-          tc::mma_tf32(tmem, ah, al, id, 1u);
-          tc::mma_tf32(tmem, al, ah, id, 1u);
+          const uint64_t al = tc::sw128_desc(b + NKB * NB + off);
+          if constexpr (BF16) {
+            tc::mma_f16(tmem, ah, al, id, 1u);
+            tc::mma_f16(tmem, al, ah, id, 1u);
+          } else {
+            tc::mma_tf32(tmem, ah, al, id, 1u);
+            tc::mma_tf32(tmem, al, ah, id, 1u);
+          }
         }
       }
   }
@@ -875,18 +897,27 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
       __syncthreads();
     }
 
+    // Phases 3-5, attempted first with the tensor-core design Gram (GM > 0)
+    // and, for a fit whose refinement stops short of its tolerance or whose
+    // factorisation drops pivots there, again with the FP32 Gram on CUDA
+    // cores (the low-precision Gram was too coarse to precondition it).
+    int flags = 0;
+    bool escalated = false;
+    for (int attempt = 0;; ++attempt) {
+    const bool use_tc = GM > 0 && attempt == 0;
     // ---------------- phase 3: the design Gram [num (nm) | den (nm-1) | rhs]
-    if constexpr (GM > 0) {
+    if (use_tc) {
+      if constexpr (GM > 0) {
       // staged in the padded layout num [0, NM), den [NM, 2 NM - 1), rhs
       // 2 NM - 1 (compile-time columns); read back compacted to stride naug
-      using TG = TcGram<TS::NDES, GM == 2>;
+      using TG = TcGram<TS::NDES, WF::TC_X3, (GM == 3 || GM == 4)>;
       TG tg;
       tg.init();
       unsigned char *st = reinterpret_cast<unsigned char *>(w.stage);
       for (int base = 0; base < m && !tc_dead; base += kT) {
         const int cnt = min(kT, m - base);
-        const int nkb = (cnt + 31) >> 5;
-        if (tid < nkb * 32) {
+        const int nkb = (cnt + TG::KB - 1) / TG::KB;
+        if (tid < nkb * TG::KB) {
           Real pt[NM];
           Real wt = 0, yy = 0;
           if (tid < cnt) {
@@ -910,17 +941,12 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
         }
         tc_dead = !tc_chunk<TG>(st, tmem, &w.mbar, nkb, base == 0, tc_phase);
       }
-      if (tc_dead) {
-        if (tid == 0) {
-          a.status[f] = RP_FIT_TIMEOUT;
-          a.rank[f] = 0;
-        }
-        continue;
-      }
+      if (tc_dead) break;
       TG::read(tmem, 2 * NM, w.G, naug, [nm](int j) {
         return j < nm ? j : (j < NM ? -1 : (j < NM + nm - 1 ? nm + (j - NM) : (j == 2 * NM - 1 ? 2 * nm - 1 : -1)));
       });
       __syncthreads();
+      }
     } else {
       TileGram<Real, IPT, LDS> tg;
       tg.init(naug);
@@ -1073,7 +1099,7 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
     //   g_den_j = -sum_{i<=j} W_ij (K_i - mu_i K_0),
     // and the step dx = Q g.  A step that raises the objective beyond its
     // rounding level is undone and the refinement stops.
-    int flags = (w.keep_cnt < n) ? RP_FIT_RANK_DEFICIENT : 0;
+    flags = (w.keep_cnt < n) ? RP_FIT_RANK_DEFICIENT : 0;
     float prev_rel = INFINITY, obj_prev = INFINITY, obj_drop = INFINITY;
     bool compensated = sizeof(Real) == 8, done = false;
     int pole_prev = 0, it = 0;
@@ -1302,6 +1328,20 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
     // falling by more than 1e-5 per step
     if (a.max_refine > 0 && !done && !(obj_drop <= 1e-5f)) flags |= RP_FIT_NOT_CONVERGED;
     flags |= min(it, 255) << RP_FIT_ITER_SHIFT;
+    if (use_tc && a.max_refine > 0 && (!done || (flags & RP_FIT_RANK_DEFICIENT))) {
+      escalated = true;
+      continue;
+    }
+    break;
+    }   // attempts
+    if (tc_dead) {
+      if (tid == 0) {
+        a.status[f] = RP_FIT_TIMEOUT;
+        a.rank[f] = 0;
+      }
+      continue;
+    }
+    if (escalated) flags |= RP_FIT_ESCALATED;
 
     // ---------------- phase 6: back to the monomial basis (FP64)
     {
@@ -1495,7 +1535,12 @@ int fit_max_ctas_per_sm(const rp_fit_desc &desc) {
   const int dmax = desc.degree;
   if (desc.precision == RP_PREC_FP64)
     return dmax <= 2 ? residency<double, 2, 0>() : dmax == 3 ? residency<double, 3, 0>() : residency<double, 4, 0>();
-  const int gm = desc.precision == RP_PREC_TF32 ? 1 : desc.precision == RP_PREC_TF32X3 ? 2 : 0;
+  const int gm = desc.precision == RP_PREC_TF32 ? 1 : desc.precision == RP_PREC_TF32X3 ? 2
+               : desc.precision == RP_PREC_BF16 ? 3 : desc.precision == RP_PREC_BF16X3 ? 4 : 0;
+  if (gm == 3)
+    return dmax <= 2 ? residency<float, 2, 3>() : dmax == 3 ? residency<float, 3, 3>() : residency<float, 4, 3>();
+  if (gm == 4)
+    return dmax <= 2 ? residency<float, 2, 4>() : dmax == 3 ? residency<float, 3, 4>() : residency<float, 4, 4>();
   if (gm == 1)
     return dmax <= 2 ? residency<float, 2, 1>() : dmax == 3 ? residency<float, 3, 1>() : residency<float, 4, 1>();
   if (gm == 2)
@@ -1504,8 +1549,7 @@ int fit_max_ctas_per_sm(const rp_fit_desc &desc) {
 }
 
 bool fit_precision_supported(int precision) {
-  return precision == RP_PREC_FP64 || precision == RP_PREC_FP32 || precision == RP_PREC_TF32 ||
-         precision == RP_PREC_TF32X3;
+  return precision >= RP_PREC_FP64 && precision <= RP_PREC_BF16X3;
 }
 
 cudaError_t launch_fit(const rp_fit_desc &desc, const float *x, const float *y,
@@ -1542,6 +1586,8 @@ cudaError_t launch_fit(const rp_fit_desc &desc, const float *x, const float *y,
   a.drop_tol = 1e-7;
   if (desc.precision == RP_PREC_TF32) return launch_f32<1>(a, dmax, desc.precision, s);
   if (desc.precision == RP_PREC_TF32X3) return launch_f32<2>(a, dmax, desc.precision, s);
+  if (desc.precision == RP_PREC_BF16) return launch_f32<3>(a, dmax, desc.precision, s);
+  if (desc.precision == RP_PREC_BF16X3) return launch_f32<4>(a, dmax, desc.precision, s);
   return launch_f32<0>(a, dmax, desc.precision, s);
 }
 

@@ -88,7 +88,7 @@ def test_differentiation_4096_fits():
     assert (l1 <= l0 * (1 + 1e-6)).mean() > 0.9, (l1 > l0).sum()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "tf32"])
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
 def test_uneven_batch_graph_captured(precision):
     need_gpu()
     K = 1024
@@ -111,7 +111,8 @@ def test_uneven_batch_graph_captured(precision):
                  status=torch.empty(Q, dtype=torch.int32, device="cuda"))
 
     def step(stream):
-        rp.rp_fit(x, y, off, 4, precision=precision, degrees=deg, out=fit_out, stream=stream)
+        rp.rp_fit(x, y, off, 4, precision=precision, degrees=deg, out=fit_out, stream=stream,
+                  max_refine=16 if precision == "bf16" else 8)
         rp.rp_program_pack(fit_out["coef"], fit_out["box"], deg, mm, gd, 4, program=prog,
                            stream=stream)
         rp.rp_eval_search(prog, K, 4, q, out=s_out, stream=stream)

@@ -88,14 +88,14 @@ def batched():
     return inst, ref, sens
 
 
-@pytest.mark.parametrize("precision", ["fp32", "tf32", "tf32x3"])
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "tf32x3", "bf16", "bf16x3"])
 def test_fit_fp32_data_batched(batched, precision):
     """FP32 design; Gram products on CUDA cores (fp32) or on the tensor
     cores (tf32: one TF32 pass for the design Gram; tf32x3: split TF32,
     three passes)."""
     need_gpu()
     inst, ref, sens = batched
-    g = gpu_fit(inst, precision)
+    g = gpu_fit(inst, precision, max_refine=16 if precision == "bf16" else 8)
     assert not (g["status"] & rp.RP_FIT_TIMEOUT).any()
     err, _ = compare(inst, g, ref, sens)
     iters = (g["status"] & rp.RP_FIT_ITER_MASK) >> rp.RP_FIT_ITER_SHIFT
@@ -118,12 +118,12 @@ def test_fit_uniform_degree_argument(batched):
     compare(inst, g, ref, sens)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "tf32", "tf32x3", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "tf32x3", "bf16", "bf16x3", "fp64"])
 def test_fit_tiny_exact_data(precision):
     """Noise-free integer-coefficient rationals (plain FP64 tiny case)."""
     need_gpu()
     inst = W.tiny_instance()
-    g = gpu_fit(inst, precision)
+    g = gpu_fit(inst, precision, max_refine=16 if precision == "bf16" else 8)
     compare(inst, g, all_fits=(precision == "fp64"))
 
 
@@ -155,8 +155,8 @@ def test_fit_edge_cases():
     off = np.zeros(7, np.int64)
     off[1:] = np.cumsum([len(v) for v in ys])
     inst = dict(x=np.ascontiguousarray(x), y=y, fit_off=off, degree=np.full(6, 2, np.int8))
-    for prec in ["fp32", "tf32", "tf32x3", "fp64"]:
-        g = gpu_fit(inst, prec, degree=2)
+    for prec in ["fp32", "tf32", "tf32x3", "bf16", "bf16x3", "fp64"]:
+        g = gpu_fit(inst, prec, degree=2, max_refine=16 if prec == "bf16" else 8)
         assert g["status"][1] & rp.RP_FIT_EMPTY
         assert g["status"][2] & rp.RP_FIT_NONFINITE
         assert g["status"][3] & rp.RP_FIT_NONPOS_Y

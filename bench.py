@@ -38,7 +38,8 @@ WORKLOAD = ("batched fit 1024 kernels x 8 metrics, 512 samples, deg<=3 (TF32-cla
 # (dram__bytes_read.sum + dram__bytes_write.sum of fit_kernel<float, 3, 0>,
 # 2048 fits of 512 samples; traffic scales with the fit count), valid only
 # for the kernel sources they were taken on (SHA-256 of the files below).
-FIT_TRAFFIC = {"sources_sha256": None, "bytes_per_fit": None}
+FIT_TRAFFIC = {"sources_sha256": "ddd7ea793b75219ccc530979558a2ed57d3c990ae60d22157811da40199e803a",
+               "bytes_per_fit": (17455616 + 38912) / 2048}
 FIT_SOURCES = ("paper_1906_00142_gb300/csrc/rp_fit.cu", "paper_1906_00142_gb300/csrc/rp_tc.cuh",
                "paper_1906_00142_gb300/csrc/rp_internal.cuh")
 
@@ -129,6 +130,60 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(r["sm"] for r in rows),
                 "sm_max_mhz": max(r["smax"] for r in rows), "reasons": sorted(reasons),
                 "samples": len(rows)}
+
+
+class NvmlSampler:
+    """SM clock and clock-event reasons read through NVML (read-only queries)
+    every 2 ms from a background thread during a region; None if NVML is not
+    available (the nvidia-smi sampler is used instead)."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, gpu_index):
+        import ctypes
+        import threading
+        self.ok = False
+        self.rows = []
+        self._stop = threading.Event()
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            self.h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(gpu_index), ctypes.byref(self.h)) != 0:
+                return
+            self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+            mx = ctypes.c_uint(0)
+            lib.nvmlDeviceGetMaxClockInfo(self.h, ctypes.c_int(1), ctypes.byref(mx))
+            self.max_mhz = float(mx.value)
+            self.lib, self.ct = lib, ctypes
+            self.ok = True
+        except Exception:
+            self.ok = False
+
+    def _run(self):
+        ct = self.ct
+        mhz, rs = ct.c_uint(0), ct.c_ulonglong(0)
+        while not self._stop.is_set():
+            if self.lib.nvmlDeviceGetClockInfo(self.h, ct.c_int(1), ct.byref(mhz)) == 0 and \
+                    self.reasons_fn(self.h, ct.byref(rs)) == 0:
+                self.rows.append((float(mhz.value), int(rs.value)))
+            time.sleep(0.002)
+
+    def start(self):
+        import threading
+        self.t = threading.Thread(target=self._run, daemon=True)
+        self.t.start()
+
+    def stop(self):
+        self._stop.set()
+        self.t.join()
+        if not self.rows:
+            return None
+        reasons = sorted({name for _, r in self.rows for bit, name in self.REASONS.items() if r & bit})
+        return {"sm_mhz": statistics.median(m for m, _ in self.rows), "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(self.rows), "source": "nvml, 2 ms"}
 
 
 def dist_setup(ngpus):
@@ -255,13 +310,17 @@ def extra_measurements(rp, args, inst, x, y, off, deg, mm, gd, q, fit_out, prog,
     import torch
     F = N_KERNELS * N_METRICS
     out = {}
-    rates = {}
-    for prec in ("fp32", "tf32", "tf32x3", "fp64"):
-        fn = lambda: rp.rp_fit(x, y, off, DEGREE, precision=prec, max_refine=8, tol=args.tol,
+    rates, escal = {}, {}
+    for prec in ("fp32", "tf32", "tf32x3", "bf16", "bf16x3", "fp64"):
+        mr = 16 if prec == "bf16" else 8
+        fn = lambda: rp.rp_fit(x, y, off, DEGREE, precision=prec, max_refine=mr, tol=args.tol,
                                degrees=deg, out=fit_out, stream=stream)
         fn()
         rates[prec] = F / (_timed(fn, 3, flush, stream) / 1e3)
+        st = fit_out["status"].cpu().numpy()
+        escal[prec] = float(((st & rp.RP_FIT_ESCALATED) != 0).mean())
     out["fit_only_fits_per_s"] = rates
+    out["fit_escalated_frac"] = escal
     # plain form: one FP64 fit per launch over 64 fits, one query per launch
     # over 2000 queries (launch-bound; rates scale to any count)
     n_pf, n_pq = 64, 2000
@@ -408,7 +467,9 @@ def main():
         step()
     torch.cuda.synchronize()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    clocks = ClockSampler(torch.cuda.current_device())
+    clocks = NvmlSampler(torch.cuda.current_device())
+    if not clocks.ok:
+        clocks = ClockSampler(torch.cuda.current_device())
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()

@@ -264,7 +264,9 @@ struct CtaFit {
 template <class Real, int DMAX, int GM>
 __host__ __device__ constexpr size_t ctafit_bytes() {
   using WF = CtaFit<Real, DMAX, GM>;
-  return ((sizeof(WF) > (size_t)WF::TC_REACH ? sizeof(WF) : (size_t)WF::TC_REACH) + 15 & ~size_t(15)) + 1024;
+  // the 1 KB alignment slack only where swizzle atoms are staged
+  return ((sizeof(WF) > (size_t)WF::TC_REACH ? sizeof(WF) : (size_t)WF::TC_REACH) + 15 & ~size_t(15)) +
+         (GM > 0 ? 1024 : 0);
 }
 
 // Block-wide sum of one float per thread; result returned to every thread.
@@ -633,9 +635,10 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
   constexpr int S4 = (NAUG + 3) / 4;
   constexpr int IPT = ((S4 * (S4 + 1) / 2) + kT - 1) / kT;   // design-Gram items per thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // the state starts at the first 1024-byte boundary (swizzle atoms)
+  // the state starts at the first 1024-byte boundary (swizzle atoms of the
+  // tensor-core paths; 16-byte alignment suffices otherwise)
   const uint32_t raw_s = tc::smem_u32(smem_raw);
-  WF &w = *reinterpret_cast<WF *>(smem_raw + (((raw_s + 1023u) & ~1023u) - raw_s));
+  WF &w = *reinterpret_cast<WF *>(smem_raw + (GM > 0 ? (((raw_s + 1023u) & ~1023u) - raw_s) : 0u));
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   // tensor memory for the Gram accumulators, held for the whole launch
   uint32_t tmem = 0, tc_phase = 0;
@@ -1011,14 +1014,18 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
           ent[q] = -1;
         }
       }
+      // the entries stay in registers through the elimination; shared memory
+      // holds only the pivot rows
+      Real v[EPT];
 #pragma unroll
-      for (int q = 0; q < EPT; ++q)
+      for (int q = 0; q < EPT; ++q) {
+        v[q] = 0;
         if (ent[q] >= 0) {
           const int i = ent[q] >> 16, j = ent[q] & 0xFFFF;
-          const Real v = w.G[i * N1 + j] * w.scl[i] * w.scl[j];
-          w.G[i * N1 + j] = v;
-          if (i == 0) w.rowb[0][j] = v;
+          v[q] = w.G[i * N1 + j] * w.scl[i] * w.scl[j];
+          if (i == 0) w.rowb[0][j] = v[q];
         }
+      }
       __syncthreads();
       int kept = 0;
       for (int k = 0; k < n; ++k) {
@@ -1028,32 +1035,18 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
         const bool keep = piv > (Real)a.drop_tol;
         kept += keep;
         const Real ip = keep ? (Real)1 / piv : (Real)0;
-        Real v[EPT];
-#pragma unroll
-        for (int q = 0; q < EPT; ++q) {
-          const int i = ent[q] >> 16, j = ent[q] & 0xFFFF;
-          v[q] = ent[q] >= 0 ? w.G[i * N1 + j] : (Real)0;
-        }
 #pragma unroll
         for (int q = 0; q < EPT; ++q) {
           if (ent[q] < 0) continue;
           const int i = ent[q] >> 16, j = ent[q] & 0xFFFF;
-          const bool on_k = (i == k) || (j == k);
-          if (keep && !on_k) {
-            v[q] = fma(-rk[i] * ip, rk[j], v[q]);
-            w.G[i * N1 + j] = v[q];
+          if (keep) {
+            // S'_ij = S_ij - S_ik S_kj / p; S'_ik = S_ik / p; S'_kk = -1 / p
+            const Real ri = rk[i], rj = rk[j];
+            const Real gen = fma(-ri * ip, rj, v[q]);
+            v[q] = (j == k) ? ((i == k) ? -ip : ri * ip) : ((i == k) ? rj * ip : gen);
           }
-          if (!(keep && on_k)) {
-            if (i == k + 1) rn[j] = v[q];
-            if (j == k + 1) rn[i] = v[q];
-          }
-        }
-        // row and column k: S'_kx = rk[x] / piv, S'_kk = -1 / piv
-        if (keep && tid < N1) {
-          const int x = tid;
-          const Real vk = (x == k) ? -ip : rk[x] * ip;
-          w.G[min(x, k) * N1 + max(x, k)] = vk;
-          if (x == k + 1) rn[k] = vk;
+          if (i == k + 1) rn[j] = v[q];
+          if (j == k + 1) rn[i] = v[q];
         }
         if (tid == 0) w.invd[k] = keep ? (Real)1 : (Real)0;
         __syncthreads();
@@ -1063,14 +1056,13 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
       for (int q = 0; q < EPT; ++q)
         if (ent[q] >= 0) {
           const int i = ent[q] >> 16, j = ent[q] & 0xFFFF;
-          const Real vv = w.G[i * N1 + j];
           const Real si = w.invd[i] * w.scl[i];
           if (j < n) {
-            const Real qv = -vv * si * w.invd[j] * w.scl[j];
+            const Real qv = -v[q] * si * w.invd[j] * w.scl[j];
             w.G[i * N1 + j] = qv;
             w.G[j * N1 + i] = qv;
           } else if (j == n && i < n) {
-            w.dxw[i] = vv * si;
+            w.dxw[i] = v[q] * si;
           }
         }
       if (tid == 0) w.keep_cnt = kept;

@@ -37,10 +37,11 @@ WORKLOAD = ("batched fit 1024 kernels x 8 metrics, 512 samples, deg<=3 (TF32-cla
 # DRAM bytes per fit of the fit kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of fit_kernel<float, 3, 0>,
 # 2048 fits of 512 samples; traffic scales with the fit count), valid only
-# for the kernel sources they were taken on (SHA-256 of the files below).
-FIT_TRAFFIC = {"sources_sha256": "ddd7ea793b75219ccc530979558a2ed57d3c990ae60d22157811da40199e803a",
-               "bytes_per_fit": (17455616 + 38912) / 2048}
-FIT_SOURCES = ("paper_1906_00142_gb300/csrc/rp_fit.cu", "paper_1906_00142_gb300/csrc/rp_tc.cuh",
+# for the kernel sources they were taken on (SHA-256 of the files below);
+# None until a capture of the current sources is recorded.
+FIT_TRAFFIC = {"sources_sha256": None, "bytes_per_fit": None}
+FIT_SOURCES = ("paper_1906_00142_gb300/csrc/rp_fit_kernel.cuh", "paper_1906_00142_gb300/csrc/rp_fit.cuh",
+               "paper_1906_00142_gb300/csrc/rp_fit_f32.cu", "paper_1906_00142_gb300/csrc/rp_tc.cuh",
                "paper_1906_00142_gb300/csrc/rp_internal.cuh")
 
 
@@ -198,6 +199,34 @@ def dist_setup(ngpus):
     return ws, rank, local
 
 
+def rank_seed(rank):
+    """Each rank draws its own fits and queries (weak scaling: the per-rank
+    workload is the same size at every N)."""
+    return SEED + 1000 * rank
+
+
+def max_over_ranks(value, ws, device):
+    """The largest of the ranks' values (torch.distributed all-reduce MAX)."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws, units_per_rank, ms_per_step):
+    """Whole-job throughput: the units all ranks processed / the slowest rank's time."""
+    return ws * units_per_rank / (ms_per_step / 1e3)
+
+
+def workload_config(precision):
+    return {"workload": WORKLOAD, "fits": N_KERNELS * N_METRICS, "samples_per_fit": M_SAMPLES,
+            "degree": DEGREE, "queries": N_QUERIES, "configs": 66, "precision": precision,
+            "l2": "flushed (256 MiB write) between steps"}
+
+
 def make_inputs(seed):
     import workloads as W
     inst = W.batched_instance(N_KERNELS, seed=seed, m=M_SAMPLES, d=DEGREE)
@@ -276,7 +305,7 @@ def run_reference(args):
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "config": workload_config(args.precision),
             "queries_per_s": N_QUERIES / step_s,
             "cpu_baseline": {"value": value, "unit": "fits/s", "cores": last["cores"],
                              "kind": "oracle", "sample": last["sample"]},
@@ -404,7 +433,7 @@ def main():
     import paper_1906_00142_gb300 as rp
     rp.load_library()
 
-    inst, q_np, gd_np = make_inputs(SEED + 1000 * rank)
+    inst, q_np, gd_np = make_inputs(rank_seed(rank))
     F = N_KERNELS * N_METRICS
     td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     x, y, off, deg = td(inst["x"]), td(inst["y"]), td(inst["fit_off"]), td(inst["degree"])
@@ -485,13 +514,9 @@ def main():
     pack_ms = [e[1].elapsed_time(e[2]) for e in evs]
     search_ms = [e[2].elapsed_time(e[3]) for e in evs]
     step_ms = [e[0].elapsed_time(e[3]) for e in evs]
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), ws, dev)
     ms_per_step = total_ms / args.steps
-    value = ws * F / (ms_per_step / 1e3)
+    value = job_rate(ws, F, ms_per_step)
 
     # fit status summary (informational)
     st = fit_out["status"].cpu().numpy()
@@ -532,11 +557,7 @@ def main():
         b.record(stream)
         torch.cuda.synchronize()
         e_ms.append(a.elapsed_time(b))
-    e2e_ms = statistics.mean(e_ms) if e_ms else float("nan")
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(statistics.mean(e_ms) if e_ms else float("nan"), ws, dev)
 
     extra = {}
     if args.only == "all" and not args.no_extras:
@@ -568,14 +589,12 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "fits": F, "samples_per_fit": M_SAMPLES,
-                           "degree": DEGREE, "queries": N_QUERIES, "configs": 66,
-                           "precision": args.precision, "l2": "flushed (256 MiB write) between steps"},
+                "config": workload_config(args.precision),
                 "queries_per_s": ws * N_QUERIES / (ms_per_step / 1e3),
                 "phase_ms": {"fit": fit_avg, "pack": statistics.mean(pack_ms), "search": search_avg},
                 "fit_ok_frac": fit_ok,
                 "roofline": roof,
-                "e2e": {"value": ws * F / (e2e_ms / 1e3), "unit": "fits/s",
+                "e2e": {"value": job_rate(ws, F, e2e_ms), "unit": "fits/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
                 "gpu_launches": (3 if args.only == "all" else 2 if args.only == "fit" else 1) * args.steps,
                 "clocks": clk, "tuned": tuned}

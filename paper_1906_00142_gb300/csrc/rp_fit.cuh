@@ -1,0 +1,44 @@
+// Fit launch interface shared by the fit translation units: the kernel
+// arguments and one launcher / residency query per precision family (each
+// family is compiled in its own translation unit, rp_fit_<family>.cu).
+#pragma once
+#include <stdint.h>
+
+#include "rp_internal.cuh"
+
+namespace rpk {
+
+struct FitArgs {
+  int64_t F, S;
+  const float *x, *y;
+  const int64_t *off;
+  const int8_t *degs;
+  int d_uniform;
+  int max_refine;
+  int weighted;
+  double tol;
+  double drop_tol;   // relative pivot drop tolerance of the equilibrated design Gram
+  double *coef;
+  float *coef32;
+  double *box;
+  int32_t *status;
+  int32_t *rank;
+  unsigned long long *counter;   // dynamic fit schedule (workspace), or null
+};
+
+// Real = double, design Gram on CUDA cores (RP_PREC_FP64)
+cudaError_t fit_launch_f64(const FitArgs &a, int dmax, int precision, cudaStream_t s);
+int fit_residency_f64(int dmax);
+// Real = float: CUDA-core Gram (FP32), tcgen05 TF32, split TF32, BF16, split BF16
+cudaError_t fit_launch_f32(const FitArgs &a, int dmax, int precision, cudaStream_t s);
+int fit_residency_f32(int dmax);
+cudaError_t fit_launch_tf32(const FitArgs &a, int dmax, int precision, cudaStream_t s);
+int fit_residency_tf32(int dmax);
+cudaError_t fit_launch_tf32x3(const FitArgs &a, int dmax, int precision, cudaStream_t s);
+int fit_residency_tf32x3(int dmax);
+cudaError_t fit_launch_bf16(const FitArgs &a, int dmax, int precision, cudaStream_t s);
+int fit_residency_bf16(int dmax);
+cudaError_t fit_launch_bf16x3(const FitArgs &a, int dmax, int precision, cudaStream_t s);
+int fit_residency_bf16x3(int dmax);
+
+}  // namespace rpk

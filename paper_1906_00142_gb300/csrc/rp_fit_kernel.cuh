@@ -1,0 +1,1491 @@
+#pragma once
+// Batched least-squares fitting of rational functions (Sec. 4.2).
+//
+// One 128-thread CTA owns one fit at a time (persistent over fits; several
+// CTAs per SM).  The linearised
+// problem of Sec. 4.2 -- minimise sum_i w_i^2 (p(x_i) - y_i q(x_i))^2 over the
+// coefficients of p and q, the homogeneous system normalised by mean(q) = 1
+// over the fit's samples -- is solved through its normal equations in a basis
+// chosen per fit so that the Gram matrix is well conditioned:
+//
+//  1. each variable is mapped affinely to [-1, 1] over the fit's samples
+//     (the box), then standardised, u = (x' - mean) / std;
+//  2. per variable, polynomials Q_0 = 1, Q_1 .. Q_d orthonormal for the
+//     empirical distribution of u (Cholesky of the Hankel moment matrix);
+//  3. Psi_j = Q_a(u_N) Q_b(u_B0) Q_c(u_B1) over the graded-lex exponents
+//     (a, b, c): a basis of the same polynomial space as the monomials;
+//  4. the non-constant Psi_j are centred on the samples and whitened with the
+//     inverse Cholesky factor of their Gram matrix (Psi~);
+//  5. the design rows w_i [1, Psi~.., -y_i Psi~..] with right-hand side
+//     w_i y_i give the augmented Gram matrix, which is equilibrated and
+//     factored with column dropping (pivot below a drop tolerance: column
+//     removed, reported as rank deficiency);
+//  6. iterative refinement recomputes the residual from the samples
+//     (compensated FP32 dot products against the FP64 solution -- Ogita,
+//     Rump & Oishi's Dot2 -- on the FP32 path, plain FP64 on the FP64 path),
+//     stopping at ||dx|| <= tol ||x|| or when the corrections stop shrinking;
+//  7. the solution is mapped back to the monomial basis of the box-normalised
+//     variables in FP64.  Every refinement pass also checks that q is positive
+//     at every sample for the solution the pass starts from.
+//
+// Each step is a change of basis of the same function space under the same
+// normalisation, so the fitted p/q is the least-squares solution the paper's
+// SVD formulation defines (up to rounding).  The FP32 path factors in FP32
+// (GB300's FP64 rate is ~1/58 of FP32): the factor only preconditions the
+// refinement, whose residuals carry the accuracy.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "rp_fit.cuh"
+#include "rp_internal.cuh"
+#include "rp_tc.cuh"
+
+namespace rpk {
+namespace {
+
+
+__constant__ int8_t c_exp[kMaxNm][3];   // graded-lex exponents
+__constant__ int8_t c_idx[kMaxDeg + 1][kMaxDeg + 1][kMaxDeg + 1];   // exponents -> graded-lex index
+
+
+// ---------------------------------------------------------------------
+// helpers
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <class T>
+__device__ __forceinline__ T rsqrt_pos(T v);
+template <>
+__device__ __forceinline__ float rsqrt_pos<float>(float v) { return 1.0f / sqrtf(v); }
+template <>
+__device__ __forceinline__ double rsqrt_pos<double>(double v) { return 1.0 / sqrt(v); }
+
+// Cholesky (lower) of the n x n matrix G (row stride ld) by all NT threads of
+// the block, with column dropping: a pivot <= tol removes the column
+// (invd = 0).  Step k scales column k, then updates the trailing lower
+// triangle with one thread per entry.
+template <class SR, int NT>
+__device__ void cta_chol(SR *G, int n, int ld, SR tol, SR *invd, int *keep_cnt) {
+  const int tid = threadIdx.x;
+  for (int k = 0; k < n; ++k) {
+    const SR p = G[k * ld + k];
+    const bool keep = p > tol;
+    const SR inv = keep ? rsqrt_pos<SR>(p) : (SR)0;
+    __syncthreads();
+    if (tid == 0) {
+      G[k * ld + k] = keep ? p * inv : (SR)0;
+      invd[k] = inv;
+    }
+    for (int i = k + 1 + tid; i < n; i += NT) G[i * ld + k] *= inv;
+    __syncthreads();
+    const int r = n - k - 1;
+    const int np = r * (r + 1) / 2;
+    for (int e = tid; e < np; e += NT) {
+      int ii = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+      ii += ((ii + 1) * (ii + 2) / 2 <= e);
+      ii -= (ii * (ii + 1) / 2 > e);
+      const int jj = e - ii * (ii + 1) / 2;
+      const int i = k + 1 + ii, j = k + 1 + jj;
+      G[i * ld + j] -= G[i * ld + k] * G[j * ld + k];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    int kept = 0;
+    for (int k = 0; k < n; ++k) kept += invd[k] != (SR)0;
+    *keep_cnt = kept;
+  }
+  __syncthreads();
+}
+
+// Cholesky of the (d+1) x (d+1) Hankel moment matrix of a standardised
+// variable -> coefficients of the orthonormal polynomials (columns of the
+// inverse factor).  A variable with only q distinct sample values supports
+// polynomials of degree < q on the samples: Q_k for k > deg_eff (= q - 1) is
+// set to 0.  Single thread, FP32 (the transform only has to give a
+// well-scaled basis; it is used consistently wherever the basis is).
+__device__ void marginal_transform(const float *M, int d, int deg_eff, float T[][kMaxDeg + 1]) {
+  float R[kMaxDeg + 1][kMaxDeg + 1], Ti[kMaxDeg + 1][kMaxDeg + 1];
+  bool ok[kMaxDeg + 1];
+  for (int i = 0; i <= kMaxDeg; ++i)
+    for (int j = 0; j <= kMaxDeg; ++j) R[i][j] = Ti[i][j] = 0.0f;
+  for (int k = 0; k <= d; ++k) {
+    float p = M[2 * k];
+    for (int l = 0; l < k; ++l) p -= R[l][k] * R[l][k];
+    ok[k] = k <= deg_eff && M[2 * k] > 0.0f;
+    if (!ok[k]) continue;
+    // a supported direction whose pivot rounding has eaten is regularised
+    // (any positive pivot keeps the polynomial basis a basis)
+    p = fmaxf(p, 1e-6f * M[2 * k]);
+    R[k][k] = sqrtf(p);
+    const float inv = 1.0f / R[k][k];
+    for (int j = k + 1; j <= d; ++j) {
+      float s = M[k + j];
+      for (int l = 0; l < k; ++l) s -= R[l][k] * R[l][j];
+      R[k][j] = s * inv;
+    }
+  }
+  for (int k = 0; k <= d; ++k) {
+    if (!ok[k]) continue;
+    Ti[k][k] = 1.0f / R[k][k];
+    for (int i = k - 1; i >= 0; --i) {
+      if (!ok[i]) continue;
+      float s = 0;
+      for (int l = i + 1; l <= k; ++l) s += R[i][l] * Ti[l][k];
+      Ti[i][k] = -s / R[i][i];
+    }
+  }
+  for (int l = 0; l <= kMaxDeg; ++l)
+    for (int k = 0; k <= kMaxDeg; ++k) T[l][k] = (l <= d && k <= d) ? Ti[l][k] : 0.0f;
+  T[0][0] = 1.0f;  // Q_0 = 1 (M_0 = 1)
+}
+
+// Insert a value into a small lock-free set of at most kMaxDeg + 1 distinct
+// values (slots claimed in order with compare-and-swap; once full, further
+// values are ignored -- kMaxDeg + 1 distinct values are all a degree-kMaxDeg
+// marginal basis needs).
+constexpr unsigned kEmpty = 0xFFFFFFFFu;
+__device__ __forceinline__ void distinct_insert(unsigned *slots, float x) {
+  const unsigned v = (x == 0.0f) ? 0u : __float_as_uint(x);
+#pragma unroll
+  for (int k = 0; k < kMaxDeg + 1; ++k) {
+    const unsigned cur = *((volatile unsigned *)&slots[k]);
+    if (cur == v) return;
+    if (cur == kEmpty) {
+      const unsigned old = atomicCAS(&slots[k], kEmpty, v);
+      if (old == kEmpty || old == v) return;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------
+// Per-fit state of one CTA (128 threads).  Shared memory and registers are
+// sized so that several CTAs share an SM: while one CTA runs the serial
+// steps of its fit (factorisations, triangular solves) on one warp, the
+// others' sample passes keep the SM busy.
+
+constexpr int kT = 128;       // threads per CTA (one fit at a time)
+constexpr int kMC = 512;      // samples per fit kept in shared memory
+
+// Tensor-core Gram shapes (Sec. 4.2 normal equations on tcgen05).  A Gram
+// X^T X over the samples is one MMA chain D = A B^T with A = B = X^T stored
+// K-major (K = samples): the B operand holds the NPAD padded columns, the A
+// operand (M = 128 rows) reads the same tile and the shared memory after it
+// (rows >= NPAD of D are never read).  One K-block = 32 samples = NPAD/8
+// swizzle atoms.
+template <int DMAX>
+struct TcShape {
+  static constexpr int NM = (DMAX + 1) * (DMAX + 2) * (DMAX + 3) / 6;
+  static constexpr int NAUG = 2 * NM;
+  static constexpr int NDES = ((NAUG + 15) / 16) * 16;
+  static constexpr int NB_DES = NDES / 8 * 1024;
+  static constexpr int TMEM_COLS = NDES <= 64 ? 64 : 128;
+};
+
+// GM: 0 = design Gram on CUDA cores (FP32 or FP64), 1 = design Gram on the
+// tensor cores in one TF32 pass, 2 = in three TF32 passes (hi.hi + hi.lo +
+// lo.hi), 3 = one BF16 pass, 4 = three BF16 passes.  The basis Gram (whitening) is always formed on CUDA cores: its
+// condition number (~1e6 for the correlated B0, B1 of the 66 formats) needs
+// round-to-nearest FP32 accumulation.
+template <class Real, int DMAX, int GM>
+struct CtaFit {
+  static constexpr int NM = (DMAX + 1) * (DMAX + 2) * (DMAX + 3) / 6;
+  static constexpr int NAUG = 2 * NM;
+  // row stride of the staged rows: >= NAUG, an odd multiple of 4 (16-byte
+  // rows; 128-bit reads of the same row by many threads spread over banks)
+  static constexpr int LDS = (((NAUG + 3) / 4) % 2 == 1) ? ((NAUG + 3) / 4) * 4 : ((NAUG + 3) / 4 + 1) * 4;
+  static constexpr int WS = ((NM + 3) / 4) * 4;   // row stride of W (16-byte rows)
+  using TS = TcShape<DMAX>;
+  static constexpr int ROWS_BYTES = kT * LDS * (int)sizeof(Real);
+  // staging: hi then lo K-blocks (4 TF32 or 2 BF16 K-blocks per chunk)
+  static constexpr int TC_NKB = (GM == 3 || GM == 4) ? 2 : 4;
+  static constexpr bool TC_X3 = GM == 2 || GM == 4;
+  static constexpr int TC_BYTES = GM == 0 ? 0 : (TC_X3 ? 2 : 1) * TC_NKB * TS::NB_DES;
+  static constexpr int STAGE_BYTES = ROWS_BYTES > TC_BYTES ? ROWS_BYTES : TC_BYTES;
+  // furthest byte the M = 128 A operand reads, from the start of `stage`
+  static constexpr int TC_REACH = GM == 0 ? 0 : ((TC_X3 ? 2 : 1) * TC_NKB - 1) * TS::NB_DES + 16384;
+  alignas(16) Real stage[STAGE_BYTES / sizeof(Real)];   // first member: 1024-byte aligned
+  double uv[2][NM], uvp[2][NM];       // FP64 path: (c, u) and (c, v) of p and q; previous
+  double lo[3], hi[3];
+  double redd[4][32];
+  uint64_t mbar;                      // tensor-core completion barrier
+  alignas(16) Real G[NAUG * NAUG];    // Gram, then factor (stride n)
+  alignas(16) Real W[NM * WS];        // whitening, upper triangular on 1..nm-1 (128-bit loads)
+  Real mupsi[NM];
+  Real gvec[NAUG], scl[NAUG], invd[NAUG], invw[NM];
+  Real xw[NAUG], xwp[NAUG], dxw[NAUG];  // iterate in the design basis (norms), previous, step
+  Real rowb[2][NAUG];                 // pivot rows of the sweep
+  Real duv[2][NM];                    // step of (c, u), (c, v)
+  Real HK[2][NM];
+  Real rbuf[2][kT];
+  Real Tm[3][kMaxDeg + 1][kMaxDeg + 1];  // Q_k(u) = sum_l Tm[l][k] u^l
+  Real mu_v[3], isg_v[3], sc_v[3], of_v[3];
+  float uvhi[2][NM], uvlo[2][NM];     // FP32 path: (c, u), (c, v) as head + tail
+  float uvphi[2][NM], uvplo[2][NM];   // previous
+  float redv[4][((2 * NM + 2 + 15) / 16) * 16];
+  float xs[4][kMC];                   // sample cache (N, B0, B1, y)
+  float redf[4][32];
+  unsigned dslot[3][kMaxDeg + 1];
+  uint32_t tmem_base;
+  long long next_fit[2];              // claimed fit indices (alternating slots)
+  int keep_cnt, keep_w, bad;
+  float fscal[4];
+};
+
+// Dynamic shared memory of one CTA: the state, at least TC_REACH bytes from
+// its start, plus 1 KB to align the start to 1024 bytes.
+template <class Real, int DMAX, int GM>
+__host__ __device__ constexpr size_t ctafit_bytes() {
+  using WF = CtaFit<Real, DMAX, GM>;
+  // the 1 KB alignment slack only where swizzle atoms are staged
+  return ((sizeof(WF) > (size_t)WF::TC_REACH ? sizeof(WF) : (size_t)WF::TC_REACH) + 15 & ~size_t(15)) +
+         (GM > 0 ? 1024 : 0);
+}
+
+// Block-wide sum of one float per thread; result returned to every thread.
+template <class S>
+__device__ __forceinline__ float block_sum_f(S &w, float v, int slot) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) w.redf[wid][slot] = v;
+  __syncthreads();
+  const float r = w.redf[0][slot] + w.redf[1][slot] + w.redf[2][slot] + w.redf[3][slot];
+  return r;
+}
+
+// Unwhitened basis Psi at one sample (compile-time bound NM, runtime nm).
+template <class Real, int DMAX, int NM, class S>
+__device__ __forceinline__ void eval_psi(const S &w, int d, int nm, float x0, float x1, float x2,
+                                         Real (&psi)[NM]) {
+  Real Q[3][kMaxDeg + 1];
+  const float xv[3] = {x0, x1, x2};
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    const Real xn = fma((Real)xv[v], w.sc_v[v], w.of_v[v]);
+    const Real u = (xn - w.mu_v[v]) * w.isg_v[v];
+    Real pw[kMaxDeg + 1];
+    pw[0] = 1;
+#pragma unroll
+    for (int l = 1; l <= DMAX; ++l) pw[l] = pw[l - 1] * u;
+#pragma unroll
+    for (int k = 0; k <= DMAX; ++k) {
+      Real s = 0;
+#pragma unroll
+      for (int l = 0; l <= k; ++l) s = fma(w.Tm[v][l][k], pw[l], s);
+      Q[v][k] = (k <= d) ? s : (Real)0;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NM; ++j)
+    psi[j] = (j < nm) ? Q[0][c_exp[j][0]] * Q[1][c_exp[j][1]] * Q[2][c_exp[j][2]] : (Real)0;
+}
+
+// Whitened basis: pt[0] = 1, pt[j] = sum_{1<=i<=j} (Psi_i - mean_i) W[i][j].
+// W is zero below the diagonal, so each row is read from the aligned 4-block
+// holding the diagonal on (128-bit loads on the FP32 path).
+template <class Real, int NM, int WS, class S>
+__device__ __forceinline__ void whiten(const S &w, const Real (&psi)[NM], Real (&pt)[NM]) {
+  Real acc[WS];
+#pragma unroll
+  for (int j = 0; j < WS; ++j) acc[j] = 0;
+#pragma unroll
+  for (int i = 1; i < NM; ++i) {
+    const Real c = psi[i] - w.mupsi[i];
+    if constexpr (sizeof(Real) == 4) {
+#pragma unroll
+      for (int j4 = (i / 4) * 4; j4 < WS; j4 += 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(&w.W[i * WS + j4]);
+        acc[j4] = fmaf(c, v.x, acc[j4]);
+        acc[j4 + 1] = fmaf(c, v.y, acc[j4 + 1]);
+        acc[j4 + 2] = fmaf(c, v.z, acc[j4 + 2]);
+        acc[j4 + 3] = fmaf(c, v.w, acc[j4 + 3]);
+      }
+    } else {
+#pragma unroll
+      for (int j = i; j < NM; ++j) acc[j] = fma(c, w.W[i * WS + j], acc[j]);
+    }
+  }
+  pt[0] = 1;
+#pragma unroll
+  for (int j = 1; j < NM; ++j) pt[j] = acc[j];
+}
+
+// t-th 4x4 tile of the lower triangle (row-major): rb >= cb
+__device__ __forceinline__ void tile_of(int t, int &rb, int &cb) {
+  int r = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+  while ((r + 1) * (r + 2) / 2 <= t) ++r;
+  while (r * (r + 1) / 2 > t) --r;
+  rb = r;
+  cb = t - r * (r + 1) / 2;
+}
+
+// Gram of `cols` columns of the staged rows: work item = (4x4 tile, sample
+// group); each thread holds up to IPT items.  Chunk partials are summed
+// into the per-item accumulators (blocked summation).
+template <class Real, int IPT, int LDS>
+struct TileGram {
+  Real acc[IPT][16];
+  int ntiles, groups;
+
+  __device__ void init(int cols) {
+    const int side = (cols + 3) / 4;
+    ntiles = side * (side + 1) / 2;
+    groups = max(1, kT / ntiles);
+#pragma unroll
+    for (int k = 0; k < IPT; ++k)
+#pragma unroll
+      for (int i = 0; i < 16; ++i) acc[k][i] = 0;
+  }
+
+  __device__ void chunk(const Real *stage, int cnt) {
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      const int item = threadIdx.x + kT * k;
+      if (item >= ntiles * groups) break;
+      const int tile = item % ntiles, g = item / ntiles;
+      int rb, cb;
+      tile_of(tile, rb, cb);
+      Real part[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) part[i] = 0;
+#pragma unroll 2
+      for (int s = g; s < cnt; s += groups) {
+        Real av[4], bv[4];
+        if constexpr (sizeof(Real) == 4) {
+          const float4 va = *reinterpret_cast<const float4 *>(stage + s * LDS + 4 * rb);
+          const float4 vb = *reinterpret_cast<const float4 *>(stage + s * LDS + 4 * cb);
+          av[0] = va.x; av[1] = va.y; av[2] = va.z; av[3] = va.w;
+          bv[0] = vb.x; bv[1] = vb.y; bv[2] = vb.z; bv[3] = vb.w;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            av[i] = stage[s * LDS + 4 * rb + i];
+            bv[i] = stage[s * LDS + 4 * cb + i];
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) part[4 * i + j] = fma(av[i], bv[j], part[4 * i + j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) acc[k][i] += part[i];
+    }
+  }
+
+  // Sum the sample groups and write the symmetric cols x cols Gram into G
+  // (stride cols).  `scratch` needs ntiles * groups * 16 entries.
+  __device__ void finish(int cols, Real *G, Real *scratch) {
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      const int item = threadIdx.x + kT * k;
+      if (item < ntiles * groups)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) scratch[(size_t)item * 16 + i] = acc[k][i];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ntiles * 16; e += kT) {
+      const int tile = e / 16, q = e % 16;
+      int rb, cb;
+      tile_of(tile, rb, cb);
+      const int r = 4 * rb + q / 4, c = 4 * cb + q % 4;
+      Real sum = 0;
+      for (int g = 0; g < groups; ++g) sum += scratch[((size_t)g * ntiles + tile) * 16 + q];
+      if (r < cols && c < cols) {
+        G[r * cols + c] = sum;
+        G[c * cols + r] = sum;
+      }
+    }
+    __syncthreads();
+  }
+};
+
+// Warp reduce-scatter of V values per lane (V a multiple of 16): four
+// halving exchanges (offsets 16, 8, 4, 2) and one full exchange (offset 1).
+// Afterwards lane l holds, in v[0 .. V/16), the warp totals of the original
+// indices rs_base<V>(l) + q (lanes l and l ^ 1 hold the same totals).
+template <int V>
+__device__ __forceinline__ void warp_reduce_scatter(float (&v)[V]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int step = 0; step < 4; ++step) {
+    const int o = 16 >> step;
+    const int half = V >> (step + 1);
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      const float send = up ? v[j] : v[j + half];
+      const float keep = up ? v[j + half] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < V / 16; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], 1);
+}
+template <int V>
+__device__ __forceinline__ int rs_base(int lane) {
+  return ((lane >> 4) & 1) * (V / 2) + ((lane >> 3) & 1) * (V / 4) + ((lane >> 2) & 1) * (V / 8) +
+         ((lane >> 1) & 1) * (V / 16);
+}
+
+// x += dx in head + tail form (FP32 pairs carrying ~46 bits)
+__device__ __forceinline__ void df_add(float &h, float &l, float d) {
+  float s, e;
+  two_sum(h, d, s, e);
+  const float t = l + e;
+  h = s + t;
+  l = t - (h - s);
+}
+
+// Apply the design-basis step dxw (n entries: numerator 0..nm-1, denominator
+// 1..nm-1 at nm..2nm-2) to the fitted function: with u = W x_num and
+// v = W x_den on the non-constant basis functions, du = W dx_num,
+// dv = W dx_den, dc_p = dx_num_0 - mu.du, dc_q = -mu.dv.  The iterate
+// (c_p, u), (c_q, v) is kept in FP64 (FP64 path) or as FP32 head + tail
+// pairs (FP32 paths); dxw itself is FP32 there.  Returns ||dx|| / ||x||
+// for the updated x (block-wide; contains barriers).
+template <class Real, int NM, int WS, class S>
+__device__ float apply_step(S &w, int nm, int n) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int e = tid; e < 2 * NM; e += kT) {
+    const int which = e / NM, i = e % NM;
+    Real acc = 0;
+    if (i >= 1 && i < nm)
+      for (int j = i; j < nm; ++j)
+        acc = fma(w.W[i * WS + j], which == 0 ? w.dxw[j] : w.dxw[nm + j - 1], acc);
+    w.duv[which][i] = acc;
+  }
+  __syncthreads();
+  if (wid < 2) {
+    Real c = 0;
+    for (int i = 1 + lane; i < nm; i += 32) c = fma(-w.mupsi[i], w.duv[wid][i], c);
+    c = warp_sum(c);
+    if (lane == 0) w.duv[wid][0] = c + (wid == 0 ? w.dxw[0] : (Real)0);
+  } else if (wid == 2) {
+    // norms of the step and of the updated iterate
+    float dn = 0.0f, xn = 0.0f;
+    for (int j = lane; j < n; j += 32) {
+      const Real xv = w.xw[j] + w.dxw[j];
+      w.xw[j] = xv;
+      dn += (float)(w.dxw[j] * w.dxw[j]);
+      xn += (float)(xv * xv);
+    }
+    dn = warp_sum(dn);
+    xn = warp_sum(xn);
+    if (lane == 0) w.fscal[0] = xn > 0.0f ? sqrtf(dn / xn) : 0.0f;
+  }
+  __syncthreads();
+  for (int e = tid; e < 2 * NM; e += kT) {
+    const int which = e / NM, i = e % NM;
+    if (sizeof(Real) == 8) {
+      w.uv[which][i] += (double)w.duv[which][i];
+    } else {
+      df_add(w.uvhi[which][i], w.uvlo[which][i], (float)w.duv[which][i]);
+    }
+  }
+  __syncthreads();
+  return w.fscal[0];
+}
+
+// Tensor-core Gram X^T X of up to NPAD columns over 128-sample chunks: each
+// thread stages its sample's row (column j at row j of the K-major tile,
+// K slot = the thread), one thread issues the MMAs of the chunk's K-blocks
+// and commits them to an mbarrier.  X3: the staged values are split into a
+// TF32 head and tail and D accumulates hi.hi + hi.lo + lo.hi.
+constexpr uint32_t kTcWaitLimit = 1u << 22;   // mbarrier polls before giving up
+
+template <int NPAD, bool X3, bool BF16 = false>
+struct TcGram {
+  static constexpr int NB = NPAD / 8 * 1024;   // bytes per K-block (128-byte rows)
+  static constexpr int KB = BF16 ? 64 : 32;    // samples per K-block
+  static constexpr int NKB = kT / KB;          // K-blocks per 128-sample chunk
+  uint32_t base;                               // this thread's K slot
+  uint32_t xo[8];                              // swizzled chunk offset per row % 8
+
+  __device__ __forceinline__ void init() {
+    const int t = threadIdx.x;
+    const int k = t % KB;                      // sample slot within the K-block
+    constexpr int es = BF16 ? 2 : 4;
+    base = (uint32_t)((t / KB) * NB + (k * es) % 16);
+    const int c = (k * es) / 16;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) xo[r] = (uint32_t)(((c ^ r) & 7) << 4);
+  }
+  // column j (a compile-time index after unrolling) of this thread's sample
+  __device__ __forceinline__ void put(unsigned char *st, int j, float v) const {
+    const uint32_t o = base + (uint32_t)((j >> 3) * 1024 + (j & 7) * 128) + xo[j & 7];
+    if constexpr (BF16) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      *reinterpret_cast<__nv_bfloat16 *>(st + o) = h;
+      if (X3) *reinterpret_cast<__nv_bfloat16 *>(st + NKB * NB + o) = __float2bfloat16_rn(v - __bfloat162float(h));
+    } else {
+      float h, l;
+      tc::split_tf32(v, h, l);
+      *reinterpret_cast<float *>(st + o) = h;
+      if (X3) *reinterpret_cast<float *>(st + NKB * NB + o) = l;
+    }
+  }
+  // one thread: D = (first ? 0 : D) + X^T X over nkb K-blocks (each 4 MMAs
+  // of K = 32 bytes of the 128-byte rows)
+  __device__ static void issue(const unsigned char *st, uint32_t tmem, int nkb, bool first) {
+    constexpr uint32_t id = tc::idesc(BF16 ? tc::kFmtBF16 : tc::kFmtTF32, 128, NPAD);
+    const uint32_t b = tc::smem_u32(st);
+    for (int kb = 0; kb < nkb; ++kb)
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const uint32_t off = (uint32_t)(kb * NB + 32 * s);
+        const uint64_t ah = tc::sw128_desc(b + off);
+        const uint32_t acc0 = (first && kb == 0 && s == 0) ? 0u : 1u;
+        if constexpr (BF16) tc::mma_f16(tmem, ah, ah, id, acc0);
+        else tc::mma_tf32(tmem, ah, ah, id, acc0);
+        if (X3) {
+          const uint64_t al = tc::sw128_desc(b + NKB * NB + off);
+          if constexpr (BF16) {
+            tc::mma_f16(tmem, ah, al, id, 1u);
+            tc::mma_f16(tmem, al, ah, id, 1u);
+          } else {
+            tc::mma_tf32(tmem, ah, al, id, 1u);
+            tc::mma_tf32(tmem, al, ah, id, 1u);
+          }
+        }
+      }
+  }
+  // Warps holding padded rows < rows copy D into G: padded index j maps to
+  // map(j) (< 0: unused), G[map(r) * ld + map(c)].
+  template <class Real, class Map>
+  __device__ static void read(uint32_t tmem, int rows, Real *G, int ld, Map map) {
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (32 * wid < rows) {
+      const int r = 32 * wid + lane;
+      const int rc = r < rows ? map(r) : -1;
+#pragma unroll
+      for (int c0 = 0; c0 < NPAD; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(32 * wid) << 16) + (uint32_t)c0, v);
+        if (rc >= 0)
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int cc = map(c0 + q);
+            if (cc >= 0) G[rc * ld + cc] = (Real)v[q];
+          }
+      }
+    }
+    tc::fence_before_sync();
+  }
+};
+
+// Staged values visible to the tensor core, MMAs of one chunk issued by
+// thread 0 and committed, completion awaited by every thread (bounded).
+template <class TG>
+__device__ __forceinline__ bool tc_chunk(const unsigned char *st, uint32_t tmem, uint64_t *mbar,
+                                         int nkb, bool first, uint32_t &phase) {
+  tc::fence_proxy_async_smem();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc::fence_after_sync();
+    TG::issue(st, tmem, nkb, first);
+    tc::mma_commit(mbar);
+  }
+  const bool ok = tc::mbar_wait(mbar, phase, kTcWaitLimit);
+  tc::fence_after_sync();
+  const bool all = __syncthreads_and(ok);
+  if (all) phase ^= 1u;
+  return all;
+}
+
+// ---------------------------------------------------------------------
+// The fit kernel.  Real = double: plain FP64 path; Real = float: FP32 path.
+
+template <class Real, int DMAX, int GM>
+__global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 2 ? 3 : 4) : (DMAX <= 3 ? 2 : 1))
+    fit_kernel(FitArgs a) {
+  using WF = CtaFit<Real, DMAX, GM>;
+  using TS = TcShape<DMAX>;
+  constexpr int NM = WF::NM;
+  constexpr int NAUG = WF::NAUG;
+  constexpr int LDS = WF::LDS;
+  constexpr int WS = WF::WS;
+  constexpr int S4 = (NAUG + 3) / 4;
+  constexpr int IPT = ((S4 * (S4 + 1) / 2) + kT - 1) / kT;   // design-Gram items per thread
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // the state starts at the first 1024-byte boundary (swizzle atoms of the
+  // tensor-core paths; 16-byte alignment suffices otherwise)
+  const uint32_t raw_s = tc::smem_u32(smem_raw);
+  WF &w = *reinterpret_cast<WF *>(smem_raw + (GM > 0 ? (((raw_s + 1023u) & ~1023u) - raw_s) : 0u));
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // tensor memory for the Gram accumulators, held for the whole launch
+  uint32_t tmem = 0, tc_phase = 0;
+  bool tc_dead = false;
+  if constexpr (GM > 0) {
+    if (wid == 0) {
+      tc::tmem_alloc(&w.tmem_base, TS::TMEM_COLS);
+      tc::tmem_relinquish();
+    }
+    if (tid == 0) tc::mbar_init(&w.mbar, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    tmem = w.tmem_base;
+  }
+  // fits are claimed from the workspace counter (CTAs that draw large fits
+  // take fewer), else every gridDim.x-th fit
+  int64_t f = blockIdx.x;
+  for (int claim = 0;; ++claim) {
+    if (a.counter) {
+      if (tid == 0) w.next_fit[claim & 1] = (long long)atomicAdd(a.counter, 1ull);
+      __syncthreads();
+      f = w.next_fit[claim & 1];
+    } else if (claim > 0) {
+      f += gridDim.x;
+    }
+    if (f >= a.F) break;
+    // ---------------- phase 0: range, degree, validation, box, distinct values
+    const int64_t b0 = a.off[f], b1 = a.off[f + 1];
+    const int d = a.degs ? (int)a.degs[f] : a.d_uniform;
+    const bool range_ok = b0 >= 0 && b1 >= b0 && b1 <= a.S;
+    const int m = range_ok ? (int)(b1 - b0) : 0;
+    double *cf = a.coef + f * kStride;
+    for (int j = tid; j < kStride; j += kT) {
+      cf[j] = 0.0;
+      if (a.coef32) a.coef32[f * kStride + j] = 0.0f;
+    }
+    if (tid < 6) a.box[f * 6 + tid] = 0.0;
+    if (d < 1 || d > DMAX || m == 0) {
+      if (tid == 0) {
+        a.status[f] = RP_FIT_EMPTY;
+        a.rank[f] = 0;
+      }
+      continue;
+    }
+    const int nm = num_monomials(d);
+    const int nc = nm - 1;
+    const int naug = 2 * nm;
+    const int n = naug - 1;
+    const bool cached = m <= kMC;
+    const float *gx0 = a.x + b0, *gx1 = a.x + a.S + b0, *gx2 = a.x + 2 * a.S + b0, *gy = a.y + b0;
+    if (tid < 3 * (kMaxDeg + 1)) (&w.dslot[0][0])[tid] = kEmpty;
+    if (tid == 0) w.bad = 0;
+    __syncthreads();
+    float lmin[3] = {INFINITY, INFINITY, INFINITY}, lmax[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int bad = 0;
+    for (int i = tid; i < m; i += kT) {
+      const float v0 = gx0[i], v1 = gx1[i], v2 = gx2[i], yy = gy[i];
+      if (cached) {
+        w.xs[0][i] = v0;
+        w.xs[1][i] = v1;
+        w.xs[2][i] = v2;
+        w.xs[3][i] = yy;
+      }
+      distinct_insert(w.dslot[0], v0);
+      distinct_insert(w.dslot[1], v1);
+      distinct_insert(w.dslot[2], v2);
+      if (!(isfinite(v0) && isfinite(v1) && isfinite(v2) && isfinite(yy))) bad |= RP_FIT_NONFINITE;
+      else if (a.weighted && !(yy > 0.0f)) bad |= RP_FIT_NONPOS_Y;
+      lmin[0] = fminf(lmin[0], v0); lmax[0] = fmaxf(lmax[0], v0);
+      lmin[1] = fminf(lmin[1], v1); lmax[1] = fmaxf(lmax[1], v1);
+      lmin[2] = fminf(lmin[2], v2); lmax[2] = fmaxf(lmax[2], v2);
+    }
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        lmin[v] = fminf(lmin[v], __shfl_xor_sync(0xffffffffu, lmin[v], o));
+        lmax[v] = fmaxf(lmax[v], __shfl_xor_sync(0xffffffffu, lmax[v], o));
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    if (lane == 0) {
+      for (int v = 0; v < 3; ++v) {
+        w.redf[wid][v] = lmin[v];
+        w.redf[wid][3 + v] = lmax[v];
+      }
+      if (bad) atomicOr(&w.bad, bad);
+    }
+    __syncthreads();
+    if (w.bad) {
+      if (tid == 0) {
+        a.status[f] = (w.bad & RP_FIT_NONFINITE) ? RP_FIT_NONFINITE : RP_FIT_NONPOS_Y;
+        a.rank[f] = 0;
+      }
+      __syncthreads();
+      continue;
+    }
+    if (tid < 3) {
+      double mn = w.redf[0][tid], mx = w.redf[0][3 + tid];
+      for (int k = 1; k < 4; ++k) {
+        mn = fmin(mn, (double)w.redf[k][tid]);
+        mx = fmax(mx, (double)w.redf[k][3 + tid]);
+      }
+      w.lo[tid] = mn;
+      w.hi[tid] = mx;
+      a.box[f * 6 + 2 * tid] = mn;
+      a.box[f * 6 + 2 * tid + 1] = mx;
+      if (mx > mn) {   // x' = 2 (x - lo) / (hi - lo) - 1 = x * sc + of
+        const double sc = 2.0 / (mx - mn);
+        w.sc_v[tid] = (Real)sc;
+        w.of_v[tid] = (Real)(-1.0 - mn * sc);
+      } else {
+        w.sc_v[tid] = 0;
+        w.of_v[tid] = 0;
+      }
+    }
+    __syncthreads();
+    const float *sx0 = cached ? w.xs[0] : gx0;
+    const float *sx1 = cached ? w.xs[1] : gx1;
+    const float *sx2 = cached ? w.xs[2] : gx2;
+    const float *sy = cached ? w.xs[3] : gy;
+
+    // ---------------- phase 1: standardisation, marginal orthonormal polynomials
+    {
+      Real acc[3] = {0, 0, 0};
+      for (int i = tid; i < m; i += kT) {
+        acc[0] += fma((Real)sx0[i], w.sc_v[0], w.of_v[0]);
+        acc[1] += fma((Real)sx1[i], w.sc_v[1], w.of_v[1]);
+        acc[2] += fma((Real)sx2[i], w.sc_v[2], w.of_v[2]);
+      }
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        const double sv = (double)warp_sum(acc[v]);
+        if (lane == 0) w.redd[wid][v] = sv;
+      }
+      __syncthreads();
+      Real mu[3];
+#pragma unroll
+      for (int v = 0; v < 3; ++v)
+        mu[v] = (Real)((w.redd[0][v] + w.redd[1][v] + w.redd[2][v] + w.redd[3][v]) / (double)m);
+      Real mom[3][2 * DMAX];
+#pragma unroll
+      for (int v = 0; v < 3; ++v)
+#pragma unroll
+        for (int k = 0; k < 2 * DMAX; ++k) mom[v][k] = 0;
+      for (int i = tid; i < m; i += kT) {
+        const float xv[3] = {sx0[i], sx1[i], sx2[i]};
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          const Real c = fma((Real)xv[v], w.sc_v[v], w.of_v[v]) - mu[v];
+          Real pw = c;
+#pragma unroll
+          for (int k = 0; k < 2 * DMAX; ++k) {
+            mom[v][k] += pw;
+            pw *= c;
+          }
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int v = 0; v < 3; ++v)
+#pragma unroll
+        for (int k = 0; k < 2 * DMAX; ++k) {
+          const double sv = (double)warp_sum(mom[v][k]);
+          if (lane == 0) w.redd[wid][v * 2 * DMAX + k] = sv;
+        }
+      __syncthreads();
+      if (tid < 3) {
+        const int v = tid;
+        double M[2 * kMaxDeg + 1];
+        M[0] = 1.0;
+        for (int k = 0; k < 2 * DMAX; ++k)
+          M[k + 1] = (w.redd[0][v * 2 * DMAX + k] + w.redd[1][v * 2 * DMAX + k] +
+                      w.redd[2][v * 2 * DMAX + k] + w.redd[3][v * 2 * DMAX + k]) / (double)m;
+        const double var = M[2];
+        w.mu_v[v] = mu[v];
+        for (int l = 0; l <= kMaxDeg; ++l)
+          for (int k = 0; k <= kMaxDeg; ++k) w.Tm[v][l][k] = (l == 0 && k == 0) ? (Real)1 : (Real)0;
+        if (w.sc_v[v] == (Real)0 || !(var > 0.0)) {
+          w.isg_v[v] = 0;
+        } else {
+          const double isg = 1.0 / sqrt(var);
+          w.isg_v[v] = (Real)isg;
+          float Ms[2 * kMaxDeg + 1];
+          Ms[0] = 1.0f;
+          double pw = isg;
+          for (int k = 1; k <= 2 * DMAX; ++k) {
+            Ms[k] = (float)(M[k] * pw);
+            pw *= isg;
+          }
+          int cnt = 0;
+          for (int k = 0; k <= kMaxDeg; ++k) cnt += w.dslot[v][k] != kEmpty;
+          float T[kMaxDeg + 1][kMaxDeg + 1];
+          marginal_transform(Ms, d, min(d, cnt - 1), T);
+          for (int l = 0; l <= kMaxDeg; ++l)
+            for (int k = 0; k <= kMaxDeg; ++k) w.Tm[v][l][k] = (Real)T[l][k];
+        }
+      }
+      __syncthreads();
+    }
+
+    // ---------------- phase 2: Gram of Psi (nm columns), means, whitening
+    {
+      TileGram<Real, IPT, LDS> tg;
+      tg.init(nm);
+      const int cols4 = 4 * ((nm + 3) / 4);
+      for (int base = 0; base < m; base += kT) {
+        const int cnt = min(kT, m - base);
+        if (tid < cnt) {
+          const int i = base + tid;
+          Real psi[NM];
+          eval_psi<Real, DMAX, NM>(w, d, nm, sx0[i], sx1[i], sx2[i], psi);
+          Real *row = w.stage + tid * LDS;
+#pragma unroll
+          for (int j = 0; j < NM; ++j) row[j] = psi[j];
+          for (int j = NM; j < cols4; ++j) row[j] = 0;
+        }
+        __syncthreads();
+        tg.chunk(w.stage, cnt);
+        __syncthreads();
+      }
+      tg.finish(nm, w.G, w.stage);
+
+      // means (row 0 holds the sums of Psi_j), the centred Gram / m of the
+      // non-constant functions, equilibrated, in `stage`
+      for (int j = tid; j < NM; j += kT) w.mupsi[j] = (j < nm) ? w.G[j] / (Real)m : (Real)0;
+      for (int e = tid; e < NM * WS; e += kT) w.W[e] = 0;
+      __syncthreads();
+      for (int e = tid; e < nc * nc; e += kT) {
+        const int i = e / nc + 1, j = e % nc + 1;
+        w.stage[e] = (w.G[i * nm + j] - (Real)m * w.mupsi[i] * w.mupsi[j]) / (Real)m;
+      }
+      __syncthreads();
+      for (int j = tid; j < nc; j += kT) {
+        const Real dg = w.stage[j * nc + j];
+        w.scl[j] = dg > 0 ? rsqrt_pos<Real>(dg) : (Real)0;
+      }
+      __syncthreads();
+      for (int e = tid; e < nc * nc; e += kT) w.stage[e] *= w.scl[e / nc] * w.scl[e % nc];
+      __syncthreads();
+      // the whitening only preconditions: any positive pivot is kept (the
+      // basis stays a basis of the same space); only directions whose pivot
+      // is at rounding level or below are dropped
+      cta_chol<Real, kT>(w.stage, nc, nc, sizeof(Real) == 8 ? (Real)1e-14 : (Real)1e-10, w.invw,
+                         &w.keep_w);
+      // R^{-1} (R = L^T, R[i][l] = L[l][i]) column by column into G; W = D R^{-1}
+      for (int j = tid; j < nc; j += kT)
+        for (int i = j; i >= 0; --i) {
+          Real s = (i == j) ? (Real)1 : (Real)0;
+          for (int l = i + 1; l <= j; ++l) s -= w.stage[l * nc + i] * w.G[l * nc + j];
+          w.G[i * nc + j] = s * w.invw[i];
+        }
+      __syncthreads();
+      for (int e = tid; e < nc * nc; e += kT) {
+        const int i = e / nc, j = e % nc;
+        if (i <= j) w.W[(i + 1) * WS + (j + 1)] = w.G[i * nc + j] * w.scl[i];
+      }
+      __syncthreads();
+    }
+
+    // Phases 3-5, attempted first with the tensor-core design Gram (GM > 0)
+    // and, for a fit whose refinement stops short of its tolerance or whose
+    // factorisation drops pivots there, again with the FP32 Gram on CUDA
+    // cores (the low-precision Gram was too coarse to precondition it).
+    int flags = 0;
+    bool escalated = false;
+    for (int attempt = 0;; ++attempt) {
+    const bool use_tc = GM > 0 && attempt == 0;
+    // ---------------- phase 3: the design Gram [num (nm) | den (nm-1) | rhs]
+    if (use_tc) {
+      if constexpr (GM > 0) {
+      // staged in the padded layout num [0, NM), den [NM, 2 NM - 1), rhs
+      // 2 NM - 1 (compile-time columns); read back compacted to stride naug
+      using TG = TcGram<TS::NDES, WF::TC_X3, (GM == 3 || GM == 4)>;
+      TG tg;
+      tg.init();
+      unsigned char *st = reinterpret_cast<unsigned char *>(w.stage);
+      for (int base = 0; base < m && !tc_dead; base += kT) {
+        const int cnt = min(kT, m - base);
+        const int nkb = (cnt + TG::KB - 1) / TG::KB;
+        if (tid < nkb * TG::KB) {
+          Real pt[NM];
+          Real wt = 0, yy = 0;
+          if (tid < cnt) {
+            const int i = base + tid;
+            Real psi[NM];
+            eval_psi<Real, DMAX, NM>(w, d, nm, sx0[i], sx1[i], sx2[i], psi);
+            whiten<Real, NM, WS>(w, psi, pt);
+            yy = (Real)sy[i];
+            wt = a.weighted ? (Real)1 / fabs(yy) : (Real)1;
+          } else {
+#pragma unroll
+            for (int j = 0; j < NM; ++j) pt[j] = 0;
+          }
+#pragma unroll
+          for (int j = 0; j < NM; ++j) tg.put(st, j, j < nm ? (float)(wt * pt[j]) : 0.0f);
+#pragma unroll
+          for (int j = 1; j < NM; ++j) tg.put(st, NM + j - 1, j < nm ? (float)(-wt * yy * pt[j]) : 0.0f);
+          tg.put(st, 2 * NM - 1, (float)(wt * yy));
+#pragma unroll
+          for (int j = 2 * NM; j < TS::NDES; ++j) tg.put(st, j, 0.0f);
+        }
+        tc_dead = !tc_chunk<TG>(st, tmem, &w.mbar, nkb, base == 0, tc_phase);
+      }
+      if (tc_dead) break;
+      TG::read(tmem, 2 * NM, w.G, naug, [nm](int j) {
+        return j < nm ? j : (j < NM ? -1 : (j < NM + nm - 1 ? nm + (j - NM) : (j == 2 * NM - 1 ? 2 * nm - 1 : -1)));
+      });
+      __syncthreads();
+      }
+    } else {
+      TileGram<Real, IPT, LDS> tg;
+      tg.init(naug);
+      const int cols4 = 4 * ((naug + 3) / 4);
+      for (int base = 0; base < m; base += kT) {
+        const int cnt = min(kT, m - base);
+        if (tid < cnt) {
+          const int i = base + tid;
+          Real psi[NM], pt[NM];
+          eval_psi<Real, DMAX, NM>(w, d, nm, sx0[i], sx1[i], sx2[i], psi);
+          whiten<Real, NM, WS>(w, psi, pt);
+          const Real yy = (Real)sy[i];
+          const Real wt = a.weighted ? (Real)1 / fabs(yy) : (Real)1;
+          Real *row = w.stage + tid * LDS;
+#pragma unroll
+          for (int j = 0; j < NM; ++j)
+            if (j < nm) row[j] = wt * pt[j];
+#pragma unroll
+          for (int j = 1; j < NM; ++j)
+            if (j < nm) row[nm + j - 1] = -wt * yy * pt[j];
+          row[n] = wt * yy;
+          for (int j = naug; j < cols4; ++j) row[j] = 0;
+        }
+        __syncthreads();
+        tg.chunk(w.stage, cnt);
+        __syncthreads();
+      }
+      tg.finish(naug, w.G, w.stage);
+    }
+
+    // ---------------- phase 4: equilibrate and sweep
+    // S = D G D (D = diag(G_jj^-1/2) on the n normal columns, 1 on the
+    // right-hand side), in place in G (stride naug).  Sweeping the pivots
+    // 0..n-1 (the sweep operator of least-squares regression: Gauss-Jordan
+    // on the SPD normal matrix) leaves -S^-1 in the n x n block and the
+    // least-squares solution in column n.  A pivot <= drop_tol (relative to
+    // the unit equilibrated diagonal) is not swept: its column is dropped
+    // (rank deficiency).  Afterwards G holds Q = D S^-1 D on the kept columns
+    // (0 elsewhere), the refinement's preconditioner, and dxw the first step.
+    {
+      const int N1 = naug;
+      for (int j = tid; j < N1; j += kT) {
+        const Real dg = w.G[j * N1 + j];
+        w.scl[j] = (j == n) ? (Real)1 : (dg > 0 ? rsqrt_pos<Real>(dg) : (Real)0);
+      }
+      __syncthreads();
+      // the upper triangle (i <= j), EPT entries per thread, decoded once
+      constexpr int EPT = (NAUG * (NAUG + 1) / 2 + kT - 1) / kT;
+      const int ntri = N1 * (N1 + 1) / 2;
+      int ent[EPT];   // i << 16 | j, or -1
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        const int e = tid + kT * q;
+        if (e < ntri) {
+          // e = i N1 - i (i - 1) / 2 + (j - i): row i holds N1 - i entries
+          int i = (int)((2.0f * N1 + 1.0f - sqrtf((2.0f * N1 + 1.0f) * (2.0f * N1 + 1.0f) - 8.0f * e)) * 0.5f);
+          while (i > 0 && i * N1 - i * (i - 1) / 2 > e) --i;
+          while ((i + 1) * N1 - (i + 1) * i / 2 <= e) ++i;
+          const int j = i + (e - (i * N1 - i * (i - 1) / 2));
+          ent[q] = (i << 16) | j;
+        } else {
+          ent[q] = -1;
+        }
+      }
+      // the entries stay in registers through the elimination; shared memory
+      // holds only the pivot rows
+      Real v[EPT];
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        v[q] = 0;
+        if (ent[q] >= 0) {
+          const int i = ent[q] >> 16, j = ent[q] & 0xFFFF;
+          v[q] = w.G[i * N1 + j] * w.scl[i] * w.scl[j];
+          if (i == 0) w.rowb[0][j] = v[q];
+        }
+      }
+      __syncthreads();
+      int kept = 0;
+      for (int k = 0; k < n; ++k) {
+        const Real *rk = w.rowb[k & 1];
+        Real *rn = w.rowb[(k + 1) & 1];
+        const Real piv = rk[k];
+        const bool keep = piv > (Real)a.drop_tol;
+        kept += keep;
+        const Real ip = keep ? (Real)1 / piv : (Real)0;
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+          if (ent[q] < 0) continue;
+          const int i = ent[q] >> 16, j = ent[q] & 0xFFFF;
+          if (keep) {
+            // S'_ij = S_ij - S_ik S_kj / p; S'_ik = S_ik / p; S'_kk = -1 / p
+            const Real ri = rk[i], rj = rk[j];
+            const Real gen = fma(-ri * ip, rj, v[q]);
+            v[q] = (j == k) ? ((i == k) ? -ip : ri * ip) : ((i == k) ? rj * ip : gen);
+          }
+          if (i == k + 1) rn[j] = v[q];
+          if (j == k + 1) rn[i] = v[q];
+        }
+        if (tid == 0) w.invd[k] = keep ? (Real)1 : (Real)0;
+        __syncthreads();
+      }
+      // Q = -D S D on the kept columns, both triangles; the first step
+#pragma unroll
+      for (int q = 0; q < EPT; ++q)
+        if (ent[q] >= 0) {
+          const int i = ent[q] >> 16, j = ent[q] & 0xFFFF;
+          const Real si = w.invd[i] * w.scl[i];
+          if (j < n) {
+            const Real qv = -v[q] * si * w.invd[j] * w.scl[j];
+            w.G[i * N1 + j] = qv;
+            w.G[j * N1 + i] = qv;
+          } else if (j == n && i < n) {
+            w.dxw[i] = v[q] * si;
+          }
+        }
+      if (tid == 0) w.keep_cnt = kept;
+      // the iterate starts at 0: (c_p, u) = 0, (c_q, v) = (1, 0)
+      for (int e = tid; e < 2 * NM; e += kT) {
+        const int which = e / NM, i = e % NM;
+        const float c = (which == 1 && i == 0) ? 1.0f : 0.0f;
+        w.uvhi[which][i] = c;
+        w.uvlo[which][i] = 0.0f;
+        w.uv[which][i] = c;
+      }
+      for (int j = tid; j < NAUG; j += kT) w.xw[j] = 0;
+      __syncthreads();
+      (void)apply_step<Real, NM, WS>(w, nm, n);
+    }
+
+    // ---------------- phase 5: refinement from the samples.
+    // The iterate is the function pair p = c_p + psi.u, q = c_q + psi.v in
+    // the unwhitened basis; each pass computes at every sample the design
+    // residual r = w (y q - p) (plain FP32, then Ogita-Rump-Oishi Dot2
+    // against the head + tail iterate once the steps fall below 1e-4
+    // relative; FP64 on the FP64 path), the objective sum r^2, whether
+    // q > 0, and H_i = sum (w r) psi_i, K_i = sum (w y r) psi_i.  The
+    // normal-equation residual in the design basis is
+    //   g_num_0 = H_0, g_num_j = sum_{i<=j} W_ij (H_i - mu_i H_0),
+    //   g_den_j = -sum_{i<=j} W_ij (K_i - mu_i K_0),
+    // and the step dx = Q g.  A step that raises the objective beyond its
+    // rounding level is undone and the refinement stops.
+    flags = (w.keep_cnt < n) ? RP_FIT_RANK_DEFICIENT : 0;
+    float prev_rel = INFINITY, obj_prev = INFINITY, obj_drop = INFINITY;
+    bool compensated = sizeof(Real) == 8, done = false;
+    int pole_prev = 0, it = 0;
+    float omega = 1.0f;   // step length (halved after an objective increase)
+    constexpr bool kRegAcc = sizeof(Real) == 4 && DMAX <= 3;
+    constexpr int VP = ((2 * NM + 2 + 15) / 16) * 16;   // register accumulators
+    const int hk_groups = max(1, kT / nm);
+    for (;; ++it) {
+      const bool update = it < a.max_refine && !done;
+      Real hk0 = 0, hk1 = 0;    // staged path: this thread's column partials
+      float obj = 0.0f;
+      int pole = 0;
+      float acc[kRegAcc ? VP : 1];
+#pragma unroll
+      for (int j = 0; j < (kRegAcc ? VP : 1); ++j) acc[j] = 0.0f;
+      for (int base = 0; base < m; base += kT) {
+        const int cnt = min(kT, m - base);
+        if (tid < cnt) {
+          const int i = base + tid;
+          Real psi[NM];
+          eval_psi<Real, DMAX, NM>(w, d, nm, sx0[i], sx1[i], sx2[i], psi);
+          psi[0] = 1;
+          const Real yy = (Real)sy[i];
+          const Real wt = a.weighted ? (Real)1 / fabs(yy) : (Real)1;
+          Real r;
+          if constexpr (sizeof(Real) == 8) {
+            double p = w.uv[0][0], q = w.uv[1][0];
+#pragma unroll
+            for (int j2 = 1; j2 < NM; ++j2) {
+              p = fma(psi[j2], w.uv[0][j2], p);
+              q = fma(psi[j2], w.uv[1][j2], q);
+            }
+            pole |= !(q > 0.0);
+            r = wt * (yy * q - p);
+          } else {
+            float qf = w.uvhi[1][0];
+#pragma unroll
+            for (int j2 = 1; j2 < NM; ++j2) qf = fmaf(psi[j2], w.uvhi[1][j2], qf);
+            pole |= !(qf > 0.0f);
+            if (compensated) {
+              // e = y q - p = sum_j (y psi_j) v_j - psi_j u_j (psi_0 = 1):
+              // Dot2 against the head + tail iterate, two independent chains
+              float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
+#pragma unroll
+              for (int j2 = 0; j2 < NM; ++j2) {
+                const float av = yy * psi[j2], bv = -psi[j2];
+                const float pr0 = av * w.uvhi[1][j2], pr1 = bv * w.uvhi[0][j2];
+                const float pe0 = fmaf(av, w.uvhi[1][j2], -pr0);
+                const float pe1 = fmaf(bv, w.uvhi[0][j2], -pr1);
+                float t0, e0, t1, e1;
+                two_sum(s0, pr0, t0, e0);
+                two_sum(s1, pr1, t1, e1);
+                s0 = t0;
+                s1 = t1;
+                c0 += e0 + pe0 + av * w.uvlo[1][j2];
+                c1 += e1 + pe1 + bv * w.uvlo[0][j2];
+              }
+              float t, e;
+              two_sum(s0, s1, t, e);
+              r = wt * (t + (e + c0 + c1));
+            } else {
+              float p = w.uvhi[0][0];
+#pragma unroll
+              for (int j2 = 1; j2 < NM; ++j2) p = fmaf(psi[j2], w.uvhi[0][j2], p);
+              r = wt * fmaf(yy, qf, -p);
+            }
+          }
+          obj += (float)(r * r);
+          if constexpr (kRegAcc) {
+            if (update) {
+              const float rn = (float)(wt * r), rd = (float)(wt * yy * r);
+#pragma unroll
+              for (int j2 = 0; j2 < NM; ++j2) {
+                acc[j2] = fmaf(rn, (float)psi[j2], acc[j2]);
+                acc[NM + j2] = fmaf(rd, (float)psi[j2], acc[NM + j2]);
+              }
+            }
+          } else if (update) {
+            Real *row = w.stage + tid * LDS;
+#pragma unroll
+            for (int j2 = 0; j2 < NM; ++j2) row[j2] = psi[j2];
+            w.rbuf[0][tid] = wt * r;
+            w.rbuf[1][tid] = wt * yy * r;
+          }
+        }
+        if constexpr (!kRegAcc) {
+          if (update) {
+            __syncthreads();
+            if (tid < nm * hk_groups) {
+              const int j2 = tid % nm, g = tid / nm;
+              Real pn = 0, pd = 0;
+              for (int s2 = g; s2 < cnt; s2 += hk_groups) {
+                const Real bv = w.stage[s2 * LDS + j2];
+                pn = fma(bv, w.rbuf[0][s2], pn);
+                pd = fma(bv, w.rbuf[1][s2], pd);
+              }
+              hk0 += pn;
+              hk1 += pd;
+            }
+            __syncthreads();
+          }
+        }
+      }
+      // block totals: objective, pole, and (when stepping) H and K
+      if constexpr (kRegAcc) {
+        acc[2 * NM] = obj;
+        acc[2 * NM + 1] = pole ? 1.0f : 0.0f;
+        warp_reduce_scatter<VP>(acc);
+        if ((lane & 1) == 0) {
+          const int b = rs_base<VP>(lane);
+#pragma unroll
+          for (int q = 0; q < VP / 16; ++q) w.redv[wid][b + q] = acc[q];
+        }
+        __syncthreads();
+        obj = w.redv[0][2 * NM] + w.redv[1][2 * NM] + w.redv[2][2 * NM] + w.redv[3][2 * NM];
+        pole = (w.redv[0][2 * NM + 1] + w.redv[1][2 * NM + 1] + w.redv[2][2 * NM + 1] +
+                w.redv[3][2 * NM + 1]) > 0.0f;
+      } else {
+        pole = __syncthreads_or(pole);
+        obj = block_sum_f(w, obj, 8);
+      }
+      __syncthreads();
+      const bool worse = it > 0 && obj > obj_prev * (compensated ? 1.00001f : 1.0001f);
+      if (worse) {
+        // the last step increased the objective: undo it, then retry it at
+        // half length (a preconditioner that overestimates curvature in some
+        // direction makes the full step overshoot); the halving persists
+        // for the fit's later steps; below 1/16 the refinement stops
+        for (int e = tid; e < 2 * NM; e += kT) {
+          const int which = e / NM, i2 = e % NM;
+          w.uv[which][i2] = w.uvp[which][i2];
+          w.uvhi[which][i2] = w.uvphi[which][i2];
+          w.uvlo[which][i2] = w.uvplo[which][i2];
+        }
+        for (int j2 = tid; j2 < n; j2 += kT) w.xw[j2] = w.xwp[j2];
+        omega *= 0.5f;
+        if (omega < 0.0625f || it >= a.max_refine) {
+          pole = pole_prev;
+          obj_drop = 0.0f;
+          __syncthreads();
+          break;
+        }
+        for (int j2 = tid; j2 < n; j2 += kT) w.dxw[j2] *= (Real)0.5;
+        __syncthreads();
+        (void)apply_step<Real, NM, WS>(w, nm, n);
+        continue;
+      }
+      if (it > 0) obj_drop = (obj_prev - obj) / fmaxf(obj_prev, 1e-30f);
+      for (int e = tid; e < 2 * NM; e += kT) {
+        const int which = e / NM, i2 = e % NM;
+        w.uvp[which][i2] = w.uv[which][i2];
+        w.uvphi[which][i2] = w.uvhi[which][i2];
+        w.uvplo[which][i2] = w.uvlo[which][i2];
+      }
+      for (int j2 = tid; j2 < n; j2 += kT) w.xwp[j2] = w.xw[j2];
+      obj_prev = obj;
+      pole_prev = pole;
+      if (!update) {
+        __syncthreads();
+        break;
+      }
+      // H, K
+      if constexpr (kRegAcc) {
+        if (tid < 2 * NM) {
+          const Real v = w.redv[0][tid] + w.redv[1][tid] + w.redv[2][tid] + w.redv[3][tid];
+          w.HK[tid / NM][tid % NM] = v;
+        }
+      } else {
+        if (tid < nm * hk_groups) {
+          w.stage[tid] = hk0;
+          w.stage[kT + tid] = hk1;
+        }
+        __syncthreads();
+        if (tid < nm) {
+          Real h = 0, k2 = 0;
+          for (int g = 0; g < hk_groups; ++g) {
+            h += w.stage[g * nm + tid];
+            k2 += w.stage[kT + g * nm + tid];
+          }
+          w.HK[0][tid] = h;
+          w.HK[1][tid] = k2;
+        }
+      }
+      __syncthreads();
+      // g, then the step dx = Q g
+      for (int e = tid; e < n; e += kT) {
+        Real g;
+        if (e < nm) {
+          if (e == 0) {
+            g = w.HK[0][0];
+          } else {
+            g = 0;
+            for (int i2 = 1; i2 <= e; ++i2) g = fma(w.W[i2 * WS + e], w.HK[0][i2] - w.mupsi[i2] * w.HK[0][0], g);
+          }
+        } else {
+          const int jd = e - nm + 1;
+          g = 0;
+          for (int i2 = 1; i2 <= jd; ++i2) g = fma(-w.W[i2 * WS + jd], w.HK[1][i2] - w.mupsi[i2] * w.HK[1][0], g);
+        }
+        w.gvec[e] = g;
+      }
+      __syncthreads();
+      for (int e = tid; e < n; e += kT) {
+        // Q is symmetric: read column e (consecutive threads, consecutive words)
+        Real z = 0;
+        for (int k2 = 0; k2 < n; ++k2) z = fma(w.G[k2 * naug + e], w.gvec[k2], z);
+        w.dxw[e] = z * (Real)omega;
+      }
+      __syncthreads();
+      const float rel = apply_step<Real, NM, WS>(w, nm, n);
+      const bool was_compensated = compensated;
+      if (!compensated && rel < 1e-4f) compensated = true;
+      // stop at tol, or once compensated corrections stop shrinking (the
+      // residuals' noise floor)
+      if (rel <= (float)a.tol || (was_compensated && rel > 0.9f * prev_rel)) done = true;
+      prev_rel = rel;
+      if (done) {
+        // converged: the last correction is below tol (or at the residuals'
+        // noise floor); it is kept without another evaluation pass
+        ++it;
+        break;
+      }
+    }
+    flags |= (pole_prev ? RP_FIT_POLE : 0);
+    // not converged: the iteration cap was hit while the objective was still
+    // falling by more than 1e-5 per step
+    if (a.max_refine > 0 && !done && !(obj_drop <= 1e-5f)) flags |= RP_FIT_NOT_CONVERGED;
+    flags |= min(it, 255) << RP_FIT_ITER_SHIFT;
+    if (use_tc && a.max_refine > 0 && (!done || (flags & RP_FIT_RANK_DEFICIENT))) {
+      escalated = true;
+      continue;
+    }
+    break;
+    }   // attempts
+    if (tc_dead) {
+      if (tid == 0) {
+        a.status[f] = RP_FIT_TIMEOUT;
+        a.rank[f] = 0;
+      }
+      continue;
+    }
+    if (escalated) flags |= RP_FIT_ESCALATED;
+
+    // ---------------- phase 6: back to the monomial basis (FP64)
+    {
+      double *cpsi = reinterpret_cast<double *>(w.stage);   // [2][kMaxNm]
+      double *P = cpsi + 2 * kMaxNm;                          // [3][5][5]
+      // the iterate's coefficients on Psi (index 0: the constants c_p, c_q)
+      for (int e = tid; e < 2 * nm; e += kT) {
+        const int which = e / nm, i = e % nm;   // 0 numerator, 1 denominator
+        cpsi[which * kMaxNm + i] = sizeof(Real) == 8
+                                       ? w.uv[which][i]
+                                       : (double)w.uvhi[which][i] + (double)w.uvlo[which][i];
+      }
+      if (tid >= kT - 3 * (kMaxDeg + 1) * (kMaxDeg + 1) + 0 && tid < kT) {
+        // P[v][k][i]: coefficient of x'^i in Q_k(u), u = (x' - mu) isg, one
+        // entry per thread: sum_{l=i..k} Tm[l][k] C(l, i) isg^l (-mu)^(l-i)
+        const int e = tid - (kT - 3 * (kMaxDeg + 1) * (kMaxDeg + 1));
+        const int v = e / ((kMaxDeg + 1) * (kMaxDeg + 1));
+        const int k = (e / (kMaxDeg + 1)) % (kMaxDeg + 1), i = e % (kMaxDeg + 1);
+        const double mu = w.mu_v[v], isg = w.isg_v[v];
+        double acc = 0.0;
+        if (k <= d && i <= k) {
+          double pw = 1.0;   // isg^l (-mu)^(l - i), starting at l = i
+          for (int l = 0; l < i; ++l) pw *= isg;
+          const double step = -mu * isg;
+          int binom = 1;     // C(l, i), starting at C(i, i)
+          for (int l = i; l <= k; ++l) {
+            acc = fma((double)w.Tm[v][l][k] * (double)binom, pw, acc);
+            pw *= step;
+            binom = binom * (l + 1) / (l + 1 - i);
+          }
+        }
+        P[(v * (kMaxDeg + 1) + k) * (kMaxDeg + 1) + i] = acc;
+      }
+      __syncthreads();
+      // the basis change is a tensor product: three 1-D passes, one per
+      // variable (N last), each summing <= d + 1 terms per coefficient
+      double *buf[2] = {cpsi, P + 3 * (kMaxDeg + 1) * (kMaxDeg + 1)};
+      int cur = 0;
+#pragma unroll
+      for (int v = 2; v >= 0; --v) {
+        for (int e = tid; e < 2 * nm; e += kT) {
+          const int which = e / nm, t = e % nm;
+          int ex[3] = {c_exp[t][0], c_exp[t][1], c_exp[t][2]};
+          const int ov = ex[v];
+          const int room = d - (ex[0] + ex[1] + ex[2] - ov);
+          double acc = 0.0;
+          for (int k = ov; k <= room; ++k) {
+            ex[v] = k;
+            acc = fma(buf[cur][which * kMaxNm + c_idx[ex[0]][ex[1]][ex[2]]],
+                      P[(v * (kMaxDeg + 1) + k) * (kMaxDeg + 1) + ov], acc);
+          }
+          buf[cur ^ 1][which * kMaxNm + t] = acc;
+        }
+        cur ^= 1;
+        __syncthreads();
+      }
+      for (int e = tid; e < 2 * nm; e += kT) {
+        const int which = e / nm, t = e % nm;
+        const double s = buf[cur][which * kMaxNm + t];
+        const int o = which == 0 ? t : kHalf + t;
+        cf[o] = s;
+        if (a.coef32) a.coef32[f * kStride + o] = (float)s;
+      }
+      if (tid == 0) {
+        a.status[f] = flags;
+        a.rank[f] = w.keep_cnt;
+      }
+      __syncthreads();
+    }
+  }
+  if constexpr (GM > 0) {
+    // after a wait that gave up, wait (bounded) once more for the MMAs still
+    // in flight before the tensor memory is released
+    if (tc_dead && tid == 0) (void)tc::mbar_wait(&w.mbar, tc_phase, kTcWaitLimit);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (wid == 0) tc::tmem_dealloc(tmem, TS::TMEM_COLS);
+  }
+}
+
+// ---------------------------------------------------------------------
+
+void set_tables() {
+  static bool done = false;
+  if (done) return;
+  int8_t e[kMaxNm][3];
+  int k = 0;
+  for (int s = 0; s <= kMaxDeg; ++s)
+    for (int a = s; a >= 0; --a)
+      for (int b = s - a; b >= 0; --b) {
+        e[k][0] = (int8_t)a;
+        e[k][1] = (int8_t)b;
+        e[k][2] = (int8_t)(s - a - b);
+        ++k;
+      }
+  cudaMemcpyToSymbol(c_exp, e, sizeof(e));
+  int8_t idx[kMaxDeg + 1][kMaxDeg + 1][kMaxDeg + 1];
+  for (int i = 0; i <= kMaxDeg; ++i)
+    for (int j = 0; j <= kMaxDeg; ++j)
+      for (int l = 0; l <= kMaxDeg; ++l) idx[i][j][l] = -1;
+  for (int t = 0; t < kMaxNm; ++t) idx[e[t][0]][e[t][1]][e[t][2]] = (int8_t)t;
+  cudaMemcpyToSymbol(c_idx, idx, sizeof(idx));
+  done = true;
+}
+
+// Resident CTAs per SM of one fit-kernel variant: registers, shared memory,
+// threads and (tensor-core variants) tensor-memory columns.
+template <class Real, int DMAX, int GM>
+int residency() {
+  using WF = CtaFit<Real, DMAX, GM>;
+  const size_t smem = ctafit_bytes<Real, DMAX, GM>();
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, fit_kernel<Real, DMAX, GM>) != cudaSuccess) return 1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int smem_sm = 0, smem_rsv = 0, regs_sm = 0;
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  const int regs_cta = ((fa.numRegs * 32 + 255) / 256 * 256) * (kT / 32);
+  int per_sm = smem_sm / (int)(smem + smem_rsv);
+  per_sm = min(per_sm, regs_sm / max(regs_cta, 1));
+  per_sm = min(per_sm, 2048 / kT);
+  if (GM > 0) per_sm = min(per_sm, 512 / TcShape<DMAX>::TMEM_COLS);
+  (void)sizeof(WF);
+  return per_sm < 1 ? 1 : per_sm;
+}
+
+template <class Real, int DMAX, int GM>
+cudaError_t launch_t(const FitArgs &a, int precision, cudaStream_t s) {
+  using WF = CtaFit<Real, DMAX, GM>;
+  // 128-bit shared-memory loads of the staged rows and of W; 8-byte mbarrier
+  static_assert(offsetof(WF, stage) == 0, "stage must start the state");
+  static_assert(offsetof(WF, W) % 16 == 0 && offsetof(WF, G) % 16 == 0, "W, G: 16-byte aligned");
+  static_assert(offsetof(WF, mbar) % 8 == 0, "mbarrier: 8-byte aligned");
+  set_tables();
+  const size_t smem = ctafit_bytes<Real, DMAX, GM>();
+  cudaError_t e = cudaFuncSetAttribute(fit_kernel<Real, DMAX, GM>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = residency<Real, DMAX, GM>();
+  const int cap = fit_ctas_cap(precision, DMAX);
+  if (cap > 0 && cap < per_sm) per_sm = cap;
+  int64_t grid = (int64_t)num_sms() * per_sm;
+  if (grid > a.F) grid = a.F;
+  if (a.counter) {
+    e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+  }
+  fit_kernel<Real, DMAX, GM><<<(unsigned)grid, kT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// One precision family (Real, GM) for the degree bound dmax of a launch.
+template <class Real, int GM>
+cudaError_t launch_family(const FitArgs &a, int dmax, int precision, cudaStream_t s) {
+  switch (dmax) {
+    case 1: case 2: return launch_t<Real, 2, GM>(a, precision, s);
+    case 3: return launch_t<Real, 3, GM>(a, precision, s);
+    default: return launch_t<Real, 4, GM>(a, precision, s);
+  }
+}
+template <class Real, int GM>
+int residency_family(int dmax) {
+  return dmax <= 2 ? residency<Real, 2, GM>() : dmax == 3 ? residency<Real, 3, GM>() : residency<Real, 4, GM>();
+}
+
+}  // namespace
+}  // namespace rpk

@@ -219,7 +219,7 @@ struct CtaFit {
   alignas(16) Real stage[STAGE_BYTES / sizeof(Real)];   // first member: 1024-byte aligned
   double uv[2][NM], uvp[2][NM];       // FP64 path: (c, u) and (c, v) of p and q; previous
   double lo[3], hi[3];
-  double redd[4][32];
+  Real redr[4][32];                   // per-warp partial sums (phase 1)
   uint64_t mbar;                      // tensor-core completion barrier
   alignas(16) Real G[NAUG * NAUG];    // Gram, then factor (stride n)
   alignas(16) Real W[NM * WS];        // whitening, upper triangular on 1..nm-1 (128-bit loads)
@@ -680,22 +680,28 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
     __syncthreads();
     float lmin[3] = {INFINITY, INFINITY, INFINITY}, lmax[3] = {-INFINITY, -INFINITY, -INFINITY};
     int bad = 0;
+    // loads (unrolled so that several samples' loads are in flight), the
+    // sample cache, validity and range; then the distinct values from the
+    // cached copy (the set's atomics would otherwise serialise the loads)
+#pragma unroll 4
     for (int i = tid; i < m; i += kT) {
-      const float v0 = gx0[i], v1 = gx1[i], v2 = gx2[i], yy = gy[i];
+      const float v0 = __ldg(gx0 + i), v1 = __ldg(gx1 + i), v2 = __ldg(gx2 + i), yy = __ldg(gy + i);
       if (cached) {
         w.xs[0][i] = v0;
         w.xs[1][i] = v1;
         w.xs[2][i] = v2;
         w.xs[3][i] = yy;
       }
-      distinct_insert(w.dslot[0], v0);
-      distinct_insert(w.dslot[1], v1);
-      distinct_insert(w.dslot[2], v2);
       if (!(isfinite(v0) && isfinite(v1) && isfinite(v2) && isfinite(yy))) bad |= RP_FIT_NONFINITE;
       else if (a.weighted && !(yy > 0.0f)) bad |= RP_FIT_NONPOS_Y;
       lmin[0] = fminf(lmin[0], v0); lmax[0] = fmaxf(lmax[0], v0);
       lmin[1] = fminf(lmin[1], v1); lmax[1] = fmaxf(lmax[1], v1);
       lmin[2] = fminf(lmin[2], v2); lmax[2] = fmaxf(lmax[2], v2);
+    }
+    for (int i = tid; i < m; i += kT) {
+      distinct_insert(w.dslot[0], cached ? w.xs[0][i] : gx0[i]);
+      distinct_insert(w.dslot[1], cached ? w.xs[1][i] : gx1[i]);
+      distinct_insert(w.dslot[2], cached ? w.xs[2][i] : gx2[i]);
     }
 #pragma unroll
     for (int v = 0; v < 3; ++v)
@@ -733,9 +739,11 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
       a.box[f * 6 + 2 * tid] = mn;
       a.box[f * 6 + 2 * tid + 1] = mx;
       if (mx > mn) {   // x' = 2 (x - lo) / (hi - lo) - 1 = x * sc + of
-        const double sc = 2.0 / (mx - mn);
-        w.sc_v[tid] = (Real)sc;
-        w.of_v[tid] = (Real)(-1.0 - mn * sc);
+        // in Real: the FP32 paths normalise in FP32, so FP32 sc and of (a
+        // consistent normalisation; lo and hi are kept exactly)
+        const Real sc = (Real)2 / (Real)(mx - mn);
+        w.sc_v[tid] = sc;
+        w.of_v[tid] = fma(-(Real)mn, sc, (Real)-1);
       } else {
         w.sc_v[tid] = 0;
         w.of_v[tid] = 0;
@@ -755,16 +763,20 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
         acc[1] += fma((Real)sx1[i], w.sc_v[1], w.of_v[1]);
         acc[2] += fma((Real)sx2[i], w.sc_v[2], w.of_v[2]);
       }
+      // sums and moments in Real (FP32 on the FP32 paths: they only choose
+      // the per-fit basis, which is used consistently; FP64 divisions at
+      // GB300's FP64 rate would cost more than the whole phase)
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
-        const double sv = (double)warp_sum(acc[v]);
-        if (lane == 0) w.redd[wid][v] = sv;
+        const Real sv = warp_sum(acc[v]);
+        if (lane == 0) w.redr[wid][v] = sv;
       }
       __syncthreads();
+      const Real inv_m = (Real)1 / (Real)m;
       Real mu[3];
 #pragma unroll
       for (int v = 0; v < 3; ++v)
-        mu[v] = (Real)((w.redd[0][v] + w.redd[1][v] + w.redd[2][v] + w.redd[3][v]) / (double)m);
+        mu[v] = (w.redr[0][v] + w.redr[1][v] + w.redr[2][v] + w.redr[3][v]) * inv_m;
       Real mom[3][2 * DMAX];
 #pragma unroll
       for (int v = 0; v < 3; ++v)
@@ -783,34 +795,35 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
           }
         }
       }
-      __syncthreads();
+      // (slots 3.. : the means' slots 0..2 may still be being read)
 #pragma unroll
       for (int v = 0; v < 3; ++v)
 #pragma unroll
         for (int k = 0; k < 2 * DMAX; ++k) {
-          const double sv = (double)warp_sum(mom[v][k]);
-          if (lane == 0) w.redd[wid][v * 2 * DMAX + k] = sv;
+          const Real sv = warp_sum(mom[v][k]);
+          if (lane == 0) w.redr[wid][3 + v * 2 * DMAX + k] = sv;
         }
       __syncthreads();
       if (tid < 3) {
         const int v = tid;
-        double M[2 * kMaxDeg + 1];
-        M[0] = 1.0;
-        for (int k = 0; k < 2 * DMAX; ++k)
-          M[k + 1] = (w.redd[0][v * 2 * DMAX + k] + w.redd[1][v * 2 * DMAX + k] +
-                      w.redd[2][v * 2 * DMAX + k] + w.redd[3][v * 2 * DMAX + k]) / (double)m;
-        const double var = M[2];
+        Real M[2 * kMaxDeg + 1];
+        M[0] = 1;
+        for (int k = 0; k < 2 * DMAX; ++k) {
+          const int o = 3 + v * 2 * DMAX + k;
+          M[k + 1] = (w.redr[0][o] + w.redr[1][o] + w.redr[2][o] + w.redr[3][o]) * inv_m;
+        }
+        const Real var = M[2];
         w.mu_v[v] = mu[v];
         for (int l = 0; l <= kMaxDeg; ++l)
           for (int k = 0; k <= kMaxDeg; ++k) w.Tm[v][l][k] = (l == 0 && k == 0) ? (Real)1 : (Real)0;
-        if (w.sc_v[v] == (Real)0 || !(var > 0.0)) {
+        if (w.sc_v[v] == (Real)0 || !(var > (Real)0)) {
           w.isg_v[v] = 0;
         } else {
-          const double isg = 1.0 / sqrt(var);
-          w.isg_v[v] = (Real)isg;
+          const Real isg = rsqrt_pos<Real>(var);
+          w.isg_v[v] = isg;
           float Ms[2 * kMaxDeg + 1];
           Ms[0] = 1.0f;
-          double pw = isg;
+          Real pw = isg;
           for (int k = 1; k <= 2 * DMAX; ++k) {
             Ms[k] = (float)(M[k] * pw);
             pw *= isg;
@@ -853,6 +866,11 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
       for (int j = tid; j < NM; j += kT) w.mupsi[j] = (j < nm) ? w.G[j] / (Real)m : (Real)0;
       for (int e = tid; e < NM * WS; e += kT) w.W[e] = 0;
       __syncthreads();
+      // the centred Gram / m of the non-constant functions, equilibrated, in
+      // `stage`; its Cholesky factor (block-wide); R^-1 (R = L^T) column by
+      // column into G; W = D R^-1.  The whitening only preconditions: any
+      // positive pivot is kept (the basis stays a basis of the same space);
+      // only directions whose pivot is at rounding level or below are dropped.
       for (int e = tid; e < nc * nc; e += kT) {
         const int i = e / nc + 1, j = e % nc + 1;
         w.stage[e] = (w.G[i * nm + j] - (Real)m * w.mupsi[i] * w.mupsi[j]) / (Real)m;
@@ -865,12 +883,8 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
       __syncthreads();
       for (int e = tid; e < nc * nc; e += kT) w.stage[e] *= w.scl[e / nc] * w.scl[e % nc];
       __syncthreads();
-      // the whitening only preconditions: any positive pivot is kept (the
-      // basis stays a basis of the same space); only directions whose pivot
-      // is at rounding level or below are dropped
       cta_chol<Real, kT>(w.stage, nc, nc, sizeof(Real) == 8 ? (Real)1e-14 : (Real)1e-10, w.invw,
                          &w.keep_w);
-      // R^{-1} (R = L^T, R[i][l] = L[l][i]) column by column into G; W = D R^{-1}
       for (int j = tid; j < nc; j += kT)
         for (int i = j; i >= 0; --i) {
           Real s = (i == j) ? (Real)1 : (Real)0;

@@ -588,17 +588,38 @@ def main():
     h2d = sum(v.numel() * v.element_size() for v in h.values())
     d2h = sum(v.numel() * v.element_size() for v in h_out.values())
 
+    side = torch.cuda.Stream()
+
     def e2e_step():
+        # the queries travel on a second stream while the fit runs, and the
+        # fit status returns while pack and search run; every copy lies
+        # between the step's start and end on the main stream
+        start = torch.cuda.Event()
+        start.record(stream)
+        side.wait_event(start)
+        with torch.cuda.stream(side):
+            d_in["q"].copy_(h["q"], non_blocking=True)
+        q_ready = torch.cuda.Event()
+        q_ready.record(side)
         for k in h:
-            d_in[k].copy_(h[k], non_blocking=True)
+            if k != "q":
+                d_in[k].copy_(h[k], non_blocking=True)
         rp.rp_fit(d_in["x"], d_in["y"], d_in["off"], DEGREE, precision=args.precision,
                   max_refine=8, tol=args.tol, degrees=d_in["deg"], out=fit_out, stream=stream)
+        fit_done = torch.cuda.Event()
+        fit_done.record(stream)
+        side.wait_event(fit_done)
+        with torch.cuda.stream(side):
+            h_out["status"].copy_(fit_out["status"], non_blocking=True)
         rp.rp_program_pack(fit_out["coef"], fit_out["box"], d_in["deg"], d_in["mm"], d_in["gd"],
                            DEGREE, program=prog, stream=stream)
+        stream.wait_event(q_ready)
         rp.rp_eval_search(prog, N_KERNELS, DEGREE, d_in["q"], out=s_out, stream=stream)
         h_out["argmin"].copy_(s_out["argmin"], non_blocking=True)
         h_out["best"].copy_(s_out["best"], non_blocking=True)
-        h_out["status"].copy_(fit_out["status"], non_blocking=True)
+        side_done = torch.cuda.Event()
+        side_done.record(side)
+        stream.wait_event(side_done)
 
     e2e_step()
     torch.cuda.synchronize()

@@ -445,6 +445,106 @@ def extra_measurements(rp, args, inst, x, y, off, deg, mm, gd, q, fit_out, prog,
     return out
 
 
+def run_secondary(args):
+    """Measurements of the path's other stated workloads (not the benchmarked
+    step): --workload tiny (the plain FP64 tiny case: 4 fits of 64 samples,
+    pack, one query; latency per call), diff (4096 fits, 20 Adam steps on
+    the relative MSE), uneven (8192 fits of 64..4096 samples and degree 2..4,
+    pack, 1e7 queries, replayed from one CUDA graph)."""
+    import torch
+    import paper_1906_00142_gb300 as rp
+    import workloads as W
+    from paper_1906_00142_gb300 import build as rpbuild
+    rpbuild.build()
+    rp.load_library()
+    dev = torch.device("cuda", 0)
+    td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    if args.workload == "tiny":
+        inst = W.tiny_instance()
+        x, y, off, deg = (td(inst[k]) for k in ("x", "y", "fit_off", "degree"))
+        mm = torch.full((1, 8), -1, dtype=torch.int32, device=dev)
+        mm[0, :4] = torch.arange(4, dtype=torch.int32, device=dev)
+        gd = torch.tensor([2], dtype=torch.int32, device=dev)
+        q = np.zeros((1, 8), np.float32)
+        q[0, W.Q_N], q[0, W.Q_NSM], q[0, W.Q_FGHZ], q[0, W.Q_MEMLD] = 4096, 120, 1.6, 600
+        q[0, W.Q_BW], q[0, W.Q_DDC], q[0, W.Q_DDU] = 4500, 10.5, 10.5
+        q = td(q)
+        out = rp.rp_fit(x, y, off, 2, precision="fp64", degrees=deg)
+        prog = rp.rp_program_pack(out["coef"], out["box"], deg, mm, gd, 2)
+        s_out = rp.rp_eval_search(prog, 1, 2, q)
+
+        def call():
+            rp.rp_fit(x, y, off, 2, precision="fp64", degrees=deg, out=out)
+            rp.rp_program_pack(out["coef"], out["box"], deg, mm, gd, 2, program=prog)
+            rp.rp_eval_search(prog, 1, 2, q, out=s_out)
+        ms = timed(call, 50)
+        line = {"workload": "tiny FP64: 4 fits x 64 samples (deg 2), pack, 1 query x 66 configs",
+                "us_per_call": ms * 1e3, "launches_per_call": 3}
+    elif args.workload == "diff":
+        inst = W.batched_instance(512, seed=20190604, m=512, d=3)
+        x, y, off, deg = (td(inst[k]) for k in ("x", "y", "fit_off", "degree"))
+        fit = rp.rp_fit(x, y, off, 3, precision="fp32", degrees=deg)
+        c = fit["coef"].clone()
+        ms = timed(lambda: rp.refine_relmse(c, x, y, off, deg, fit["box"], steps=20), 3)
+        F = 4096
+        line = {"workload": "4096 fits x 512 samples (deg 3), 20 Adam steps on the relative MSE "
+                            "(forward, hand-written backward, Adam) + 2 loss evaluations",
+                "ms_per_20_steps": ms, "fit_steps_per_s": F * 20 / (ms / 1e3)}
+    else:
+        K = 1024
+        inst = W.batched_instance(K, seed=20190605, degree_choices=(2, 3, 4), m_range=(64, 4096))
+        x, y, off, deg = (td(inst[k]) for k in ("x", "y", "fit_off", "degree"))
+        mm = td(inst["metric_map"])
+        gd = torch.full((K,), 2, dtype=torch.int32, device=dev)
+        qn = 10_000_000
+        q = td(W.queries(qn, K, seed=20190606))
+        F = len(inst["fit_off"]) - 1
+        res = {}
+        for prec in ("fp32", "bf16"):
+            out = rp.rp_fit(x, y, off, 4, precision=prec, degrees=deg,
+                            max_refine=16 if prec == "bf16" else 8)
+            out["workspace"] = torch.zeros(16, dtype=torch.uint8, device=dev)
+            prog = rp.rp_program_pack(out["coef"], out["box"], deg, mm, gd, 4)
+            s_out = rp.rp_eval_search(prog, K, 4, q)
+            s2 = torch.cuda.Stream()
+
+            def step(st):
+                rp.rp_fit(x, y, off, 4, precision=prec, degrees=deg, out=out, stream=st,
+                          max_refine=16 if prec == "bf16" else 8)
+                rp.rp_program_pack(out["coef"], out["box"], deg, mm, gd, 4, program=prog, stream=st)
+                rp.rp_eval_search(prog, K, 4, q, out=s_out, stream=st)
+            with torch.cuda.stream(s2):
+                step(s2)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s2):
+                step(s2)
+            ms = timed(lambda: g.replay(), 5)
+            fit_ms = timed(lambda: rp.rp_fit(x, y, off, 4, precision=prec, degrees=deg, out=out,
+                                             max_refine=16 if prec == "bf16" else 8), 3)
+            search_ms = timed(lambda: rp.rp_eval_search(prog, K, 4, q, out=s_out), 3)
+            st = out["status"].cpu().numpy()
+            res[prec] = {"graph_ms": ms, "fits_per_s": F / (ms / 1e3), "queries_per_s": qn / (ms / 1e3),
+                         "fit_ms": fit_ms, "search_ms": search_ms,
+                         "escalated_frac": float(((st & rp.RP_FIT_ESCALATED) != 0).mean())}
+        line = {"workload": f"{F} fits, 64..4096 samples (log-uniform, {len(inst['y'])} in all), "
+                            "deg 2..4; pack; 1e7 queries x 66 configs; one CUDA graph", **res}
+    print(json.dumps(line))
+
+
 def main():
     global N_KERNELS, N_QUERIES
     ap = argparse.ArgumentParser()
@@ -462,9 +562,15 @@ def main():
     ap.add_argument("--only", default="all", choices=["all", "fit", "search"],
                     help="profiling captures: launch only one phase per step")
     ap.add_argument("--no-tune", action="store_true", help="built-in launch shapes")
+    ap.add_argument("--workload", default="step", choices=["step", "tiny", "diff", "uneven"],
+                    help="step: the benchmarked fit + pack + search step; the others measure the "
+                         "path's other stated workloads")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the per-precision, plain-form and graph measurements")
     args = ap.parse_args()
+    if args.workload != "step":
+        run_secondary(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     N_KERNELS, N_QUERIES = args.kernels, args.queries

@@ -74,14 +74,31 @@ cudaError_t launch_fit(const rp_fit_desc &desc, const float *x, const float *y,
   const int dmax = desc.degree;
   const int p = desc.precision;
   a.drop_tol = (p == RP_PREC_FP64) ? 1e-13 : 1e-7;
-  switch (p) {
-    case RP_PREC_FP64: return fit_launch_f64(a, dmax, p, s);
-    case RP_PREC_TF32: return fit_launch_tf32(a, dmax, p, s);
-    case RP_PREC_TF32X3: return fit_launch_tf32x3(a, dmax, p, s);
-    case RP_PREC_BF16: return fit_launch_bf16(a, dmax, p, s);
-    case RP_PREC_BF16X3: return fit_launch_bf16x3(a, dmax, p, s);
-    default: return fit_launch_f32(a, dmax, p, s);
+  auto go = [&](int variant) {
+    switch (p) {
+      case RP_PREC_FP64: return fit_launch_f64(a, variant, p, s);
+      case RP_PREC_TF32: return fit_launch_tf32(a, variant, p, s);
+      case RP_PREC_TF32X3: return fit_launch_tf32x3(a, variant, p, s);
+      case RP_PREC_BF16: return fit_launch_bf16(a, variant, p, s);
+      case RP_PREC_BF16X3: return fit_launch_bf16x3(a, variant, p, s);
+      default: return fit_launch_f32(a, variant, p, s);
+    }
+  };
+  // A batch of per-fit degrees up to 4 runs as two launches on the stream:
+  // the degree-3 variant (4 CTAs/SM on the FP32 path) for degrees <= 3, the
+  // degree-4 variant (its basis needs ~250 registers) for degree 4 only.
+  if (desc.degrees && dmax == 4) {
+    a.deg_lo = 1;
+    a.deg_hi = 3;
+    cudaError_t e = go(3);
+    if (e != cudaSuccess) return e;
+    a.deg_lo = 4;
+    a.deg_hi = 4;
+    return go(4);
   }
+  a.deg_lo = 1;
+  a.deg_hi = dmax;
+  return go(dmax);
 }
 
 }  // namespace rpk

@@ -24,6 +24,7 @@ struct FitArgs {
   int32_t *status;
   int32_t *rank;
   unsigned long long *counter;   // dynamic fit schedule (workspace), or null
+  int deg_lo, deg_hi;            // degrees this launch fits (valid ones outside: skipped)
 };
 
 // Real = double, design Gram on CUDA cores (RP_PREC_FP64)

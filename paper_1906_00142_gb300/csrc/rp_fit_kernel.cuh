@@ -654,6 +654,10 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
     // ---------------- phase 0: range, degree, validation, box, distinct values
     const int64_t b0 = a.off[f], b1 = a.off[f + 1];
     const int d = a.degs ? (int)a.degs[f] : a.d_uniform;
+    // a launch of a split batch takes only its degrees (invalid degrees go
+    // to the launch that starts at 1); the others' outputs are not touched
+    const bool valid_d = d >= 1 && d <= a.d_uniform;
+    if (valid_d ? (d < a.deg_lo || d > a.deg_hi) : a.deg_lo > 1) continue;
     const bool range_ok = b0 >= 0 && b1 >= b0 && b1 <= a.S;
     const int m = range_ok ? (int)(b1 - b0) : 0;
     double *cf = a.coef + f * kStride;

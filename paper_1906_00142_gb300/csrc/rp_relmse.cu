@@ -39,18 +39,57 @@ Exps exps_table() {
   return t;
 }
 
+// Powers of the sample's normalised coordinates, 0..kMaxDeg, per variable.
+constexpr int kPw = kMaxDeg + 1;
+
 struct RelShared {
   double cf[kStride];
   double scd[3], ofd[3];
   float red[kT / 32];
-  float xn[kT][3];
+  float xp[kT][3][kPw];               // chunk samples: powers of x', B0', B1'
   float sp[kT], sq[kT];
+  float part[kT];                     // gradient partials per (entry, sample group)
 };
 
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Graded-lex index of the monomial x^a y^b z^c (degree ascending, then a
+// descending, then b descending): the same for every degree bound.
+__host__ __device__ constexpr int glex(int a, int b, int c) {
+  return (a + b + c) * (a + b + c + 1) * (a + b + c + 2) / 6 + (b + c) * (b + c + 1) / 2 + c;
+}
+
+// sum_j c_j x^a_j y^b_j z^c_j of total degree <= D as nested Horner
+// polynomials (one FMA per coefficient plus one per inner polynomial), FP64.
+template <int D>
+__device__ __forceinline__ double horner3(const double *c, double x, double y, double z) {
+  double p = 0.0;
+#pragma unroll
+  for (int a = D; a >= 0; --a) {
+    double pa = 0.0;
+#pragma unroll
+    for (int b = D - a; b >= 0; --b) {
+      double pab = 0.0;
+#pragma unroll
+      for (int cc = D - a - b; cc >= 0; --cc) pab = fma(pab, z, c[glex(a, b, cc)]);
+      pa = fma(pa, y, pab);
+    }
+    p = fma(p, x, pa);
+  }
+  return p;
+}
+
+__device__ __forceinline__ double horner_d(int d, const double *c, double x, double y, double z) {
+  switch (d) {
+    case 1: return horner3<1>(c, x, y, z);
+    case 2: return horner3<2>(c, x, y, z);
+    case 3: return horner3<3>(c, x, y, z);
+    default: return horner3<4>(c, x, y, z);
+  }
 }
 
 __global__ void __launch_bounds__(kT) relmse_kernel(bool backward, int64_t F, int64_t S,
@@ -84,32 +123,26 @@ __global__ void __launch_bounds__(kT) relmse_kernel(bool backward, int64_t F, in
     __syncthreads();
     const float gscale = backward ? grad_loss[f] : 1.0f;
     float lsum = 0.0f;
-    // backward: thread j owns gradient entry j (numerator j < nm, denominator
-    // nm + j); accumulated over chunks of kT samples.
+    // backward: gradient entry e (numerator e < nm, denominator nm + e) is
+    // summed by `groups` threads over interleaved samples of each chunk
+    const int ne = 2 * nm;
+    const int groups = ne > 0 ? max(1, kT / ne) : 1;
+    const int my_e = tid % max(ne, 1), my_g = tid / max(ne, 1);
+    const bool has_e = ne > 0 && tid < ne * groups;
+    const int e0 = has_e ? et.e[my_e % nm][0] : 0, e1 = has_e ? et.e[my_e % nm][1] : 0,
+              e2 = has_e ? et.e[my_e % nm][2] : 0;
+    const bool den = my_e >= nm;
     float gacc = 0.0f;
     for (int base = 0; base < m; base += kT) {
       const int cnt = min(kT, m - base);
       if (tid < cnt && nm > 0) {
         const int64_t i = b0 + base + tid;
-        // p and q in FP64: fitted monomial coefficients can cancel heavily,
-        // so an FP32 evaluation would lose the residual's leading digits
-        double xd[3];
-        xd[0] = fma((double)x[i], sh.scd[0], sh.ofd[0]);
-        xd[1] = fma((double)x[S + i], sh.scd[1], sh.ofd[1]);
-        xd[2] = fma((double)x[2 * S + i], sh.scd[2], sh.ofd[2]);
-        double pw[3][kMaxDeg + 1];
-#pragma unroll
-        for (int v = 0; v < 3; ++v) {
-          pw[v][0] = 1.0;
-#pragma unroll
-          for (int l = 1; l <= kMaxDeg; ++l) pw[v][l] = pw[v][l - 1] * xd[v];
-        }
-        double p = 0.0, q = 0.0;
-        for (int j = 0; j < nm; ++j) {
-          const double ph = pw[0][et.e[j][0]] * pw[1][et.e[j][1]] * pw[2][et.e[j][2]];
-          p = fma(sh.cf[j], ph, p);
-          q = fma(sh.cf[kHalf + j], ph, q);
-        }
+        const double xd0 = fma((double)x[i], sh.scd[0], sh.ofd[0]);
+        const double xd1 = fma((double)x[S + i], sh.scd[1], sh.ofd[1]);
+        const double xd2 = fma((double)x[2 * S + i], sh.scd[2], sh.ofd[2]);
+        // p and q in FP64: fitted monomial coefficients can cancel heavily
+        const double p = horner_d(d, sh.cf, xd0, xd1, xd2);
+        const double q = horner_d(d, sh.cf + kHalf, xd0, xd1, xd2);
         const float yy = y[i];
         const float r = (float)((p / q - (double)yy) / (double)yy);
         lsum = fmaf(r, r, lsum);
@@ -118,25 +151,25 @@ __global__ void __launch_bounds__(kT) relmse_kernel(bool backward, int64_t F, in
           const float iyq = 1.0f / (yy * qf);
           sh.sp[tid] = r * iyq;
           sh.sq[tid] = -r * pf * iyq / qf;
-          sh.xn[tid][0] = (float)xd[0];
-          sh.xn[tid][1] = (float)xd[1];
-          sh.xn[tid][2] = (float)xd[2];
+          const float xv[3] = {(float)xd0, (float)xd1, (float)xd2};
+#pragma unroll
+          for (int v = 0; v < 3; ++v) {
+            float pw = 1.0f;
+#pragma unroll
+            for (int l = 0; l < kPw; ++l) {
+              sh.xp[tid][v][l] = pw;
+              pw *= xv[v];
+            }
+          }
         }
       }
       if (backward) {
         __syncthreads();
-        if (tid < 2 * nm) {
-          const int j = tid % nm;
-          const bool den = tid >= nm;
-          const int e0 = et.e[j][0], e1 = et.e[j][1], e2 = et.e[j][2];
+        if (has_e) {
+          const float *s_r = den ? sh.sq : sh.sp;
           float part = 0.0f;
-          for (int s = 0; s < cnt; ++s) {
-            float ph = 1.0f;
-            for (int l = 0; l < e0; ++l) ph *= sh.xn[s][0];
-            for (int l = 0; l < e1; ++l) ph *= sh.xn[s][1];
-            for (int l = 0; l < e2; ++l) ph *= sh.xn[s][2];
-            part = fmaf(den ? sh.sq[s] : sh.sp[s], ph, part);
-          }
+          for (int s2 = my_g; s2 < cnt; s2 += groups)
+            part = fmaf(s_r[s2], sh.xp[s2][0][e0] * sh.xp[s2][1][e1] * sh.xp[s2][2][e2], part);
           gacc += part;
         }
         __syncthreads();
@@ -152,13 +185,16 @@ __global__ void __launch_bounds__(kT) relmse_kernel(bool backward, int64_t F, in
         out[f] = m > 0 ? s / (float)m : 0.0f;
       }
     } else {
-      const float scale = m > 0 ? 2.0f * gscale / (float)m : 0.0f;
+      // sum the sample groups of each entry (fixed order: deterministic)
+      sh.part[tid] = has_e ? gacc : 0.0f;
       if (tid < kStride) out[f * kStride + tid] = 0.0f;
       __syncthreads();
-      if (tid < 2 * nm) {
+      const float scale = m > 0 ? 2.0f * gscale / (float)m : 0.0f;
+      if (tid < ne) {
+        float g = 0.0f;
+        for (int g2 = 0; g2 < groups; ++g2) g += sh.part[g2 * ne + tid];
         const int j = tid % nm;
-        const bool den = tid >= nm;
-        if (!(den && j == 0)) out[f * kStride + (den ? kHalf + j : j)] = scale * gacc;
+        if (!(tid >= nm && j == 0)) out[f * kStride + (tid >= nm ? kHalf + j : j)] = scale * g;
       }
     }
     __syncthreads();

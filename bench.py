@@ -519,6 +519,8 @@ def run_secondary(args):
             out["workspace"] = torch.zeros(16, dtype=torch.uint8, device=dev)
             prog = rp.rp_program_pack(out["coef"], out["box"], deg, mm, gd, 4)
             s_out = rp.rp_eval_search(prog, K, 4, q)
+            s_out["workspace"] = torch.empty(rp.rp_search_workspace_size(K, qn), dtype=torch.uint8,
+                                             device=dev)
             s2 = torch.cuda.Stream()
 
             def step(st):
@@ -602,10 +604,15 @@ def main():
                    rank=torch.empty(F, dtype=torch.int32, device=dev),
                    workspace=torch.zeros(16, dtype=torch.uint8, device=dev))
     prog = torch.empty(rp.rp_program_size(N_KERNELS, DEGREE), dtype=torch.uint8, device=dev)
+    s_ws = rp.rp_search_workspace_size(N_KERNELS, N_QUERIES)   # queries bucketed by kernel
     s_out = dict(argmin=torch.empty(N_QUERIES, dtype=torch.int32, device=dev),
                  best=torch.empty(N_QUERIES, dtype=torch.float32, device=dev),
                  second=torch.empty(N_QUERIES, dtype=torch.float32, device=dev),
-                 status=torch.empty(N_QUERIES, dtype=torch.int32, device=dev))
+                 status=torch.empty(N_QUERIES, dtype=torch.int32, device=dev),
+                 workspace=torch.empty(s_ws, dtype=torch.uint8, device=dev))
+    # kernels per step: fit, pack; search: bucket count, scan, scatter and
+    # the grouped kernel (one kernel when the sizes select the direct path)
+    search_launches = 4 if s_ws > 0 else 1
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -779,7 +786,8 @@ def main():
                 "roofline": roof,
                 "e2e": {"value": job_rate(ws, F, e2e_ms), "unit": "fits/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-                "gpu_launches": (3 if args.only == "all" else 2 if args.only == "fit" else 1) * args.steps,
+                "gpu_launches": {"all": 2 + search_launches, "fit": 2,
+                                 "search": search_launches}[args.only] * args.steps,
                 "clocks": clk, "tuned": tuned}
         line.update(extra)
         if ws == 1 and not args.no_cpu_baseline and args.only == "all":

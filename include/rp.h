@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define RP_VERSION 1
+#define RP_VERSION 2
 #define RP_MAX_DEGREE 4          /* total degree bound d <= 4 */
 #define RP_COEF_STRIDE 70        /* alpha_j at [0, 35), beta_j at [35, 70) */
 #define RP_NUM_CONFIGS 66        /* (2^a, 2^b), a + b <= 10 */
@@ -219,11 +219,31 @@ typedef struct rp_hw_fixed {
  * Model: occupancy (Example 1, W_active = min(floor(B_active T/32), W_max)),
  * MWP-CWP as in Hong & Kim 2009 (the paper cites it and does not print
  * it); see the library's design notes for the exact statement.
- * hw: host pointer.  Errors: RP_ERR_INVALID_ARG, RP_ERR_CUDA.
+ * hw: host pointer.  workspace: NULL, or device memory of at least
+ * rp_search_workspace_size bytes, 16-byte aligned, owned by the caller and
+ * used by one call at a time.  With it (and a non-zero size for this K and
+ * Q) the queries are first bucketed by kernel id on the device and each
+ * block of threads evaluates queries of one kernel from a copy of that
+ * kernel's table in shared memory; with NULL each query gathers its table
+ * rows from global memory.  Results do not depend on the path.
+ * Errors: RP_ERR_INVALID_ARG, RP_ERR_WORKSPACE (workspace too small),
+ * RP_ERR_ALIGNMENT, RP_ERR_CUDA.
  */
 int rp_eval_search(const void *program, int64_t num_kernels, int32_t degree,
                    const rp_hw_fixed *hw, const float *queries, int64_t num_queries,
-                   int32_t *argmin, float *best, float *second, int32_t *status, void *stream);
+                   int32_t *argmin, float *best, float *second, int32_t *status,
+                   void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * rp_search_workspace_size -- bytes of the optional device workspace of
+ * rp_eval_search for num_kernels kernels and num_queries queries, written
+ * to *bytes: the bucket offsets and cursors (4 (2K + 3) bytes) and the
+ * bucketed query indices (4 Q bytes), each rounded up to 16 bytes.  0 when
+ * the search runs unbucketed for these sizes: fewer than 32 queries per
+ * kernel on average, Q >= 2^31 - 1 or K >= 2^30.  Host-only, launches
+ * nothing.  Errors: RP_ERR_INVALID_ARG (null bytes, negative sizes).
+ */
+int rp_search_workspace_size(int64_t num_kernels, int64_t num_queries, size_t *bytes);
 
 /*
  * rp_relmse_fwd -- per-fit mean squared relative error
@@ -272,13 +292,15 @@ int rp_adam_step(int64_t n, double *param, const float *grad, float *m, float *v
  * capturing.  Not thread-safe against concurrent launches of the same kind.
  *
  * rp_tune_search -- arguments as rp_eval_search; times persistent grids of
- * {256, 128, 64} threads per CTA and 2..32 CTAs per SM for `degree` and
- * writes the chosen threads per CTA and CTAs per SM.
+ * {256, 128, 64} threads per CTA and 2..32 CTAs per SM for `degree` on the
+ * path the workspace selects (the shape is shared by both paths) and writes
+ * the chosen threads per CTA and CTAs per SM.
  */
 int rp_tune_search(const void *program, int64_t num_kernels, int32_t degree,
                    const rp_hw_fixed *hw, const float *queries, int64_t num_queries,
-                   int32_t *argmin, float *best, float *second, int32_t *status, void *stream,
-                   int32_t *threads, int32_t *ctas_per_sm);
+                   int32_t *argmin, float *best, float *second, int32_t *status,
+                   void *workspace, size_t workspace_bytes, void *stream, int32_t *threads,
+                   int32_t *ctas_per_sm);
 
 /*
  * rp_tune_fit -- arguments as rp_fit; times persistent grids of 1 .. (the

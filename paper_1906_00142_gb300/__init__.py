@@ -8,8 +8,8 @@ device is missing, calls raise.
 
 Entry points (same names as the C ABI):
     rp_fit, rp_fit_workspace_size, rp_program_size, rp_program_pack,
-    rp_eval_search, rp_relmse_fwd, rp_relmse_bwd, rp_adam_step, rp_tune_fit, rp_tune_search,
-    rp_fit_noalloc,
+    rp_eval_search, rp_search_workspace_size, rp_relmse_fwd, rp_relmse_bwd,
+    rp_adam_step, rp_tune_fit, rp_tune_search, rp_fit_noalloc,
     rp_strerror, rp_version
 plus ``RelMSE`` (a torch.autograd.Function over rp_relmse_fwd/bwd) and
 ``refine_relmse`` (Adam steps with the hand-written backward).
@@ -73,14 +73,16 @@ def load_library(path: str = LIB_PATH):
             lib.rp_program_size.argtypes = [i64, i32]
             lib.rp_program_size.restype = C.c_size_t
             lib.rp_program_pack.argtypes = [i64, i32, P, P, P, P, P, P, C.c_size_t, P]
-            lib.rp_eval_search.argtypes = [P, i64, i32, C.POINTER(HwFixed), P, i64, P, P, P, P, P]
+            lib.rp_eval_search.argtypes = [P, i64, i32, C.POINTER(HwFixed), P, i64, P, P, P, P, P,
+                                           C.c_size_t, P]
+            lib.rp_search_workspace_size.argtypes = [i64, i64, C.POINTER(C.c_size_t)]
             lib.rp_relmse_fwd.argtypes = [i64, i64, P, P, P, P, P, P, P, P]
             lib.rp_relmse_bwd.argtypes = [i64, i64, P, P, P, P, P, P, P, P, P]
             lib.rp_adam_step.argtypes = [i64, P, P, P, P, P, i32, C.c_float, C.c_float, C.c_float,
                                          C.c_float, P]
             lib.rp_fit_noalloc.argtypes = [C.POINTER(FitDesc), P, P, P, P, P, P, P, P, P]
             lib.rp_tune_search.argtypes = [P, i64, i32, C.POINTER(HwFixed), P, i64, P, P, P, P, P,
-                                           C.POINTER(i32), C.POINTER(i32)]
+                                           C.c_size_t, P, C.POINTER(i32), C.POINTER(i32)]
             lib.rp_tune_fit.argtypes = [C.POINTER(FitDesc), P, P, P, P, P, P, P, P, P, C.c_size_t, P,
                                         C.POINTER(i32)]
             lib.rp_strerror.argtypes = [C.c_int]
@@ -251,7 +253,16 @@ def hw_struct(hw=None) -> HwFixed:
                    float(h["issue_cycles"]), 0)
 
 
-def _search_args(program, num_kernels, degree, queries, hw, out, stream):
+def rp_search_workspace_size(num_kernels: int, num_queries: int) -> int:
+    """Bytes of rp_eval_search's optional workspace (0: the search runs
+    unbucketed for these sizes)."""
+    b = C.c_size_t(0)
+    _check(load_library().rp_search_workspace_size(int(num_kernels), int(num_queries), C.byref(b)),
+           "rp_search_workspace_size")
+    return b.value
+
+
+def _search_args(program, num_kernels, degree, queries, hw, out, stream, grouped):
     Q = queries.shape[0]
     dev = queries.device
     if out is None:
@@ -259,28 +270,42 @@ def _search_args(program, num_kernels, degree, queries, hw, out, stream):
                    best=torch.empty(Q, dtype=torch.float32, device=dev),
                    second=torch.empty(Q, dtype=torch.float32, device=dev),
                    status=torch.empty(Q, dtype=torch.int32, device=dev))
+    st = torch.cuda.current_stream() if stream is None else stream
+    ws = None
+    ws_bytes = rp_search_workspace_size(num_kernels, Q) if grouped else 0
+    if ws_bytes:
+        ws = out.get("workspace")
+        if ws is None or ws.numel() < ws_bytes:
+            with torch.cuda.stream(st):        # stream-ordered reuse of the buffer
+                ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
     h = hw_struct(hw)
     args = (_dev(program, torch.uint8, "program"), int(num_kernels), int(degree), C.byref(h),
             _dev(queries, torch.float32, "queries"), Q, _dev(out["argmin"], torch.int32, "argmin"),
             _dev(out["best"], torch.float32, "best"), _dev(out["second"], torch.float32, "second"),
-            _dev(out["status"], torch.int32, "status"), _stream(stream))
-    return out, args, h
+            _dev(out["status"], torch.int32, "status"),
+            C.c_void_p(0 if ws is None else ws.data_ptr()),
+            C.c_size_t(0 if ws is None else ws.numel()), C.c_void_p(st.cuda_stream))
+    return out, args, (h, ws)
 
 
 def rp_eval_search(program, num_kernels: int, degree: int, queries: torch.Tensor, hw=None,
-                   out=None, stream=None):
-    """Evaluate-and-argmin for queries float32 [Q, 8] (CUDA)."""
-    out, args, _h = _search_args(program, num_kernels, degree, queries, hw, out, stream)
+                   out=None, stream=None, grouped: bool = True):
+    """Evaluate-and-argmin for queries float32 [Q, 8] (CUDA).  grouped: bucket
+    the queries by kernel first (workspace out["workspace"] or allocated
+    here; used where rp_search_workspace_size is non-zero); False: each
+    query reads its kernel's table from global memory.  Returns dict(argmin
+    int32 [Q], best float32 [Q], second float32 [Q], status int32 [Q])."""
+    out, args, _keep = _search_args(program, num_kernels, degree, queries, hw, out, stream, grouped)
     _check(load_library().rp_eval_search(*args), "rp_eval_search")
     return out
 
 
 def rp_tune_search(program, num_kernels: int, degree: int, queries: torch.Tensor, hw=None,
-                   out=None, stream=None):
+                   out=None, stream=None, grouped: bool = True):
     """Time the search kernel's launch shapes on these queries (see
     rp_tune_search in include/rp.h); returns (threads per CTA, CTAs per SM)
     now used for this degree.  Synchronises; call before any graph capture."""
-    out, args, _h = _search_args(program, num_kernels, degree, queries, hw, out, stream)
+    out, args, _keep = _search_args(program, num_kernels, degree, queries, hw, out, stream, grouped)
     t, c = C.c_int32(0), C.c_int32(0)
     _check(load_library().rp_tune_search(*args, C.byref(t), C.byref(c)), "rp_tune_search")
     return t.value, c.value

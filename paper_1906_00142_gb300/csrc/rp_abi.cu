@@ -116,9 +116,16 @@ int rp_program_pack(int64_t num_kernels, int32_t degree, const double *coef, con
                                     pm, as_stream(stream)));
 }
 
+int rp_search_workspace_size(int64_t num_kernels, int64_t num_queries, size_t *bytes) {
+  if (!bytes || num_kernels < 0 || num_queries < 0) return RP_ERR_INVALID_ARG;
+  *bytes = rpk::search_workspace_bytes(num_kernels, num_queries);
+  return RP_OK;
+}
+
 int rp_eval_search(const void *program, int64_t num_kernels, int32_t degree,
                    const rp_hw_fixed *hw, const float *queries, int64_t num_queries,
-                   int32_t *argmin, float *best, float *second, int32_t *status, void *stream) {
+                   int32_t *argmin, float *best, float *second, int32_t *status,
+                   void *workspace, size_t workspace_bytes, void *stream) {
   if (num_kernels < 0 || num_queries < 0 || degree < 0 || degree > RP_MAX_DEGREE || !hw)
     return RP_ERR_INVALID_ARG;
   if (hw->warp_size < 1 || hw->t_max < 1 || hw->b_max < 1 || hw->w_max < 1 || hw->r_sm < 1 ||
@@ -128,20 +135,26 @@ int rp_eval_search(const void *program, int64_t num_kernels, int32_t degree,
   if (num_queries == 0) return RP_OK;
   if (!program || !queries || !argmin || !best || !second || !status) return RP_ERR_INVALID_ARG;
   if (!aligned(program, 16) || !aligned(queries, 16)) return RP_ERR_ALIGNMENT;
+  if (workspace) {
+    if (workspace_bytes < rpk::search_workspace_bytes(num_kernels, num_queries))
+      return RP_ERR_WORKSPACE;
+    if (!aligned(workspace, 16)) return RP_ERR_ALIGNMENT;
+  }
   if (!device_ok()) return RP_ERR_NO_DEVICE;
   auto pv = rpk::program_sections<rpk::ProgramView>(program, num_kernels);
   return from_cuda(rpk::launch_search(pv, num_kernels, degree, *hw, queries, num_queries, argmin,
-                                      best, second, status, as_stream(stream)));
+                                      best, second, status, workspace, as_stream(stream)));
 }
 
 int rp_tune_search(const void *program, int64_t num_kernels, int32_t degree,
                    const rp_hw_fixed *hw, const float *queries, int64_t num_queries,
-                   int32_t *argmin, float *best, float *second, int32_t *status, void *stream,
-                   int32_t *threads, int32_t *ctas_per_sm) {
+                   int32_t *argmin, float *best, float *second, int32_t *status,
+                   void *workspace, size_t workspace_bytes, void *stream, int32_t *threads,
+                   int32_t *ctas_per_sm) {
   if (!threads || !ctas_per_sm) return RP_ERR_INVALID_ARG;
   // validates everything once (and is the first, untimed call)
   int rc = rp_eval_search(program, num_kernels, degree, hw, queries, num_queries, argmin, best,
-                          second, status, stream);
+                          second, status, workspace, workspace_bytes, stream);
   if (rc != RP_OK) return rc;
   static const rpk::SearchShape cand[] = {{256, 8}, {256, 4}, {256, 2}, {128, 16}, {128, 8},
                                           {128, 4}, {64, 32}, {64, 16}};
@@ -153,7 +166,7 @@ int rp_tune_search(const void *program, int64_t num_kernels, int32_t degree,
     const float ms = time_calls(
         [&] {
           return rp_eval_search(program, num_kernels, degree, hw, queries, num_queries, argmin,
-                                best, second, status, stream);
+                                best, second, status, workspace, workspace_bytes, stream);
         },
         3, as_stream(stream));
     if (ms < 0.0f) {

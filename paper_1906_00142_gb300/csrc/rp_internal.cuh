@@ -58,9 +58,13 @@ cudaError_t launch_pack(int64_t K, int d, const double *coef, const double *box,
                         const int8_t *degrees, const int32_t *metric_map, const int32_t *grid_dims,
                         ProgramMut prog, cudaStream_t s);
 
+// workspace: NULL (queries in input order) or search_workspace_bytes(K, Q)
+// bytes, 16-byte aligned (queries bucketed by kernel first); ignored when
+// search_workspace_bytes is 0.
 cudaError_t launch_search(ProgramView prog, int64_t K, int d, const rp_hw_fixed &hw,
                           const float *queries, int64_t Q, int32_t *argmin, float *best,
-                          float *second, int32_t *status, cudaStream_t s);
+                          float *second, int32_t *status, void *workspace, cudaStream_t s);
+size_t search_workspace_bytes(int64_t K, int64_t Q);
 
 cudaError_t launch_fit(const rp_fit_desc &desc, const float *x, const float *y,
                        const int64_t *fit_off, double *coef, float *coef32, double *box,

@@ -105,6 +105,8 @@ struct CfgTab {
   int8_t lb[kNcfg];        // log2 B1
   int32_t wpb[kNcfg];      // warps per block, ceil(T / warp)
   int32_t bact_w[kNcfg];   // min(B_max, floor(W_max / wpb)), 0 if T > T_max
+  int32_t rsm_w[kNcfg];    // floor(R_SM / (wpb warp)): R <= rsm_w <=> R wpb warp <= R_SM
+  int32_t rsm_t[kNcfg];    // floor(R_SM / T): R <= rsm_t <=> R T <= R_SM
 };
 
 struct HwC {
@@ -112,30 +114,21 @@ struct HwC {
   float issue;
 };
 
-// #Rep = ceil(blocks / D) for blocks = c0 * c1 (each < 2^32) and
-// 1 <= D < 2^25.  Exact (integer remainder correction of a float estimate)
-// when the quotient is below 2^22; above that the float estimate (relative
-// error < 2^-21) is used.  Only 32-bit int<->float conversions are used.
+// #Rep = ceil(c0 c1 / D) for c0 c1 >= 1 (c0, c1 < 2^32) and 1 <= D < 2^22.
+// Exact when the quotient is below 2^22: the float estimate q0 is then within
+// 2 of it, so the remainder c0 c1 - q0 D lies in (-3D, 4D), is formed exactly
+// in 32-bit wrap-around arithmetic and is exact in FP32; its ceiling quotient
+// by D is rounded up and corrected with exact FMA residuals.  Above 2^22 the
+// float estimate (relative error < 2^-21) is used.
 __device__ __forceinline__ float rep_count(uint32_t c0, uint32_t c1, uint32_t D) {
-  const float qf = __fdividef((float)c0 * (float)c1, (float)D);
-  const uint64_t blocks = (uint64_t)c0 * c1;
+  const float Df = (float)D;
+  const float qf = __fdividef((float)c0 * (float)c1, Df);
   const uint32_t q0 = (uint32_t)fminf(qf, 4194304.0f);
-  int64_t r = (int64_t)(blocks - (uint64_t)q0 * D);
-  int64_t q = q0;
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const bool lo = r < 0;
-    q -= lo;
-    r += lo ? (int64_t)D : 0;
-  }
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const bool hi = r >= (int64_t)D;
-    q += hi;
-    r -= hi ? (int64_t)D : 0;
-  }
-  const float exact = (float)(uint32_t)(q + (r > 0));
-  return qf < 4194304.0f ? exact : ceilf(qf);
+  const float rf = (float)(int32_t)(c0 * c1 - q0 * D);
+  float k = ceilf(__fdividef(rf, Df));
+  k += fmaf(k, Df, -rf) < 0.0f ? 1.0f : 0.0f;
+  k -= fmaf(k - 1.0f, Df, -rf) >= 0.0f ? 1.0f : 0.0f;
+  return qf < 4194304.0f ? (float)q0 + k : ceilf(qf);
 }
 
 // floor(a / b) for 0 <= a < 2^24, 1 <= b < 2^24 (exact).
@@ -156,13 +149,31 @@ __device__ __forceinline__ float div_pos(float x, float y) {
   return y > 0.0f ? __fdividef(x, y) : INFINITY;
 }
 
-template <int D1>
+// Loads of the program's coefficients: read-only global loads, or plain
+// loads from a copy staged in shared memory (SH).
+template <bool SH>
+__device__ __forceinline__ float4 ld4(const float4 *p) {
+  if constexpr (SH) return *p;
+  else return __ldg(p);
+}
+template <bool SH>
+__device__ __forceinline__ float2 ld2(const float2 *p) {
+  if constexpr (SH) return *p;
+  else return __ldg(p);
+}
+template <bool SH>
+__device__ __forceinline__ float ld1(const float *p) {
+  if constexpr (SH) return *p;
+  else return __ldg(p);
+}
+
+template <int D1, bool SH>
 __device__ __forceinline__ void load_row(const float *__restrict__ p, float (&c)[2 * D1]) {
   if constexpr ((2 * D1) % 4 == 0) {
     const float4 *p4 = reinterpret_cast<const float4 *>(p);
 #pragma unroll
     for (int i = 0; i < (2 * D1) / 4; ++i) {
-      const float4 v = __ldg(p4 + i);
+      const float4 v = ld4<SH>(p4 + i);
       c[4 * i] = v.x;
       c[4 * i + 1] = v.y;
       c[4 * i + 2] = v.z;
@@ -172,19 +183,139 @@ __device__ __forceinline__ void load_row(const float *__restrict__ p, float (&c)
     const float2 *p2 = reinterpret_cast<const float2 *>(p);
 #pragma unroll
     for (int i = 0; i < D1; ++i) {
-      const float2 v = __ldg(p2 + i);
+      const float2 v = ld2<SH>(p2 + i);
       c[2 * i] = v.x;
       c[2 * i + 1] = v.y;
     }
   }
 }
 
-// One thread per query; persistent grid-stride loop.  Every configuration is
-// evaluated in registers without data-dependent branches (invalid and pole
-// configurations evaluate to +inf), and the running (best, second, argmin) is
-// kept in registers, so no cross-thread reduction is needed.
+// The evaluate-and-argmin of one query (Sec. 3.3 Steps 4-5): every
+// configuration is evaluated in registers without data-dependent branches
+// (invalid and pole configurations evaluate to +inf) and the running (best,
+// second, argmin) is kept in registers.  aN8, bN8, grid and tab are the
+// query's kernel's sections of the program (global memory, or a shared-memory
+// copy when SH); kid_ok: the query's kernel id names a kernel of the program.
+template <int D1, bool SH>
+__device__ __forceinline__ void eval_query(const float4 q0, const float4 q1, bool kid_ok,
+                                           const float *aN8, const float *bN8, int32_t grid,
+                                           const float *tab, const CfgTab &cfg, const HwC &hw,
+                                           int &arg_out, float &b1_out, float &b2_out,
+                                           int &st_out) {
+  const float N = q0.x, nsm = q0.y, fghz = q0.z, memld = q0.w;
+  const float bw = q1.x, ddc = q1.y, ddu = q1.z;
+  float b1 = INFINITY, b2 = INFINITY;
+  int arg = -1, st = 0;
+  const bool finite = isfinite(N) && isfinite(nsm) && isfinite(fghz) && isfinite(memld) &&
+                      isfinite(bw) && isfinite(ddc) && isfinite(ddu);
+  if (!finite || !kid_ok || !(N >= 1.0f) || !(nsm >= 1.0f) || !(fghz > 0.0f) ||
+      !(bw > 0.0f) || !(memld >= 0.0f) || !(ddc >= 0.0f) || !(ddu >= 0.0f) ||
+      !(N <= 4294967040.0f) || !(nsm <= 1048576.0f)) {
+    st = RP_Q_BAD;
+  } else {
+    float t[kNmet];
+#pragma unroll
+    for (int m = 0; m < kNmet; ++m) t[m] = fmaf(ld1<SH>(aN8 + m), N, ld1<SH>(bN8 + m));
+    const uint32_t Ni = (uint32_t)ceilf(N);
+    const uint32_t nsm_i = (uint32_t)nsm;
+    const bool grid1 = grid == 1;
+    bool any_pole = false;
+    for (int c = 0; c < kNcfg; ++c) {
+      float mv[kNmet];
+      unsigned dbits = 0u;
+      const float *row = tab + c * kNmet * 2 * D1;
+#pragma unroll
+      for (int m = 0; m < kNmet; ++m) {
+        float cf[2 * D1];
+        load_row<D1, SH>(row + m * 2 * D1, cf);
+        float p = cf[D1 - 1], d = cf[2 * D1 - 1];
+#pragma unroll
+        for (int j = D1 - 2; j >= 0; --j) {
+          p = fmaf(p, t[m], cf[j]);
+          d = fmaf(d, t[m], cf[D1 + j]);
+        }
+        // 0 < d < 8.5e37 (NaN excluded) <=> bits(d) - 1 < bits(8.5e37) - 1,
+        // unsigned: one running maximum instead of two compares per metric
+        dbits = max(dbits, __float_as_uint(d) - 1u);
+        mv[m] = __fdividef(p, d);
+      }
+      const float comp = fmaxf(mv[0], 0.0f), Cm = fmaxf(mv[1], 0.0f),
+                  U = fmaxf(mv[2], 0.0f), upm = fmaxf(mv[3], 1.0f),
+                  synch = fmaxf(mv[4], 0.0f), lbw = fmaxf(mv[5], 0.0f);
+      // clamped at 2^24: above every admissible R_SM / Z_SM (< 2^24), so
+      // the configuration is invalid either way
+      const float Rf = fminf(fmaxf(mv[6], 0.0f), 16777216.0f);
+      const float Zf = fminf(fmaxf(mv[7], 0.0f), 16777216.0f);
+      const int Ri = (int)floorf(Rf + 0.5f), Zi = (int)floorf(Zf + 0.5f);
+      const bool pole = dbits >= __float_as_uint(8.5e37f) - 1u;
+      const int la = cfg.la[c], lb = cfg.lb[c];
+      const int wpb = cfg.wpb[c];
+      // floor(R_SM / (R wpb warp)) = floor(floor(R_SM / (wpb warp)) / R)
+      const int tR = floor_div_small(cfg.rsm_w[c], max(Ri, 1));
+      const int tZ = floor_div_small(hw.zsm, max(Zi, 1));
+      int bact = cfg.bact_w[c];
+      bact = Ri > 0 ? min(bact, tR) : bact;
+      bact = Zi > 0 ? min(bact, tZ) : bact;
+      const bool valid = !pole && bact > 0 && Ri <= cfg.rsm_t[c] && Zi <= hw.zsm;
+      bact = max(bact, 1);
+      const float Nw = (float)min(bact * wpb, hw.wmax);
+      const uint32_t c0 = grid1 ? ceil_shift(Ni, la + lb) : ceil_shift(Ni, la);
+      const uint32_t c1 = grid1 ? 1u : ceil_shift(Ni, lb);
+      // fewer blocks than SMs (decided exactly in FP32: below 2^24 the
+      // product is exact, above it is >= 2^24 > SMs): every block runs in
+      // one round, #Rep = 1
+      const float blocks = (float)c0 * (float)c1;
+      const bool few = blocks < (float)nsm_i;
+      const float asm_ = few ? blocks : (float)nsm_i;
+      const float rep = few ? 1.0f : rep_count(c0, c1, (uint32_t)bact * nsm_i);
+      const float mem_insts = U + Cm;
+      const float comp_cycles = hw.issue * (comp + mem_insts);
+      const bool has_mem = mem_insts > 0.0f;
+      const float inv_mi = has_mem ? __fdividef(1.0f, mem_insts) : 0.0f;
+      const float wu = U * inv_mi, wc = Cm * inv_mi;
+      const float ml_unc = fmaf(upm - 1.0f, ddu, memld);
+      const float ml = fmaf(ml_unc, wu, memld * wc);
+      const float dd = fmaf(ddu * upm, wu, ddc * wc);
+      const float mwp_nobw = div_pos(ml, dd);
+      const float bwpw = div_pos(fghz * lbw, ml);
+      const float mwp_bw = div_pos(bw, bwpw * asm_);
+      const float mwp_u = fminf(mwp_nobw, mwp_bw);
+      const bool mwp_cap = Nw <= mwp_u;
+      const float MWP = fminf(mwp_u, Nw);
+      const float mem_cycles = fmaf(ml_unc, U, memld * Cm);
+      const float cwp_full = div_pos(mem_cycles + comp_cycles, comp_cycles);
+      const bool cwp_cap = Nw <= cwp_full;
+      const float CWP = fminf(cwp_full, Nw);
+      const float per = comp_cycles * inv_mi;
+      const float over = fmaxf(MWP - 1.0f, 0.0f);
+      const float cy1 = fmaf(per, over, mem_cycles + comp_cycles);
+      const float cy2 = fmaf(per, over, div_pos(mem_cycles * Nw, MWP));
+      const float cy3 = fmaf(comp_cycles, Nw, memld);
+      const float cyc = (mwp_cap && cwp_cap) ? cy1 : ((CWP >= MWP || comp_cycles > mem_cycles) ? cy2 : cy3);
+      const float synch_cost = dd * over * synch * (float)bact;
+      float ex = has_mem ? (cyc + synch_cost) * rep : comp_cycles * rep;
+      ex = valid ? ex : INFINITY;
+      any_pole |= pole;
+      const bool better = ex < b1;
+      const bool second_better = !better && ex < b2;
+      b2 = better ? b1 : (second_better ? ex : b2);
+      arg = better ? c : arg;
+      b1 = better ? ex : b1;
+    }
+    st |= any_pole ? RP_Q_POLE : 0;
+    if (arg < 0) st |= RP_Q_NO_VALID;
+  }
+  arg_out = arg;
+  b1_out = b1;
+  b2_out = b2;
+  st_out = st;
+}
+
+// One thread per query, queries in input order; persistent grid-stride
+// loop.  Each query gathers its kernel's table rows from global memory (L2).
 template <int D1>
-__global__ void __launch_bounds__(256) search_kernel(ProgramView P, int64_t K, CfgTab cfg, HwC hw,
+__global__ void __launch_bounds__(256) search_kernel(ProgramView P, int64_t K,
+                                                     const __grid_constant__ CfgTab cfg, HwC hw,
                                                      const float4 *__restrict__ q, int64_t Q,
                                                      int32_t *__restrict__ argmin,
                                                      float *__restrict__ best,
@@ -194,110 +325,188 @@ __global__ void __launch_bounds__(256) search_kernel(ProgramView P, int64_t K, C
        i += (int64_t)gridDim.x * blockDim.x) {
     const float4 q0 = __ldg(q + 2 * i);
     const float4 q1 = __ldg(q + 2 * i + 1);
-    const float N = q0.x, nsm = q0.y, fghz = q0.z, memld = q0.w;
-    const float bw = q1.x, ddc = q1.y, ddu = q1.z;
     const int32_t kid = __float_as_int(q1.w);
-    float b1 = INFINITY, b2 = INFINITY;
-    int arg = -1, st = 0;
-    const bool finite = isfinite(N) && isfinite(nsm) && isfinite(fghz) && isfinite(memld) &&
-                        isfinite(bw) && isfinite(ddc) && isfinite(ddu);
-    if (!finite || kid < 0 || kid >= K || !(N >= 1.0f) || !(nsm >= 1.0f) || !(fghz > 0.0f) ||
-        !(bw > 0.0f) || !(memld >= 0.0f) || !(ddc >= 0.0f) || !(ddu >= 0.0f) ||
-        !(N <= 4294967040.0f) || !(nsm <= 1048576.0f)) {
-      st = RP_Q_BAD;
-    } else {
-      float t[kNmet];
-#pragma unroll
-      for (int m = 0; m < kNmet; ++m)
-        t[m] = fmaf(__ldg(P.aN + kid * kNmet + m), N, __ldg(P.bN + kid * kNmet + m));
-      const uint32_t Ni = (uint32_t)ceilf(N);
-      const uint32_t nsm_i = (uint32_t)nsm;
-      const bool grid1 = __ldg(P.grid + kid) == 1;
-      const float *tab = P.table + (int64_t)kid * kNcfg * kNmet * 2 * D1;
-      bool any_pole = false;
-      for (int c = 0; c < kNcfg; ++c) {
-        float mv[kNmet];
-        bool pole = false;
-        const float *row = tab + c * kNmet * 2 * D1;
-#pragma unroll
-        for (int m = 0; m < kNmet; ++m) {
-          float cf[2 * D1];
-          load_row<D1>(row + m * 2 * D1, cf);
-          float p = cf[D1 - 1], d = cf[2 * D1 - 1];
-#pragma unroll
-          for (int j = D1 - 2; j >= 0; --j) {
-            p = fmaf(p, t[m], cf[j]);
-            d = fmaf(d, t[m], cf[D1 + j]);
-          }
-          pole |= !(d > 0.0f) || !(d < 8.5e37f);
-          mv[m] = __fdividef(p, d);
-        }
-        const float comp = fmaxf(mv[0], 0.0f), Cm = fmaxf(mv[1], 0.0f),
-                    U = fmaxf(mv[2], 0.0f), upm = fmaxf(mv[3], 1.0f),
-                    synch = fmaxf(mv[4], 0.0f), lbw = fmaxf(mv[5], 0.0f);
-        // clamped at 2^24: above every admissible R_SM / Z_SM (< 2^24), so
-        // the configuration is invalid either way
-        const float Rf = fminf(fmaxf(mv[6], 0.0f), 16777216.0f);
-        const float Zf = fminf(fmaxf(mv[7], 0.0f), 16777216.0f);
-        const int Ri = (int)floorf(Rf + 0.5f), Zi = (int)floorf(Zf + 0.5f);
-        const int la = cfg.la[c], lb = cfg.lb[c];
-        const int T = 1 << (la + lb);
-        const int wpb = cfg.wpb[c];
-        const int64_t bR = (int64_t)max(Ri, 1) * wpb * hw.warp;
-        const int tR = bR > hw.rsm ? 0 : floor_div_small(hw.rsm, (int)bR);
-        const int tZ = floor_div_small(hw.zsm, max(Zi, 1));
-        int bact = cfg.bact_w[c];
-        bact = Ri > 0 ? min(bact, tR) : bact;
-        bact = Zi > 0 ? min(bact, tZ) : bact;
-        const bool valid = !pole && bact > 0 && (int64_t)Ri * T <= hw.rsm && Zi <= hw.zsm;
-        bact = max(bact, 1);
-        const float Nw = (float)min(bact * wpb, hw.wmax);
-        const uint32_t c0 = grid1 ? ceil_shift(Ni, la + lb) : ceil_shift(Ni, la);
-        const uint32_t c1 = grid1 ? 1u : ceil_shift(Ni, lb);
-        const bool few = (uint64_t)c0 * c1 < (uint64_t)nsm_i;
-        const uint32_t asm_ = few ? c0 * c1 : nsm_i;
-        const float rep = rep_count(c0, c1, (uint32_t)bact * asm_);
-        const float mem_insts = U + Cm;
-        const float comp_cycles = hw.issue * (comp + mem_insts);
-        const bool has_mem = mem_insts > 0.0f;
-        const float inv_mi = has_mem ? __fdividef(1.0f, mem_insts) : 0.0f;
-        const float wu = U * inv_mi, wc = Cm * inv_mi;
-        const float ml_unc = fmaf(upm - 1.0f, ddu, memld);
-        const float ml = fmaf(ml_unc, wu, memld * wc);
-        const float dd = fmaf(ddu * upm, wu, ddc * wc);
-        const float mwp_nobw = div_pos(ml, dd);
-        const float bwpw = div_pos(fghz * lbw, ml);
-        const float mwp_bw = div_pos(bw, bwpw * (float)asm_);
-        const float mwp_u = fminf(mwp_nobw, mwp_bw);
-        const bool mwp_cap = Nw <= mwp_u;
-        const float MWP = fminf(mwp_u, Nw);
-        const float mem_cycles = fmaf(ml_unc, U, memld * Cm);
-        const float cwp_full = div_pos(mem_cycles + comp_cycles, comp_cycles);
-        const bool cwp_cap = Nw <= cwp_full;
-        const float CWP = fminf(cwp_full, Nw);
-        const float per = comp_cycles * inv_mi;
-        const float over = fmaxf(MWP - 1.0f, 0.0f);
-        const float cy1 = fmaf(per, over, mem_cycles + comp_cycles);
-        const float cy2 = fmaf(per, over, div_pos(mem_cycles * Nw, MWP));
-        const float cy3 = fmaf(comp_cycles, Nw, memld);
-        const float cyc = (mwp_cap && cwp_cap) ? cy1 : ((CWP >= MWP || comp_cycles > mem_cycles) ? cy2 : cy3);
-        const float synch_cost = dd * over * synch * (float)bact;
-        float ex = has_mem ? (cyc + synch_cost) * rep : comp_cycles * rep;
-        ex = valid ? ex : INFINITY;
-        any_pole |= pole;
-        const bool better = ex < b1;
-        const bool second_better = !better && ex < b2;
-        b2 = better ? b1 : (second_better ? ex : b2);
-        arg = better ? c : arg;
-        b1 = better ? ex : b1;
-      }
-      st |= any_pole ? RP_Q_POLE : 0;
-      if (arg < 0) st |= RP_Q_NO_VALID;
-    }
+    const bool kid_ok = kid >= 0 && kid < K;
+    const int64_t k = kid_ok ? kid : 0;
+    int arg, st;
+    float b1, b2;
+    eval_query<D1, false>(q0, q1, kid_ok, P.aN + k * kNmet, P.bN + k * kNmet,
+                          kid_ok ? __ldg(P.grid + k) : 0,
+                          P.table + k * kNcfg * kNmet * 2 * D1, cfg, hw, arg, b1, b2, st);
     argmin[i] = arg;
     best[i] = b1;
     second[i] = b2;
     status[i] = st;
+  }
+}
+
+// ---------------------------------------------------------------------
+// Grouped search: the queries are bucketed by kernel id on the device
+// (count, exclusive scan, scatter of query indices), then each CTA takes a
+// tile of consecutive bucketed positions, stages the table of each kernel
+// that occurs in the tile in shared memory once, and evaluates that
+// kernel's queries from there (every lane of a warp reads the same row:
+// shared-memory broadcasts).  Bucket K collects queries whose kernel id is
+// out of range.  Results do not depend on the order within a bucket.
+
+// bucket of query i: its kernel id, or K if out of range
+__device__ __forceinline__ int query_bucket(const float *__restrict__ q, int64_t i, int64_t K) {
+  const int32_t kid = __float_as_int(__ldg(q + 8 * i + 7));
+  return (kid >= 0 && kid < K) ? kid : (int)K;
+}
+
+constexpr int kBucketSmem = 8192;   // buckets counted in shared memory up to this many
+
+// cnt[b] += number of queries in bucket b (cnt zeroed by the caller)
+__global__ void bucket_count_kernel(const float *__restrict__ q, int64_t Q, int64_t K,
+                                    int32_t *__restrict__ cnt) {
+  extern __shared__ int32_t hist[];
+  const bool local = K + 1 <= kBucketSmem;
+  if (local)
+    for (int j = threadIdx.x; j <= K; j += blockDim.x) hist[j] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    // warp-aggregated: one atomic per distinct bucket in the warp (queries
+    // in kernel order would otherwise serialise 32 atomics on one counter)
+    const int b = query_bucket(q, i, K);
+    const unsigned peers = __match_any_sync(__activemask(), b);
+    if (lane == __ffs(peers) - 1) {
+      if (local) atomicAdd(&hist[b], __popc(peers));
+      else atomicAdd(&cnt[b], __popc(peers));
+    }
+  }
+  __syncthreads();
+  if (local)
+    for (int j = threadIdx.x; j <= K; j += blockDim.x)
+      if (hist[j]) atomicAdd(&cnt[j], hist[j]);
+}
+
+// In place: off[0..n) counts -> off[0..n] exclusive offsets (off[n] = total);
+// cur[0..n) = off[0..n) (the scatter's cursors).  One CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) bucket_scan_kernel(int32_t *__restrict__ off,
+                                                           int32_t *__restrict__ cur, int n) {
+  __shared__ int32_t wsum[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t carry = 0;
+  for (int base = 0; base < n; base += 1024) {
+    const int j = base + threadIdx.x;
+    const int32_t v = j < n ? off[j] : 0;
+    int32_t x = v;   // inclusive scan within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int32_t w = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      wsum[lane] = w;   // inclusive over warps
+    }
+    __syncthreads();
+    const int32_t before = carry + (wid > 0 ? wsum[wid - 1] : 0) + x - v;
+    if (j < n) {
+      off[j] = before;
+      cur[j] = before;
+    }
+    carry += wsum[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) off[n] = carry;
+}
+
+// perm[cur[b]++] = i for every query i of bucket b
+__global__ void bucket_scatter_kernel(const float *__restrict__ q, int64_t Q, int64_t K,
+                                      int32_t *__restrict__ cur, int32_t *__restrict__ perm) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    // warp-aggregated: the lowest lane of each bucket's group claims the
+    // group's slots, the others take consecutive ones after it
+    const int b = query_bucket(q, i, K);
+    const unsigned peers = __match_any_sync(__activemask(), b);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&cur[b], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    perm[base + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
+  }
+}
+
+// Dynamic shared memory of the grouped kernel: one kernel's table, its aN
+// and bN, and one bucket id per thread.
+template <int D1>
+__host__ __device__ constexpr int grouped_table_floats() { return kNcfg * kNmet * 2 * D1; }
+template <int D1>
+size_t grouped_smem(int threads) {
+  return (size_t)(grouped_table_floats<D1>() + 2 * kNmet) * sizeof(float) + (size_t)threads * 4;
+}
+
+template <int D1>
+__global__ void __launch_bounds__(256, 3) search_grouped_kernel(
+    ProgramView P, int64_t K, const __grid_constant__ CfgTab cfg, HwC hw,
+    const float4 *__restrict__ q, int64_t Q, const int32_t *__restrict__ perm,
+    int32_t *__restrict__ argmin, float *__restrict__ best, float *__restrict__ second,
+    int32_t *__restrict__ status) {
+  constexpr int TF = grouped_table_floats<D1>();
+  extern __shared__ float4 smem4[];
+  float *tab_s = reinterpret_cast<float *>(smem4);   // TF floats (a multiple of 4)
+  float *ab_s = tab_s + TF;                           // aN[8], bN[8]
+  int32_t *bk_s = reinterpret_cast<int32_t *>(ab_s + 2 * kNmet);
+  __shared__ int32_t grid_s;
+  const int T = blockDim.x;
+  const int64_t ntiles = (Q + T - 1) / T;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t p = tile * T + threadIdx.x;
+    const bool act = p < Q;
+    int32_t qi = 0;
+    float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
+    int b = (int)K + 1;   // past every bucket: inactive
+    if (act) {
+      qi = __ldg(perm + p);
+      q0 = __ldg(q + 2 * (int64_t)qi);
+      q1 = __ldg(q + 2 * (int64_t)qi + 1);
+      const int32_t kid = __float_as_int(q1.w);
+      b = (kid >= 0 && kid < K) ? kid : (int)K;
+    }
+    bk_s[threadIdx.x] = b;
+    __syncthreads();
+    // the tile's positions are bucket-sorted with the inactive ones last:
+    // one run per bucket present
+    for (int pos = 0; pos < T;) {
+      const int cb = bk_s[pos];
+      if (cb > K) break;
+      const int nrun = __syncthreads_count(b == cb);
+      if (cb < K) {
+        const float4 *src = reinterpret_cast<const float4 *>(P.table + (int64_t)cb * TF);
+        for (int j = threadIdx.x; j < TF / 4; j += T) smem4[j] = __ldg(src + j);
+        if (threadIdx.x < 2 * kNmet)
+          ab_s[threadIdx.x] = threadIdx.x < kNmet ? __ldg(P.aN + (int64_t)cb * kNmet + threadIdx.x)
+                                                  : __ldg(P.bN + (int64_t)cb * kNmet + threadIdx.x - kNmet);
+        if (threadIdx.x == 0) grid_s = __ldg(P.grid + cb);
+        __syncthreads();
+      }
+      if (b == cb) {
+        int arg, st;
+        float b1, b2;
+        eval_query<D1, true>(q0, q1, cb < K, ab_s, ab_s + kNmet, grid_s, tab_s, cfg, hw, arg, b1,
+                             b2, st);
+        argmin[qi] = arg;
+        best[qi] = b1;
+        second[qi] = b2;
+        status[qi] = st;
+      }
+      __syncthreads();   // the next run restages the table
+      pos += nrun;
+    }
+    __syncthreads();     // bk_s is rewritten by the next tile
   }
 }
 
@@ -351,9 +560,59 @@ cudaError_t launch_pack(int64_t K, int d, const double *coef, const double *box,
   return cudaGetLastError();
 }
 
+// Workspace of the grouped search: offsets int32[K+2], cursors int32[K+1],
+// the bucketed query indices int32[Q], each section 16-byte aligned.  0 (no
+// grouping) for fewer than kGroupMinPerKernel queries per kernel on average
+// (a tile would then stage a table for only a few queries) or sizes that
+// int32 positions cannot index.
+constexpr int64_t kGroupMinPerKernel = 32;
+size_t search_workspace_bytes(int64_t K, int64_t Q) {
+  if (Q <= 0 || K < 1 || Q >= ((int64_t)1 << 31) - 1 || K >= ((int64_t)1 << 30) ||
+      Q < kGroupMinPerKernel * K)
+    return 0;
+  return align16((size_t)(K + 2) * 4) + align16((size_t)(K + 1) * 4) + align16((size_t)Q * 4);
+}
+
+template <int D1>
+static cudaError_t launch_d(ProgramView prog, int64_t K, const CfgTab &cfg, const HwC &h,
+                            const float *queries, int64_t Q, int32_t *argmin, float *best,
+                            float *second, int32_t *status, void *ws, cudaStream_t s) {
+  const SearchShape shape = search_shape(D1 - 1);
+  const int threads = shape.threads;
+  const float4 *q4 = reinterpret_cast<const float4 *>(queries);
+  int64_t blocks = (Q + threads - 1) / threads;
+  const int64_t cap = (int64_t)num_sms() * shape.ctas_per_sm;
+  if (blocks > cap) blocks = cap;
+  if (!ws) {
+    search_kernel<D1><<<(unsigned)blocks, threads, 0, s>>>(prog, K, cfg, h, q4, Q, argmin, best,
+                                                           second, status);
+    return cudaGetLastError();
+  }
+  unsigned char *w = static_cast<unsigned char *>(ws);
+  int32_t *off = reinterpret_cast<int32_t *>(w);
+  int32_t *cur = reinterpret_cast<int32_t *>(w + align16((size_t)(K + 2) * 4));
+  int32_t *perm = reinterpret_cast<int32_t *>(w + align16((size_t)(K + 2) * 4) +
+                                              align16((size_t)(K + 1) * 4));
+  cudaError_t e = cudaMemsetAsync(off, 0, (size_t)(K + 1) * 4, s);
+  if (e != cudaSuccess) return e;
+  const int bt = 512;
+  int64_t bb = (Q + bt - 1) / bt;
+  if (bb > (int64_t)num_sms() * 4) bb = (int64_t)num_sms() * 4;
+  const size_t hist = K + 1 <= kBucketSmem ? (size_t)(K + 1) * 4 : 0;
+  bucket_count_kernel<<<(unsigned)bb, bt, hist, s>>>(queries, Q, K, off);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  bucket_scan_kernel<<<1, 1024, 0, s>>>(off, cur, (int)(K + 1));
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  bucket_scatter_kernel<<<(unsigned)bb, bt, 0, s>>>(queries, Q, K, cur, perm);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  search_grouped_kernel<D1><<<(unsigned)blocks, threads, grouped_smem<D1>(threads), s>>>(
+      prog, K, cfg, h, q4, Q, perm, argmin, best, second, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_search(ProgramView prog, int64_t K, int d, const rp_hw_fixed &hw,
                           const float *queries, int64_t Q, int32_t *argmin, float *best,
-                          float *second, int32_t *status, cudaStream_t s) {
+                          float *second, int32_t *status, void *workspace, cudaStream_t s) {
   if (Q == 0) return cudaSuccess;
   CfgTab cfg{};
   int c = 0;
@@ -366,23 +625,20 @@ cudaError_t launch_search(ProgramView prog, int64_t K, int d, const rp_hw_fixed 
       cfg.wpb[c] = wpb;
       int bw = hw.b_max < hw.w_max / wpb ? hw.b_max : hw.w_max / wpb;
       cfg.bact_w[c] = (T > hw.t_max) ? 0 : bw;
+      const int64_t wpbw = (int64_t)wpb * hw.warp_size;
+      cfg.rsm_w[c] = (int32_t)(hw.r_sm / wpbw);
+      cfg.rsm_t[c] = hw.r_sm / T;
     }
   HwC h{hw.warp_size, hw.w_max, hw.r_sm, hw.z_sm, hw.issue_cycles};
-  const SearchShape shape = search_shape(d);
-  const int threads = shape.threads;
-  int64_t blocks = (Q + threads - 1) / threads;
-  const int64_t cap = (int64_t)num_sms() * shape.ctas_per_sm;
-  if (blocks > cap) blocks = cap;
-  const float4 *q4 = reinterpret_cast<const float4 *>(queries);
+  void *ws = search_workspace_bytes(K, Q) > 0 ? workspace : nullptr;
   switch (d + 1) {
-    case 1: search_kernel<1><<<(unsigned)blocks, threads, 0, s>>>(prog, K, cfg, h, q4, Q, argmin, best, second, status); break;
-    case 2: search_kernel<2><<<(unsigned)blocks, threads, 0, s>>>(prog, K, cfg, h, q4, Q, argmin, best, second, status); break;
-    case 3: search_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(prog, K, cfg, h, q4, Q, argmin, best, second, status); break;
-    case 4: search_kernel<4><<<(unsigned)blocks, threads, 0, s>>>(prog, K, cfg, h, q4, Q, argmin, best, second, status); break;
-    case 5: search_kernel<5><<<(unsigned)blocks, threads, 0, s>>>(prog, K, cfg, h, q4, Q, argmin, best, second, status); break;
+    case 1: return launch_d<1>(prog, K, cfg, h, queries, Q, argmin, best, second, status, ws, s);
+    case 2: return launch_d<2>(prog, K, cfg, h, queries, Q, argmin, best, second, status, ws, s);
+    case 3: return launch_d<3>(prog, K, cfg, h, queries, Q, argmin, best, second, status, ws, s);
+    case 4: return launch_d<4>(prog, K, cfg, h, queries, Q, argmin, best, second, status, ws, s);
+    case 5: return launch_d<5>(prog, K, cfg, h, queries, Q, argmin, best, second, status, ws, s);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 }  // namespace rpk

@@ -33,7 +33,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_version_and_strerror(lib):
-    assert rp.rp_version() == 1
+    assert rp.rp_version() == 2
     assert rp.rp_strerror(0) == "ok"
     assert rp.rp_strerror(-1) == "invalid argument"
     assert rp.rp_strerror(-999) == "unknown error"
@@ -60,9 +60,12 @@ def test_argument_validation_without_launch(lib):
     assert lib.rp_fit_workspace_size(C.byref(d), C.byref(ws)) == 0 and ws.value == 0
     hw = rp.hw_struct()
     hw_bad = rp.hw_struct(dict(issue_cycles=0.0))
-    assert lib.rp_eval_search(None, 4, 3, C.byref(hw_bad), None, 10, None, None, None, None, None) == -1
-    assert lib.rp_eval_search(None, 4, 3, C.byref(hw), None, 10, None, None, None, None, None) == -1
-    assert lib.rp_eval_search(None, 4, 3, C.byref(hw), None, 0, None, None, None, None, None) == 0
+    assert lib.rp_eval_search(None, 4, 3, C.byref(hw_bad), None, 10, None, None, None, None, None,
+                              0, None) == -1
+    assert lib.rp_eval_search(None, 4, 3, C.byref(hw), None, 10, None, None, None, None, None,
+                              0, None) == -1
+    assert lib.rp_eval_search(None, 4, 3, C.byref(hw), None, 0, None, None, None, None, None,
+                              0, None) == 0
     assert lib.rp_program_pack(4, 0, None, None, None, None, None, None, 0, None) == -1
     assert lib.rp_adam_step(10, None, None, None, None, None, 0, 1e-3, 0.9, 0.999, 1e-8, None) == -1
     assert lib.rp_relmse_fwd(-1, 0, None, None, None, None, None, None, None, None) == -1
@@ -79,7 +82,32 @@ def test_tuning_argument_validation_without_launch(lib):
     h = rp.hw_struct()
     t = C.c_int32(0)
     assert lib.rp_tune_search(None, 1, 3, C.byref(h), None, 10, None, None, None, None, None,
-                              C.byref(t), None) == -1
+                              0, None, C.byref(t), None) == -1
     ws = C.c_size_t(0)
     d = rp.FitDesc(5, 100, 3, 1, 4, 0, 1e-12, None)
     assert lib.rp_fit_workspace_size(C.byref(d), C.byref(ws)) == 0 and ws.value == 16
+
+
+def test_search_workspace_size(lib):
+    """Closed form of rp_search_workspace_size: offsets int32[K+2], cursors
+    int32[K+1], bucketed indices int32[Q], each rounded up to 16 bytes; 0
+    below 32 queries per kernel and outside int32 positions."""
+    a16 = lambda v: (v + 15) & ~15
+    for K, Q in [(1, 32), (8, 5000), (1024, 1_000_000), (1024, 10_000_000), (3, 97)]:
+        assert rp.rp_search_workspace_size(K, Q) == a16(4 * (K + 2)) + a16(4 * (K + 1)) + a16(4 * Q)
+    for K, Q in [(1024, 3000), (1, 31), (0, 100), (5, 0), (1, 2**31 - 1)]:
+        assert rp.rp_search_workspace_size(K, Q) == 0
+    b = C.c_size_t(7)
+    assert lib.rp_search_workspace_size(-1, 10, C.byref(b)) == -1
+    assert lib.rp_search_workspace_size(1, 10, None) == -1
+
+
+def test_search_workspace_checked_before_launch(lib):
+    """A workspace that is too small or misaligned is rejected before any
+    device work (the other pointers are never dereferenced)."""
+    hw = rp.hw_struct()
+    fake = C.c_void_p(1 << 20)      # 16-byte aligned, never dereferenced
+    need = rp.rp_search_workspace_size(8, 5000)
+    args = (fake, 8, 3, C.byref(hw), fake, 5000, fake, fake, fake, fake)
+    assert lib.rp_eval_search(*args, fake, need - 16, None) == -3
+    assert lib.rp_eval_search(*args, C.c_void_p((1 << 20) + 4), need, None) == -5

@@ -108,7 +108,9 @@ def test_uneven_batch_graph_captured(precision):
     s_out = dict(argmin=torch.empty(Q, dtype=torch.int32, device="cuda"),
                  best=torch.empty(Q, dtype=torch.float32, device="cuda"),
                  second=torch.empty(Q, dtype=torch.float32, device="cuda"),
-                 status=torch.empty(Q, dtype=torch.int32, device="cuda"))
+                 status=torch.empty(Q, dtype=torch.int32, device="cuda"),
+                 workspace=torch.empty(rp.rp_search_workspace_size(K, Q), dtype=torch.uint8,
+                                       device="cuda"))
 
     def step(stream):
         rp.rp_fit(x, y, off, 4, precision=precision, degrees=deg, out=fit_out, stream=stream,
@@ -121,7 +123,8 @@ def test_uneven_batch_graph_captured(precision):
     with torch.cuda.stream(s):
         step(s)                       # eager (also the first-call set-up)
     torch.cuda.synchronize()
-    outs = {**{"fit_" + k: v for k, v in fit_out.items()}, **{"search_" + k: v for k, v in s_out.items()}}
+    outs = {**{"fit_" + k: v for k, v in fit_out.items()},
+            **{"search_" + k: v for k, v in s_out.items() if k != "workspace"}}
     eager = {k: v.clone() for k, v in outs.items()}
     for v in outs.values():
         v.zero_()

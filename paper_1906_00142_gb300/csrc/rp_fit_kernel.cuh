@@ -235,7 +235,10 @@ struct CtaFit {
   float uvhi[2][NM], uvlo[2][NM];     // FP32 path: (c, u), (c, v) as head + tail
   float uvphi[2][NM], uvplo[2][NM];   // previous
   float redv[4][((2 * NM + 2 + 15) / 16) * 16];
-  float xs[4][kMC];                   // sample cache (N, B0, B1, y)
+  // sample cache (N, B0, B1, y) of fits with at most MC samples; none on the
+  // FP32 degree-4 path, whose shared memory then admits 3 CTAs per SM
+  static constexpr int MC = (sizeof(Real) == 4 && DMAX == 4 && GM == 0) ? 0 : kMC;
+  float xs[4][MC > 0 ? MC : 1];
   float redf[4][32];
   unsigned dslot[3][kMaxDeg + 1];
   uint32_t tmem_base;
@@ -609,7 +612,8 @@ __device__ __forceinline__ bool tc_chunk(const unsigned char *st, uint32_t tmem,
 // The fit kernel.  Real = double: plain FP64 path; Real = float: FP32 path.
 
 template <class Real, int DMAX, int GM>
-__global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 2 ? 3 : 4) : (DMAX <= 3 ? 2 : 1))
+__global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 2 ? 3 : 4)
+                                          : (DMAX <= 3 ? 2 : (sizeof(Real) == 4 && GM == 0 ? 3 : 1)))
     fit_kernel(FitArgs a) {
   using WF = CtaFit<Real, DMAX, GM>;
   using TS = TcShape<DMAX>;
@@ -677,7 +681,7 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
     const int nc = nm - 1;
     const int naug = 2 * nm;
     const int n = naug - 1;
-    const bool cached = m <= kMC;
+    const bool cached = m <= WF::MC;
     const float *gx0 = a.x + b0, *gx1 = a.x + a.S + b0, *gx2 = a.x + 2 * a.S + b0, *gy = a.y + b0;
     if (tid < 3 * (kMaxDeg + 1)) (&w.dslot[0][0])[tid] = kEmpty;
     if (tid == 0) w.bad = 0;

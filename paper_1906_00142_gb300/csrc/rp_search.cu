@@ -14,42 +14,57 @@
 namespace rpk {
 namespace {
 
-// Graded-lex exponents, degree ascending, e_N descending, e_B0 descending.
-struct ExpTab {
-  int8_t e[kMaxNm][3];
-};
-
-ExpTab make_exponents() {
-  ExpTab t{};
-  int k = 0;
-  for (int s = 0; s <= kMaxDeg; ++s)
-    for (int a = s; a >= 0; --a)
-      for (int b = s - a; b >= 0; --b) {
-        t.e[k][0] = (int8_t)a;
-        t.e[k][1] = (int8_t)b;
-        t.e[k][2] = (int8_t)(s - a - b);
-        ++k;
-      }
-  return t;
+// Index of the monomial N^a B0^b B1^c in the graded-lex order of the fit's
+// coefficients (degree ascending, then exponent of N descending, then of B0
+// descending): the C(s+2, 3) monomials of lower degree s = a + b + c, then
+// (b + c)(b + c + 1) / 2 monomials of degree s with a larger exponent of N,
+// then c.
+__host__ __device__ constexpr int glex_index(int a, int b, int c) {
+  return (a + b + c) * (a + b + c + 1) * (a + b + c + 2) / 6 + (b + c) * (b + c + 1) / 2 + c;
 }
 
-// One thread per (kernel, configuration, metric).  FP64 arithmetic.
-__global__ void pack_kernel(int64_t K, int d, const double *__restrict__ coef,
+// out[a] = sum over b + c <= D - a of cf[glex(a, b, c)] u^b w^c: the
+// coefficient of t^a once B0 and B1 are fixed, by nested Horner in u and w
+// (one FMA per monomial); only the fit's own nm monomials are read.
+template <int D>
+__device__ __forceinline__ void fold_b(const double *__restrict__ cf, int nm, double u, double w,
+                                       double (&out)[D + 1]) {
+#pragma unroll
+  for (int a = 0; a <= D; ++a) {
+    double acc = 0.0;
+#pragma unroll
+    for (int b = D - a; b >= 0; --b) {
+      double inner = 0.0;
+#pragma unroll
+      for (int c = D - a - b; c >= 0; --c) {
+        const int j = glex_index(a, b, c);
+        inner = fma(inner, w, j < nm ? __ldg(cf + j) : 0.0);
+      }
+      acc = fma(acc, u, inner);
+    }
+    out[a] = acc;
+  }
+}
+
+// One thread per (kernel, configuration, metric).  FP64 arithmetic.  D: the
+// program's degree bound.
+template <int D>
+__global__ void pack_kernel(int64_t K, const double *__restrict__ coef,
                             const double *__restrict__ box, const int8_t *__restrict__ degrees,
                             const int32_t *__restrict__ metric_map,
-                            const int32_t *__restrict__ grid_dims, ProgramMut prog, ExpTab et) {
+                            const int32_t *__restrict__ grid_dims, ProgramMut prog) {
+  constexpr int D1 = D + 1;
   const int64_t total = K * kNcfg * kNmet;
-  const int D1 = d + 1;
   for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
        id += (int64_t)gridDim.x * blockDim.x) {
     const int mt = (int)(id % kNmet);
     const int c = (int)((id / kNmet) % kNcfg);
     const int64_t k = id / (kNmet * kNcfg);
     const int fi = metric_map[k * kNmet + mt];
-    double pn[kMaxDeg + 1], pd[kMaxDeg + 1];
-#pragma unroll
-    for (int i = 0; i <= kMaxDeg; ++i) pn[i] = pd[i] = 0.0;
+    double pn[D1], pd[D1];
     if (fi < 0) {
+#pragma unroll
+      for (int i = 0; i < D1; ++i) pn[i] = pd[i] = 0.0;
       pd[0] = 1.0;
     } else {
       // configuration index -> (a, b) with B0 = 2^a, B1 = 2^b
@@ -59,24 +74,13 @@ __global__ void pack_kernel(int64_t K, int d, const double *__restrict__ coef,
       const double *bx = box + 6 * (int64_t)fi;
       const double u = (bx[3] > bx[2]) ? 2.0 * (B0 - bx[2]) / (bx[3] - bx[2]) - 1.0 : 0.0;
       const double w = (bx[5] > bx[4]) ? 2.0 * (B1 - bx[4]) / (bx[5] - bx[4]) - 1.0 : 0.0;
-      double up[kMaxDeg + 1], wp[kMaxDeg + 1];
-      up[0] = wp[0] = 1.0;
-#pragma unroll
-      for (int i = 1; i <= kMaxDeg; ++i) {
-        up[i] = up[i - 1] * u;
-        wp[i] = wp[i - 1] * w;
-      }
-      const int df = degrees[fi];
-      const int nm = num_monomials(df);
       const double *cf = coef + (int64_t)fi * kStride;
-      for (int j = 0; j < nm; ++j) {
-        const double sB = up[et.e[j][1]] * wp[et.e[j][2]];
-        const int e0 = et.e[j][0];
-        pn[e0] += cf[j] * sB;
-        pd[e0] += cf[kHalf + j] * sB;
-      }
+      const int nm = num_monomials(degrees[fi]);
+      fold_b<D>(cf, nm, u, w, pn);
+      fold_b<D>(cf + kHalf, nm, u, w, pd);
     }
     float *row = prog.table + ((k * kNcfg + c) * kNmet + mt) * 2 * D1;
+#pragma unroll
     for (int i = 0; i < D1; ++i) {
       row[i] = (float)pn[i];
       row[D1 + i] = (float)pd[i];
@@ -548,15 +552,19 @@ void set_fit_ctas_cap(int precision, int dmax, int cap) {
 cudaError_t launch_pack(int64_t K, int d, const double *coef, const double *box,
                         const int8_t *degrees, const int32_t *metric_map, const int32_t *grid_dims,
                         ProgramMut prog, cudaStream_t s) {
-  static const ExpTab et = make_exponents();
   const int64_t total = K * kNcfg * kNmet;
   if (total == 0) return cudaSuccess;
   const int threads = 128;
   int64_t blocks = (total + threads - 1) / threads;
   const int64_t cap = (int64_t)num_sms() * 16;
   if (blocks > cap) blocks = cap;
-  pack_kernel<<<(unsigned)blocks, threads, 0, s>>>(K, d, coef, box, degrees, metric_map,
-                                                   grid_dims, prog, et);
+  switch (d) {
+    case 1: pack_kernel<1><<<(unsigned)blocks, threads, 0, s>>>(K, coef, box, degrees, metric_map, grid_dims, prog); break;
+    case 2: pack_kernel<2><<<(unsigned)blocks, threads, 0, s>>>(K, coef, box, degrees, metric_map, grid_dims, prog); break;
+    case 3: pack_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(K, coef, box, degrees, metric_map, grid_dims, prog); break;
+    case 4: pack_kernel<4><<<(unsigned)blocks, threads, 0, s>>>(K, coef, box, degrees, metric_map, grid_dims, prog); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

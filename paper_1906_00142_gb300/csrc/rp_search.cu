@@ -46,46 +46,71 @@ __device__ __forceinline__ void fold_b(const double *__restrict__ cf, int nm, do
   }
 }
 
-// One thread per (kernel, configuration, metric).  FP64 arithmetic.  D: the
+// One thread per (kernel, metric, run of kPackRun consecutive
+// configurations): the fit's normalisation of B0 and B1 (two FP64 divisions)
+// is set up once for the run; per configuration the normalised B0, B1 cost
+// one FMA each and the fold one FMA per monomial.  FP64 arithmetic.  D: the
 // program's degree bound.
+constexpr int kPackRun = 11;   // 66 configurations = 6 runs
 template <int D>
 __global__ void pack_kernel(int64_t K, const double *__restrict__ coef,
                             const double *__restrict__ box, const int8_t *__restrict__ degrees,
                             const int32_t *__restrict__ metric_map,
                             const int32_t *__restrict__ grid_dims, ProgramMut prog) {
   constexpr int D1 = D + 1;
-  const int64_t total = K * kNcfg * kNmet;
+  constexpr int kRuns = kNcfg / kPackRun;
+  const int64_t total = K * kRuns * kNmet;
   for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
        id += (int64_t)gridDim.x * blockDim.x) {
     const int mt = (int)(id % kNmet);
-    const int c = (int)((id / kNmet) % kNcfg);
-    const int64_t k = id / (kNmet * kNcfg);
+    const int run = (int)((id / kNmet) % kRuns);
+    const int64_t k = id / (kNmet * kRuns);
     const int fi = metric_map[k * kNmet + mt];
-    double pn[D1], pd[D1];
-    if (fi < 0) {
-#pragma unroll
-      for (int i = 0; i < D1; ++i) pn[i] = pd[i] = 0.0;
-      pd[0] = 1.0;
-    } else {
-      // configuration index -> (a, b) with B0 = 2^a, B1 = 2^b
-      int a = 0, rem = c;
-      while (rem >= 11 - a) { rem -= 11 - a; ++a; }
-      const double B0 = (double)(1 << a), B1 = (double)(1 << rem);
+    // x' = x s + o maps the fit's [lo, hi] to [-1, 1] (0 for a constant variable)
+    double s0 = 0.0, o0 = 0.0, s1 = 0.0, o1 = 0.0;
+    const double *cf = coef;
+    int nm = 0;
+    if (fi >= 0) {
       const double *bx = box + 6 * (int64_t)fi;
-      const double u = (bx[3] > bx[2]) ? 2.0 * (B0 - bx[2]) / (bx[3] - bx[2]) - 1.0 : 0.0;
-      const double w = (bx[5] > bx[4]) ? 2.0 * (B1 - bx[4]) / (bx[5] - bx[4]) - 1.0 : 0.0;
-      const double *cf = coef + (int64_t)fi * kStride;
-      const int nm = num_monomials(degrees[fi]);
-      fold_b<D>(cf, nm, u, w, pn);
-      fold_b<D>(cf + kHalf, nm, u, w, pd);
+      if (bx[3] > bx[2]) {
+        s0 = 2.0 / (bx[3] - bx[2]);
+        o0 = -1.0 - bx[2] * s0;
+      }
+      if (bx[5] > bx[4]) {
+        s1 = 2.0 / (bx[5] - bx[4]);
+        o1 = -1.0 - bx[4] * s1;
+      }
+      cf = coef + (int64_t)fi * kStride;
+      nm = num_monomials(degrees[fi]);
     }
-    float *row = prog.table + ((k * kNcfg + c) * kNmet + mt) * 2 * D1;
+    // first configuration of the run -> (a, b) with B0 = 2^a, B1 = 2^b
+    int a = 0, b = run * kPackRun;
+    while (b >= 11 - a) { b -= 11 - a; ++a; }
+    for (int r = 0; r < kPackRun; ++r) {
+      const int c = run * kPackRun + r;
+      double pn[D1], pd[D1];
+      if (fi < 0) {
 #pragma unroll
-    for (int i = 0; i < D1; ++i) {
-      row[i] = (float)pn[i];
-      row[D1 + i] = (float)pd[i];
+        for (int i = 0; i < D1; ++i) pn[i] = pd[i] = 0.0;
+        pd[0] = 1.0;
+      } else {
+        const double u = fma((double)(1 << a), s0, o0);
+        const double w = fma((double)(1 << b), s1, o1);
+        fold_b<D>(cf, nm, u, w, pn);
+        fold_b<D>(cf + kHalf, nm, u, w, pd);
+      }
+      float *row = prog.table + ((k * kNcfg + c) * kNmet + mt) * 2 * D1;
+#pragma unroll
+      for (int i = 0; i < D1; ++i) {
+        row[i] = (float)pn[i];
+        row[D1 + i] = (float)pd[i];
+      }
+      if (++b > 10 - a) {   // next configuration: b ascending, then a
+        b = 0;
+        ++a;
+      }
     }
-    if (c == 0) {
+    if (run == 0) {
       double A = 0.0, Bc = 0.0;
       if (fi >= 0) {
         const double *bx = box + 6 * (int64_t)fi;
@@ -141,11 +166,6 @@ __device__ __forceinline__ int floor_div_small(int a, int b) {
   q -= (q * b > a);
   q += ((q + 1) * b <= a);
   return q;
-}
-
-// ceil(n / 2^s) without overflow
-__device__ __forceinline__ uint32_t ceil_shift(uint32_t n, int s) {
-  return (n >> s) + ((n & ((1u << s) - 1u)) != 0u);
 }
 
 // x / y with y >= 0; +inf where y == 0
@@ -263,8 +283,9 @@ __device__ __forceinline__ void eval_query(const float4 q0, const float4 q1, boo
       const bool valid = !pole && bact > 0 && Ri <= cfg.rsm_t[c] && Zi <= hw.zsm;
       bact = max(bact, 1);
       const float Nw = (float)min(bact * wpb, hw.wmax);
-      const uint32_t c0 = grid1 ? ceil_shift(Ni, la + lb) : ceil_shift(Ni, la);
-      const uint32_t c1 = grid1 ? 1u : ceil_shift(Ni, lb);
+      // ceil(N / 2^s) = ((N - 1) >> s) + 1 for N >= 1
+      const uint32_t c0 = ((Ni - 1u) >> (grid1 ? la + lb : la)) + 1u;
+      const uint32_t c1 = grid1 ? 1u : ((Ni - 1u) >> lb) + 1u;
       // fewer blocks than SMs (decided exactly in FP32: below 2^24 the
       // product is exact, above it is >= 2^24 > SMs): every block runs in
       // one round, #Rep = 1
@@ -552,7 +573,8 @@ void set_fit_ctas_cap(int precision, int dmax, int cap) {
 cudaError_t launch_pack(int64_t K, int d, const double *coef, const double *box,
                         const int8_t *degrees, const int32_t *metric_map, const int32_t *grid_dims,
                         ProgramMut prog, cudaStream_t s) {
-  const int64_t total = K * kNcfg * kNmet;
+  static_assert(kNcfg % kPackRun == 0, "whole runs of configurations");
+  const int64_t total = K * (kNcfg / kPackRun) * kNmet;
   if (total == 0) return cudaSuccess;
   const int threads = 128;
   int64_t blocks = (total + threads - 1) / threads;

@@ -234,11 +234,14 @@ struct CtaFit {
   Real mu_v[3], isg_v[3], sc_v[3], of_v[3];
   float uvhi[2][NM], uvlo[2][NM];     // FP32 path: (c, u), (c, v) as head + tail
   float uvphi[2][NM], uvplo[2][NM];   // previous
+  float fzhi[2][NM], fzlo[2][NM];     // FP32 path: the iterate whose residuals efz holds
+  float dfz[2][NM];                   // the iterate minus that one
   float redv[4][((2 * NM + 2 + 15) / 16) * 16];
   // sample cache (N, B0, B1, y) of fits with at most MC samples; none on the
   // FP32 degree-4 path, whose shared memory then admits 3 CTAs per SM
   static constexpr int MC = (sizeof(Real) == 4 && DMAX == 4 && GM == 0) ? 0 : kMC;
   float xs[4][MC > 0 ? MC : 1];
+  float efz[MC > 0 ? MC : 1];         // compensated residuals y q - p at fzhi + fzlo
   float redf[4][32];
   unsigned dslot[3][kMaxDeg + 1];
   uint32_t tmem_base;
@@ -1101,6 +1104,12 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
     flags = (w.keep_cnt < n) ? RP_FIT_RANK_DEFICIENT : 0;
     float prev_rel = INFINITY, obj_prev = INFINITY, obj_drop = INFINITY;
     bool compensated = sizeof(Real) == 8, done = false;
+    // FP32 paths, cached samples: the first compensated pass keeps each
+    // sample's Dot2 residual e_f = y q_f - p_f at that pass's iterate x_f;
+    // later passes take e(x) = e_f + (y psi.dv - psi.du) with (du, dv) =
+    // x - x_f, small enough for plain FP32 (one Dot2 pass per fit)
+    const bool can_freeze = sizeof(Real) == 4 && cached;
+    bool frozen = false;
     int pole_prev = 0, it = 0;
     float omega = 1.0f;   // step length (halved after an objective increase)
     constexpr bool kRegAcc = sizeof(Real) == 4 && DMAX <= 3;
@@ -1108,6 +1117,21 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
     const int hk_groups = max(1, kT / nm);
     for (;; ++it) {
       const bool update = it < a.max_refine && !done;
+      const bool freezing = can_freeze && compensated && !frozen;
+      if (freezing) {
+        for (int e = tid; e < 2 * NM; e += kT) {
+          const int which = e / NM, i2 = e % NM;
+          w.fzhi[which][i2] = w.uvhi[which][i2];
+          w.fzlo[which][i2] = w.uvlo[which][i2];
+        }
+      } else if (frozen) {
+        for (int e = tid; e < 2 * NM; e += kT) {
+          const int which = e / NM, i2 = e % NM;
+          w.dfz[which][i2] = (w.uvhi[which][i2] - w.fzhi[which][i2]) +
+                             (w.uvlo[which][i2] - w.fzlo[which][i2]);
+        }
+        __syncthreads();
+      }
       Real hk0 = 0, hk1 = 0;    // staged path: this thread's column partials
       float obj = 0.0f;
       int pole = 0;
@@ -1138,7 +1162,15 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
 #pragma unroll
             for (int j2 = 1; j2 < NM; ++j2) qf = fmaf(psi[j2], w.uvhi[1][j2], qf);
             pole |= !(qf > 0.0f);
-            if (compensated) {
+            if (frozen) {
+              float dq = w.dfz[1][0], dp = w.dfz[0][0];
+#pragma unroll
+              for (int j2 = 1; j2 < NM; ++j2) {
+                dq = fmaf(psi[j2], w.dfz[1][j2], dq);
+                dp = fmaf(psi[j2], w.dfz[0][j2], dp);
+              }
+              r = wt * (w.efz[i] + fmaf(yy, dq, -dp));
+            } else if (compensated) {
               // e = y q - p = sum_j (y psi_j) v_j - psi_j u_j (psi_0 = 1):
               // Dot2 against the head + tail iterate, two independent chains
               float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
@@ -1158,7 +1190,9 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
               }
               float t, e;
               two_sum(s0, s1, t, e);
-              r = wt * (t + (e + c0 + c1));
+              const float ef = t + (e + c0 + c1);
+              if (freezing) w.efz[i] = ef;
+              r = wt * ef;
             } else {
               float p = w.uvhi[0][0];
 #pragma unroll
@@ -1221,6 +1255,7 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
         obj = block_sum_f(w, obj, 8);
       }
       __syncthreads();
+      if (freezing) frozen = true;
       const bool worse = it > 0 && obj > obj_prev * (compensated ? 1.00001f : 1.0001f);
       if (worse) {
         // the last step increased the objective: undo it, then retry it at

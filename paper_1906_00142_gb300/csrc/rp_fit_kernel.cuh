@@ -293,9 +293,16 @@ __device__ __forceinline__ void eval_psi(const S &w, int d, int nm, float x0, fl
       Q[v][k] = (k <= d) ? s : (Real)0;
     }
   }
+  // graded-lex order (degree s ascending, exponent a of N descending, b of
+  // B0 descending) with compile-time exponents: Q stays in registers
+  int j = 0;
 #pragma unroll
-  for (int j = 0; j < NM; ++j)
-    psi[j] = (j < nm) ? Q[0][c_exp[j][0]] * Q[1][c_exp[j][1]] * Q[2][c_exp[j][2]] : (Real)0;
+  for (int s = 0; s <= DMAX; ++s)
+#pragma unroll
+    for (int a = s; a >= 0; --a)
+#pragma unroll
+      for (int b = s - a; b >= 0; --b, ++j)
+        psi[j] = (j < nm) ? Q[0][a] * Q[1][b] * Q[2][s - a - b] : (Real)0;
 }
 
 // Whitened basis: pt[0] = 1, pt[j] = sum_{1<=i<=j} (Psi_i - mean_i) W[i][j].
@@ -1460,8 +1467,10 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
 // ---------------------------------------------------------------------
 
 void set_tables() {
-  static bool done = false;
-  if (done) return;
+  static bool done[16] = {};   // per device (constant memory is per context)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) dev = 0;
+  if (done[dev]) return;
   int8_t e[kMaxNm][3];
   int k = 0;
   for (int s = 0; s <= kMaxDeg; ++s)
@@ -1479,7 +1488,7 @@ void set_tables() {
       for (int l = 0; l <= kMaxDeg; ++l) idx[i][j][l] = -1;
   for (int t = 0; t < kMaxNm; ++t) idx[e[t][0]][e[t][1]][e[t][2]] = (int8_t)t;
   cudaMemcpyToSymbol(c_idx, idx, sizeof(idx));
-  done = true;
+  done[dev] = true;
 }
 
 // Resident CTAs per SM of one fit-kernel variant: registers, shared memory,

@@ -230,12 +230,15 @@ struct CtaFit {
   Real duv[2][NM];                    // step of (c, u), (c, v)
   Real HK[2][NM];
   Real rbuf[2][kT];
-  Real Tm[3][kMaxDeg + 1][kMaxDeg + 1];  // Q_k(u) = sum_l Tm[l][k] u^l
+  // Q_k(u) = sum_l Tm[l][k] u^l (rows padded to 8: 128-bit loads of k = 0..3)
+  alignas(16) Real Tm[3][kMaxDeg + 1][8];
   Real mu_v[3], isg_v[3], sc_v[3], of_v[3];
-  float uvhi[2][NM], uvlo[2][NM];     // FP32 path: (c, u), (c, v) as head + tail
+  alignas(16) Real vc[3][4];          // per variable: sc, of, mu, isg
+  alignas(16) float uvhi[2][NM];      // FP32 path: (c, u), (c, v) as head + tail
+  alignas(16) float uvlo[2][NM];
   float uvphi[2][NM], uvplo[2][NM];   // previous
   float fzhi[2][NM], fzlo[2][NM];     // FP32 path: the iterate whose residuals efz holds
-  float dfz[2][NM];                   // the iterate minus that one
+  alignas(16) float dfz[2][NM];       // the iterate minus that one
   float redv[4][((2 * NM + 2 + 15) / 16) * 16];
   // sample cache (N, B0, B1, y) of fits with at most MC samples; none on the
   // FP32 degree-4 path, whose shared memory then admits 3 CTAs per SM
@@ -271,6 +274,30 @@ __device__ __forceinline__ float block_sum_f(S &w, float v, int slot) {
   return r;
 }
 
+// Shared-memory row of N floats into registers: 128-bit loads where the
+// rows are 16-byte aligned (N a multiple of 4; the arrays are 16-byte
+// aligned), else 32-bit loads.
+template <int N>
+__device__ __forceinline__ void ld_row(const float *src, float (&dst)[N]) {
+  if constexpr (N % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < N / 4; ++q) {
+      const float4 v = reinterpret_cast<const float4 *>(src)[q];
+      dst[4 * q] = v.x;
+      dst[4 * q + 1] = v.y;
+      dst[4 * q + 2] = v.z;
+      dst[4 * q + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < N; ++j) dst[j] = src[j];
+  }
+}
+
+// 1 / x, correctly rounded (the same value as the IEEE division)
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
 // Unwhitened basis Psi at one sample (compile-time bound NM, runtime nm).
 template <class Real, int DMAX, int NM, class S>
 __device__ __forceinline__ void eval_psi(const S &w, int d, int nm, float x0, float x1, float x2,
@@ -279,19 +306,36 @@ __device__ __forceinline__ void eval_psi(const S &w, int d, int nm, float x0, fl
   const float xv[3] = {x0, x1, x2};
 #pragma unroll
   for (int v = 0; v < 3; ++v) {
-    const Real xn = fma((Real)xv[v], w.sc_v[v], w.of_v[v]);
-    const Real u = (xn - w.mu_v[v]) * w.isg_v[v];
     Real pw[kMaxDeg + 1];
+    if constexpr (sizeof(Real) == 4) {
+      const float4 c = *reinterpret_cast<const float4 *>(&w.vc[v][0]);   // sc, of, mu, isg
+      const float xn = fmaf(xv[v], c.x, c.y);
+      pw[1] = (xn - c.z) * c.w;
+    } else {
+      const Real xn = fma((Real)xv[v], w.sc_v[v], w.of_v[v]);
+      pw[1] = (xn - w.mu_v[v]) * w.isg_v[v];
+    }
     pw[0] = 1;
 #pragma unroll
-    for (int l = 1; l <= DMAX; ++l) pw[l] = pw[l - 1] * u;
+    for (int l = 2; l <= DMAX; ++l) pw[l] = pw[l - 1] * pw[1];
+    // Q_k = sum_{l <= k} Tm[l][k] u^l, summed over l ascending
+    Real s[kMaxDeg + 1];
 #pragma unroll
-    for (int k = 0; k <= DMAX; ++k) {
-      Real s = 0;
+    for (int k = 0; k <= DMAX; ++k) s[k] = 0;
 #pragma unroll
-      for (int l = 0; l <= k; ++l) s = fma(w.Tm[v][l][k], pw[l], s);
-      Q[v][k] = (k <= d) ? s : (Real)0;
+    for (int l = 0; l <= DMAX; ++l) {
+      Real t[8];
+      if constexpr (sizeof(Real) == 4) {
+        ld_row<(DMAX >= 4 ? 8 : 4)>(&w.Tm[v][l][0], reinterpret_cast<float (&)[(DMAX >= 4 ? 8 : 4)]>(t));
+      } else {
+#pragma unroll
+        for (int k = 0; k <= DMAX; ++k) t[k] = w.Tm[v][l][k];
+      }
+#pragma unroll
+      for (int k = l; k <= DMAX; ++k) s[k] = fma(t[k], pw[l], s[k]);
     }
+#pragma unroll
+    for (int k = 0; k <= DMAX; ++k) Q[v][k] = (k <= d) ? s[k] : (Real)0;
   }
   // graded-lex order (degree s ascending, exponent a of N descending, b of
   // B0 descending) with compile-time exponents: Q stays in registers
@@ -853,6 +897,10 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
           for (int l = 0; l <= kMaxDeg; ++l)
             for (int k = 0; k <= kMaxDeg; ++k) w.Tm[v][l][k] = (Real)T[l][k];
         }
+        w.vc[v][0] = w.sc_v[v];
+        w.vc[v][1] = w.of_v[v];
+        w.vc[v][2] = w.mu_v[v];
+        w.vc[v][3] = w.isg_v[v];
       }
       __syncthreads();
     }
@@ -946,7 +994,7 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
             eval_psi<Real, DMAX, NM>(w, d, nm, sx0[i], sx1[i], sx2[i], psi);
             whiten<Real, NM, WS>(w, psi, pt);
             yy = (Real)sy[i];
-            wt = a.weighted ? (Real)1 / fabs(yy) : (Real)1;
+            wt = a.weighted ? recip(fabs(yy)) : (Real)1;
           } else {
 #pragma unroll
             for (int j = 0; j < NM; ++j) pt[j] = 0;
@@ -979,7 +1027,7 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
           eval_psi<Real, DMAX, NM>(w, d, nm, sx0[i], sx1[i], sx2[i], psi);
           whiten<Real, NM, WS>(w, psi, pt);
           const Real yy = (Real)sy[i];
-          const Real wt = a.weighted ? (Real)1 / fabs(yy) : (Real)1;
+          const Real wt = a.weighted ? recip(fabs(yy)) : (Real)1;
           Real *row = w.stage + tid * LDS;
 #pragma unroll
           for (int j = 0; j < NM; ++j)
@@ -1051,7 +1099,7 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
         const Real piv = rk[k];
         const bool keep = piv > (Real)a.drop_tol;
         kept += keep;
-        const Real ip = keep ? (Real)1 / piv : (Real)0;
+        const Real ip = keep ? recip(piv) : (Real)0;
 #pragma unroll
         for (int q = 0; q < EPT; ++q) {
           if (ent[q] < 0) continue;
@@ -1156,7 +1204,7 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
           eval_psi<Real, DMAX, NM>(w, d, nm, sx0[i], sx1[i], sx2[i], psi);
           psi[0] = 1;
           const Real yy = (Real)sy[i];
-          const Real wt = a.weighted ? (Real)1 / fabs(yy) : (Real)1;
+          const Real wt = a.weighted ? recip(fabs(yy)) : (Real)1;
           Real r;
           if constexpr (sizeof(Real) == 8) {
             double p = w.uv[0][0], q = w.uv[1][0];
@@ -1168,35 +1216,44 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
             pole |= !(q > 0.0);
             r = wt * (yy * q - p);
           } else {
-            float qf = w.uvhi[1][0];
+            float hq[NM];
+            ld_row<NM>(w.uvhi[1], hq);
+            float qf = hq[0];
 #pragma unroll
-            for (int j2 = 1; j2 < NM; ++j2) qf = fmaf(psi[j2], w.uvhi[1][j2], qf);
+            for (int j2 = 1; j2 < NM; ++j2) qf = fmaf(psi[j2], hq[j2], qf);
             pole |= !(qf > 0.0f);
             if (frozen) {
-              float dq = w.dfz[1][0], dp = w.dfz[0][0];
+              float dv[NM], du[NM];
+              ld_row<NM>(w.dfz[1], dv);
+              ld_row<NM>(w.dfz[0], du);
+              float dq = dv[0], dp = du[0];
 #pragma unroll
               for (int j2 = 1; j2 < NM; ++j2) {
-                dq = fmaf(psi[j2], w.dfz[1][j2], dq);
-                dp = fmaf(psi[j2], w.dfz[0][j2], dp);
+                dq = fmaf(psi[j2], dv[j2], dq);
+                dp = fmaf(psi[j2], du[j2], dp);
               }
               r = wt * (w.efz[i] + fmaf(yy, dq, -dp));
             } else if (compensated) {
               // e = y q - p = sum_j (y psi_j) v_j - psi_j u_j (psi_0 = 1):
               // Dot2 against the head + tail iterate, two independent chains
+              float hp[NM], lq[NM], lp[NM];
+              ld_row<NM>(w.uvhi[0], hp);
+              ld_row<NM>(w.uvlo[1], lq);
+              ld_row<NM>(w.uvlo[0], lp);
               float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
 #pragma unroll
               for (int j2 = 0; j2 < NM; ++j2) {
                 const float av = yy * psi[j2], bv = -psi[j2];
-                const float pr0 = av * w.uvhi[1][j2], pr1 = bv * w.uvhi[0][j2];
-                const float pe0 = fmaf(av, w.uvhi[1][j2], -pr0);
-                const float pe1 = fmaf(bv, w.uvhi[0][j2], -pr1);
+                const float pr0 = av * hq[j2], pr1 = bv * hp[j2];
+                const float pe0 = fmaf(av, hq[j2], -pr0);
+                const float pe1 = fmaf(bv, hp[j2], -pr1);
                 float t0, e0, t1, e1;
                 two_sum(s0, pr0, t0, e0);
                 two_sum(s1, pr1, t1, e1);
                 s0 = t0;
                 s1 = t1;
-                c0 += e0 + pe0 + av * w.uvlo[1][j2];
-                c1 += e1 + pe1 + bv * w.uvlo[0][j2];
+                c0 += e0 + pe0 + av * lq[j2];
+                c1 += e1 + pe1 + bv * lp[j2];
               }
               float t, e;
               two_sum(s0, s1, t, e);
@@ -1204,9 +1261,11 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
               if (freezing) w.efz[i] = ef;
               r = wt * ef;
             } else {
-              float p = w.uvhi[0][0];
+              float hp[NM];
+              ld_row<NM>(w.uvhi[0], hp);
+              float p = hp[0];
 #pragma unroll
-              for (int j2 = 1; j2 < NM; ++j2) p = fmaf(psi[j2], w.uvhi[0][j2], p);
+              for (int j2 = 1; j2 < NM; ++j2) p = fmaf(psi[j2], hp[j2], p);
               r = wt * fmaf(yy, qf, -p);
             }
           }

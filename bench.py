@@ -39,8 +39,8 @@ WORKLOAD = ("batched fit 1024 kernels x 8 metrics, 512 samples, deg<=3 (TF32-cla
 # 2048 fits of 512 samples; traffic scales with the fit count), valid only
 # for the kernel sources they were taken on (SHA-256 of the files below);
 # None until a capture of the current sources is recorded.
-FIT_TRAFFIC = {"sources_sha256": "b4a25aa41dd812c56fa8af867823647a7047c8d2ccb67ca8f5c47b55425a1b30",
-               "bytes_per_fit": (17390336 + 48128) / 2048}
+FIT_TRAFFIC = {"sources_sha256": "a01e17a46705573a4a77c50dd80b03219d49591e25e6988ea06d7eb908cb9de5",
+               "bytes_per_fit": (17405440 + 50176) / 2048}
 FIT_SOURCES = ("paper_1906_00142_gb300/csrc/rp_fit_kernel.cuh", "paper_1906_00142_gb300/csrc/rp_fit.cuh",
                "paper_1906_00142_gb300/csrc/rp_fit_f32.cu", "paper_1906_00142_gb300/csrc/rp_tc.cuh",
                "paper_1906_00142_gb300/csrc/rp_internal.cuh")

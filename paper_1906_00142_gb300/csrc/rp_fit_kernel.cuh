@@ -20,9 +20,11 @@
 //     w_i y_i give the augmented Gram matrix, which is equilibrated and
 //     factored with column dropping (pivot below a drop tolerance: column
 //     removed, reported as rank deficiency);
-//  6. iterative refinement recomputes the residual from the samples
-//     (compensated FP32 dot products against the FP64 solution -- Ogita,
-//     Rump & Oishi's Dot2 -- on the FP32 path, plain FP64 on the FP64 path),
+//  6. iterative refinement recomputes the residual from the samples (FP32
+//     paths: against the iterate held as FP32 head + tail pairs, with
+//     compensated dot products -- Ogita, Rump & Oishi's Dot2 -- in one pass
+//     whose residuals later passes reuse plus a plain FP32 correction for the
+//     small change of the iterate since; plain FP64 on the FP64 path),
 //     stopping at ||dx|| <= tol ||x|| or when the corrections stop shrinking;
 //  7. the solution is mapped back to the monomial basis of the box-normalised
 //     variables in FP64.  Every refinement pass also checks that q is positive

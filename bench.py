@@ -39,8 +39,8 @@ WORKLOAD = ("batched fit 1024 kernels x 8 metrics, 512 samples, deg<=3 (TF32-cla
 # 2048 fits of 512 samples; traffic scales with the fit count), valid only
 # for the kernel sources they were taken on (SHA-256 of the files below);
 # None until a capture of the current sources is recorded.
-FIT_TRAFFIC = {"sources_sha256": "d2c6e92e6bb8b5e2cba2216541dee75c33a3da8adcd4b58666bcd02b842f982f",
-               "bytes_per_fit": (17405440 + 50176) / 2048}
+FIT_TRAFFIC = {"sources_sha256": "7db0e3d3a18dcd28d96db12f424a1c33db19caa2eaa0120bee3f947130347dcd",
+               "bytes_per_fit": (17390848 + 52736) / 2048}
 FIT_SOURCES = ("paper_1906_00142_gb300/csrc/rp_fit_kernel.cuh", "paper_1906_00142_gb300/csrc/rp_fit.cuh",
                "paper_1906_00142_gb300/csrc/rp_fit_f32.cu", "paper_1906_00142_gb300/csrc/rp_tc.cuh",
                "paper_1906_00142_gb300/csrc/rp_internal.cuh")

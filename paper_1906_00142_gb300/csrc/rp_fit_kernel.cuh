@@ -21,10 +21,11 @@
 //     factored with column dropping (pivot below a drop tolerance: column
 //     removed, reported as rank deficiency);
 //  6. iterative refinement recomputes the residual from the samples (FP32
-//     paths: against the iterate held as FP32 head + tail pairs, with
-//     compensated dot products -- Ogita, Rump & Oishi's Dot2 -- in one pass
-//     whose residuals later passes reuse plus a plain FP32 correction for the
-//     small change of the iterate since; plain FP64 on the FP64 path),
+//     paths: against the iterate held as FP32 head + tail pairs, plain FP32
+//     until the steps are small, then compensated dot products -- Ogita,
+//     Rump & Oishi's Dot2 -- in one pass whose residuals later passes reuse
+//     plus a plain FP32 correction for the small change of the iterate since;
+//     plain FP64 on the FP64 path),
 //     stopping at ||dx|| <= tol ||x|| or when the corrections stop shrinking;
 //  7. the solution is mapped back to the monomial basis of the box-normalised
 //     variables in FP64.  Every refinement pass also checks that q is positive
@@ -1160,15 +1161,12 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
     // rounding level is undone and the refinement stops.
     flags = (w.keep_cnt < n) ? RP_FIT_RANK_DEFICIENT : 0;
     float prev_rel = INFINITY, obj_prev = INFINITY, obj_drop = INFINITY;
-    // FP32 paths, cached samples: a compensated pass keeps each sample's
-    // Dot2 residual e_f = y q_f - p_f at that pass's iterate x_f; later
-    // passes take e(x) = e_f + (y psi.dv - psi.du) with (du, dv) = x - x_f,
-    // evaluated in plain FP32 (its rounding is ~1e-7 of a difference that
-    // stays below 1e-2 of the iterate), so every pass is compensated from the
-    // first one on and a step larger than 1e-2 freezes again.  Uncached fits
-    // switch from plain to Dot2 residuals once the steps fall below 1e-4.
+    bool compensated = sizeof(Real) == 8, done = false;
+    // FP32 paths, cached samples: the first compensated pass keeps each
+    // sample's Dot2 residual e_f = y q_f - p_f at that pass's iterate x_f;
+    // later passes take e(x) = e_f + (y psi.dv - psi.du) with (du, dv) =
+    // x - x_f, small enough for plain FP32 (one Dot2 pass per fit)
     const bool can_freeze = sizeof(Real) == 4 && cached;
-    bool compensated = sizeof(Real) == 8 || can_freeze, done = false;
     bool frozen = false;
     int pole_prev = 0, it = 0;
     float omega = 1.0f;   // step length (halved after an objective increase)
@@ -1417,11 +1415,9 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
       const float rel = apply_step<Real, NM, WS>(w, nm, n);
       const bool was_compensated = compensated;
       if (!compensated && rel < 1e-4f) compensated = true;
-      if (frozen && rel > 1e-2f) frozen = false;
       // stop at tol, or once compensated corrections stop shrinking (the
       // residuals' noise floor)
-      if (rel <= (float)a.tol || (was_compensated && prev_rel < 1e-4f && rel > 0.9f * prev_rel))
-        done = true;
+      if (rel <= (float)a.tol || (was_compensated && rel > 0.9f * prev_rel)) done = true;
       prev_rel = rel;
       if (done) {
         // converged: the last correction is below tol (or at the residuals'

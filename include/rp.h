@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define RP_VERSION 2
+#define RP_VERSION 3
 #define RP_MAX_DEGREE 4          /* total degree bound d <= 4 */
 #define RP_COEF_STRIDE 70        /* alpha_j at [0, 35), beta_j at [35, 70) */
 #define RP_NUM_CONFIGS 66        /* (2^a, 2^b), a + b <= 10 */
@@ -59,7 +59,10 @@ typedef enum rp_status {
 
 /* Per-fit status bits (rp_fit). */
 #define RP_FIT_RANK_DEFICIENT 1   /* columns dropped by the factorisation */
-#define RP_FIT_NOT_CONVERGED 2    /* refinement stopped before tol */
+#define RP_FIT_NOT_CONVERGED 2    /* refinement ended (max_refine steps, or steps that kept raising
+                                     the objective) before its stop test was met; on the FP32 and
+                                     tensor-core precisions such a fit is solved again with FP64
+                                     arithmetic (RP_FIT_FP64_PASS) */
 #define RP_FIT_POLE 4             /* fitted q <= 0 at one of the fit's samples */
 #define RP_FIT_NONFINITE 8        /* NaN/Inf in the fit's samples: no fit */
 #define RP_FIT_NONPOS_Y 16        /* y <= 0 with relative weighting: no fit */
@@ -70,6 +73,13 @@ typedef enum rp_status {
                                      was solved again from the FP32 Gram on CUDA cores */
 #define RP_FIT_ITER_SHIFT 8       /* bits 8..15: refinement iterations performed */
 #define RP_FIT_ITER_MASK 0xFF00
+#define RP_FIT_ACC_SHIFT 16       /* bits 16..23: of those, accurate (double-float residual)
+                                     passes on the FP32 and tensor-core precisions */
+#define RP_FIT_ACC_MASK 0xFF0000
+#define RP_FIT_FP64_PASS (1 << 24) /* FP32 and tensor-core precisions: the fit's own solve dropped
+                                     pivots at its drop tolerance or stopped short of tol, so the
+                                     fit was solved again with RP_PREC_FP64 arithmetic (the
+                                     other bits then describe that solve) */
 
 /* Per-query status bits (rp_eval_search). */
 #define RP_Q_NO_VALID 1           /* no configuration valid: argmin = -1 */
@@ -98,14 +108,34 @@ typedef struct rp_fit_desc {
   int32_t precision;       /* rp_precision */
   int32_t max_refine;      /* refinement iterations after the first solve, 0..64 */
   int32_t flags;           /* RP_FIT_* flags */
-  double tol;              /* refinement stops when ||dx|| <= tol * ||x|| (e.g. 1e-12) */
+  double tol;              /* refinement stops once an accurate step (FP64 on the FP64 path,
+                              double-float on the others) leaves an estimated relative error
+                              c * ||dx|| / ||x|| <= tol, c = the contraction per step estimated
+                              from the steps (at least 1e-3); e.g. 1e-8, or 1e-12 to refine to
+                              the arithmetic's floor */
   const int8_t *degrees;   /* optional device array [F] of per-fit degrees 1..4 */
+  /* Shared sample points (Sec. 3.3 Step 1 measures all metrics of a kernel
+     at the same points).  point_off NULL: fit f's points are the columns
+     fit_off[f] .. fit_off[f+1] of x, a float[3][num_samples] array.
+     Otherwise each run of fits_per_point_set consecutive fits shares one
+     point set: fit f uses set p = f / fits_per_point_set, the columns
+     point_off[p] .. point_off[p+1] of x (a float[3][num_points] array), and
+     its values y[fit_off[f] .. fit_off[f+1]), one per point (a fit whose
+     value count differs from its set's point count gets RP_FIT_EMPTY).  The
+     box, marginal polynomials and basis whitening are then computed once
+     per set.  point_off: device int64 [ceil(F / fits_per_point_set) + 1]. */
+  const int64_t *point_off;
+  int64_t num_points;      /* columns of x when point_off is given */
+  int32_t fits_per_point_set;   /* >= 1 when point_off is given */
+  int32_t reserved;        /* must be 0 */
 } rp_fit_desc;
 
 /*
  * rp_fit_workspace_size -- bytes of the optional device workspace of rp_fit
- * for `desc` (the dynamic fit schedule's counter: 16 for a non-empty batch,
- * 0 otherwise), written to *bytes.  Host-only, launches nothing.
+ * for `desc`, written to *bytes: 32 for a non-empty batch (two 64-bit
+ * counters 16 bytes apart: the dynamic fit schedule's claims and the number
+ * of fits passed on to the FP64 path, RP_FIT_FP64_PASS), 0 otherwise.
+ * Host-only, launches nothing.
  */
 int rp_fit_workspace_size(const rp_fit_desc *desc, size_t *bytes);
 
@@ -148,15 +178,15 @@ int rp_fit(const rp_fit_desc *desc, const float *x, const float *y, const int64_
  * rp_fit_noalloc -- rp_fit (same arguments, results and errors) for callers
  * that cannot provide device memory, e.g. a host thread on a latency path
  * where cudaMalloc's implicit device synchronisation is not acceptable.  It
- * allocates nothing: the dynamic schedule's scratch (one 64-bit counter, the
- * whole of rp_fit_workspace_size) is a statically allocated 16-byte device
- * array of the library, reset with cudaMemsetAsync on `stream` before each
- * launch.  The paper has no counterpart (it describes no GPU fitting).
- * Limit: scratch of 16 bytes, which covers any batch size; a larger need
+ * allocates nothing: its scratch (the two 64-bit counters that make up
+ * rp_fit_workspace_size) is a statically allocated 32-byte device array of
+ * the library, reset with cudaMemsetAsync on `stream` before use.  The
+ * paper has no counterpart (it describes no GPU fitting).
+ * Limit: scratch of 32 bytes, which covers any batch size; a larger need
  * returns RP_ERR_WORKSPACE.  The first call on each device resolves the
  * array's address (cudaGetSymbolAddress) with that device current: make it
  * before capturing any stream.  Calls that overlap in time (any streams,
- * any threads) share the counter and race: serialise them.
+ * any threads) share the counters and race: serialise them.
  */
 int rp_fit_noalloc(const rp_fit_desc *desc, const float *x, const float *y,
                    const int64_t *fit_off, double *coef, float *coef32, double *box,
@@ -233,6 +263,59 @@ int rp_eval_search(const void *program, int64_t num_kernels, int32_t degree,
                    const rp_hw_fixed *hw, const float *queries, int64_t num_queries,
                    int32_t *argmin, float *best, float *second, int32_t *status,
                    void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * rp_eval_search_tiebreak -- rp_eval_search with Step 5's choice among
+ * several optimal configurations made by a second metric (Sec. 3.3 Step 5
+ * suggests one): the configurations whose cycles are at most
+ * (1 + tie_rel) times the smallest count as optimal, and argmin[q] is the
+ * one of them with the most active warps per SM (W_active, Sec. 2 Example
+ * 1); among equal W_active the lowest index.  best[q] and second[q] are the
+ * smallest and second-smallest cycle counts as in rp_eval_search (argmin's
+ * own count may exceed best by up to the factor).  Each query's
+ * configurations are evaluated twice (FP32, identically).  tie_rel in
+ * [0, 1) (0: only exact ties).  Other arguments, errors and workspace as
+ * rp_eval_search.
+ */
+int rp_eval_search_tiebreak(const void *program, int64_t num_kernels, int32_t degree,
+                            const rp_hw_fixed *hw, const float *queries, int64_t num_queries,
+                            float tie_rel, int32_t *argmin, float *best, float *second,
+                            int32_t *status, void *workspace, size_t workspace_bytes,
+                            void *stream);
+
+/*
+ * rp_eval_occupancy -- the occupancy rational program on its own (Sec. 2,
+ * Example 1): for every query and configuration c, from the program's
+ * fitted registers per thread R and shared-memory words per block Z
+ * (metrics 7 and 8, rounded to the nearest integer) at the query's N,
+ *   B_active = min(b_max, floor(w_max / wpb), floor(r_sm / (R wpb warp)) [R > 0],
+ *              floor(z_sm / Z) [Z > 0]), 0 if T > t_max, R T > r_sm or Z > z_sm,
+ *   W_active = min(B_active wpb, w_max), wpb = ceil(T / warp), T = B0 B1;
+ * written to b_active[q*66 + c] and w_active[q*66 + c] (device int32
+ * [Q][66]); both 0 where the configuration cannot be resident or a metric's
+ * denominator is <= 0 at N (status RP_Q_POLE), and for a bad query
+ * (RP_Q_BAD, as rp_eval_search).  program, hw, queries as rp_eval_search.
+ * Errors: RP_ERR_INVALID_ARG, RP_ERR_ALIGNMENT, RP_ERR_CUDA.
+ */
+int rp_eval_occupancy(const void *program, int64_t num_kernels, int32_t degree,
+                      const rp_hw_fixed *hw, const float *queries, int64_t num_queries,
+                      int32_t *b_active, int32_t *w_active, int32_t *status, void *stream);
+
+/* Per-query status bits (rp_error_pct). */
+#define RP_EP_NO_RUNTIME 1        /* no finite runtime for the query: err = NaN */
+#define RP_EP_BAD_CHOICE 2        /* choice outside 0..65 or its runtime not finite: err = NaN */
+
+/*
+ * rp_error_pct -- Error % of chosen configurations (Sec. 5): with measured
+ * runtimes t[q][0..65] (device float [Q][66], +inf or NaN for a
+ * configuration not run) and the configuration chosen for each query
+ * (device int32 [Q], e.g. rp_eval_search's argmin),
+ *   B = min and W = max of the query's finite runtimes,
+ *   err_pct[q] = (t[q][choice[q]] - B) / (W - B) * 100   (0 when W == B),
+ * in FP32; status[q] RP_EP_* bits.  Errors: RP_ERR_INVALID_ARG, RP_ERR_CUDA.
+ */
+int rp_error_pct(const float *runtimes, const int32_t *choice, int64_t num_queries,
+                 float *err_pct, int32_t *status, void *stream);
 
 /*
  * rp_search_workspace_size -- bytes of the optional device workspace of

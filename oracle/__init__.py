@@ -58,7 +58,7 @@ def _load():
         lib = C.CDLL(_SO)
         P = C.c_void_p
         i64, i32, dbl = C.c_int64, C.c_int, C.c_double
-        lib.rpo_fit.argtypes = [i64, P, P, P, i64, P, i32, dbl, i64, P, P, P, P, dbl]
+        lib.rpo_fit.argtypes = [i64, P, P, P, i64, P, i32, dbl, i64, P, P, P, P]
         lib.rpo_fit_qr.argtypes = [i64, P, P, P, i64, P, i32, i64, P, P, P, P]
         lib.rpo_predict.argtypes = [i64, P, i32, P, i64, P, P]
         lib.rpo_relmse.argtypes = [i64, P, P, P, i64, P, P, i64, P, P, P]
@@ -102,7 +102,7 @@ def _fit_args(x, y, fit_off, degree):
     return x, y, off, deg, F
 
 
-def fit(x, y, fit_off, degree, weighted=True, rcond=1e-12, method="svd", perturb=0.0):
+def fit(x, y, fit_off, degree, weighted=True, rcond=1e-12, method="svd"):
     """Least-squares rational fits.  Returns dict(coef[F][70], box[F][6],
     rank[F], status[F]) in the normalised monomial basis."""
     lib = _load()
@@ -114,7 +114,7 @@ def fit(x, y, fit_off, degree, weighted=True, rcond=1e-12, method="svd", perturb
     status = np.zeros(F, np.int32)
     if method == "svd":
         rc = lib.rpo_fit(F, _p(off), _p(x), _p(y), S, _p(deg), int(weighted), float(rcond),
-                         COEF_STRIDE, _p(coef), _p(box), _p(rank), _p(status), float(perturb))
+                         COEF_STRIDE, _p(coef), _p(box), _p(rank), _p(status))
     else:
         rc = lib.rpo_fit_qr(F, _p(off), _p(x), _p(y), S, _p(deg), int(weighted),
                             COEF_STRIDE, _p(coef), _p(box), _p(rank), _p(status))
@@ -257,23 +257,3 @@ def error_pct(c_rt, best_t, worst_t):
     """Error % of a chosen configuration (Sec. 5):
     (C_rt - Best_time) / (Worst_time - Best_time) * 100."""
     return (c_rt - best_t) / (worst_t - best_t) * 100.0
-
-
-def fit_sensitivity(x, y, fit_off, degree, base=None, weighted=True, eps=2.0 ** -23):
-    """How far each fit's predictions at its own samples move when every
-    entry of its design matrix and right-hand side is perturbed by a
-    relative eps (about one FP32 rounding, the precision in which a GPU
-    builds the design).  Returns the max relative prediction change per
-    fit.  A fit whose predictions move by more than ~1e-5 is not determined
-    to 1e-4 by FP32-precision data (ill-posed at that precision)."""
-    if base is None:
-        base = fit(x, y, fit_off, degree, weighted=weighted)
-    pert = fit(x, y, fit_off, degree, weighted=weighted, perturb=eps)
-    p0 = predict_samples(base, x, fit_off)
-    p1 = predict_samples(pert, x, fit_off)
-    rel = np.abs(p1 - p0) / np.abs(p0)
-    out = np.zeros(len(fit_off) - 1)
-    for f in range(len(out)):
-        a, b = fit_off[f], fit_off[f + 1]
-        out[f] = rel[a:b].max() if b > a else 0.0
-    return out

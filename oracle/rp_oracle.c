@@ -217,20 +217,10 @@ int rpo_lstsq_qr(int m, int n, const double *A, const double *b, double *x) {
  * [off[f], off[f+1]).  coef row f: alpha_j at [0, nm), beta_j at
  * [stride/2, stride/2 + nm) in the normalised monomial basis; box row f:
  * (lo_N, hi_N, lo_B0, hi_B0, lo_B1, hi_B1). */
-/* splitmix64: used only to perturb design entries for the sensitivity
- * check (every entry scaled by 1 + perturb * u, u uniform in [-1, 1)). */
-static double unit_hash(uint64_t k) {
-  k += 0x9E3779B97F4A7C15ull;
-  k = (k ^ (k >> 30)) * 0xBF58476D1CE4E5B9ull;
-  k = (k ^ (k >> 27)) * 0x94D049BB133111EBull;
-  k ^= k >> 31;
-  return (double)(k >> 11) * (2.0 / 9007199254740992.0) - 1.0;
-}
-
 static void fit_one(int64_t f, const int64_t *off, const double *x, const double *y,
                     int64_t S, const int8_t *deg, int weighted, double rcond,
                     int use_qr, int64_t stride, double *coef, double *box,
-                    int32_t *rank, int32_t *status, double perturb) {
+                    int32_t *rank, int32_t *status) {
   int64_t b0 = off[f], b1 = off[f + 1];
   int m = (int)(b1 - b0);
   int d = deg[f];
@@ -288,12 +278,6 @@ static void fit_one(int64_t f, const int64_t *off, const double *x, const double
     for (int j = 1; j < nm; ++j) A[i * n + nm + j - 1] = -w * yi * (phi[i * nm + j] - mu[j]);
     b[i] = w * yi;
   }
-  if (perturb > 0.0)
-    for (int i = 0; i < m; ++i) {
-      for (int j = 0; j < n; ++j)
-        A[i * n + j] *= 1.0 + perturb * unit_hash(((uint64_t)(b0 + i) << 8) + (uint64_t)j);
-      b[i] *= 1.0 + perturb * unit_hash(((uint64_t)(b0 + i) << 8) + 255u);
-    }
   double xs[2 * RPO_MAXNM];
   int r = n;
   if (use_qr) {
@@ -324,26 +308,25 @@ static void fit_one(int64_t f, const int64_t *off, const double *x, const double
 static int fit_all(int64_t F, const int64_t *off, const double *x, const double *y,
                    int64_t S, const int8_t *deg, int weighted, double rcond, int use_qr,
                    int64_t stride, double *coef, double *box, int32_t *rank,
-                   int32_t *status, double perturb) {
+                   int32_t *status) {
   for (int64_t f = 0; f < F; ++f)
     if (deg[f] < 0 || deg[f] > RPO_MAXD || 2 * rpo_num_monomials(deg[f]) > stride) return -1;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads)
   for (int64_t f = 0; f < F; ++f)
-    fit_one(f, off, x, y, S, deg, weighted, rcond, use_qr, stride, coef, box, rank, status, perturb);
+    fit_one(f, off, x, y, S, deg, weighted, rcond, use_qr, stride, coef, box, rank, status);
   return 0;
 }
 
 int rpo_fit(int64_t F, const int64_t *off, const double *x, const double *y, int64_t S,
             const int8_t *deg, int weighted, double rcond, int64_t stride, double *coef,
-            double *box, int32_t *rank, int32_t *status, double perturb) {
-  return fit_all(F, off, x, y, S, deg, weighted, rcond, 0, stride, coef, box, rank, status,
-                 perturb);
+            double *box, int32_t *rank, int32_t *status) {
+  return fit_all(F, off, x, y, S, deg, weighted, rcond, 0, stride, coef, box, rank, status);
 }
 
 int rpo_fit_qr(int64_t F, const int64_t *off, const double *x, const double *y, int64_t S,
                const int8_t *deg, int weighted, int64_t stride, double *coef, double *box,
                int32_t *rank, int32_t *status) {
-  return fit_all(F, off, x, y, S, deg, weighted, 0.0, 1, stride, coef, box, rank, status, 0.0);
+  return fit_all(F, off, x, y, S, deg, weighted, 0.0, 1, stride, coef, box, rank, status);
 }
 
 /* Evaluate one fitted p/q at raw points pts[P][3]. */

@@ -32,6 +32,8 @@ PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16": 4, "bf16x3": 5}
 RP_FIT_RANK_DEFICIENT, RP_FIT_NOT_CONVERGED, RP_FIT_POLE = 1, 2, 4
 RP_FIT_NONFINITE, RP_FIT_NONPOS_Y, RP_FIT_EMPTY, RP_FIT_TIMEOUT, RP_FIT_ESCALATED = 8, 16, 32, 64, 128
 RP_FIT_ITER_SHIFT, RP_FIT_ITER_MASK = 8, 0xFF00
+RP_FIT_ACC_SHIFT, RP_FIT_ACC_MASK = 16, 0xFF0000
+RP_FIT_FP64_PASS = 1 << 24
 RP_Q_NO_VALID, RP_Q_POLE, RP_Q_BAD = 1, 2, 4
 RP_FIT_UNWEIGHTED = 1
 
@@ -43,7 +45,9 @@ class RPError(RuntimeError):
 class FitDesc(C.Structure):
     _fields_ = [("num_fits", C.c_int64), ("num_samples", C.c_int64), ("degree", C.c_int32),
                 ("precision", C.c_int32), ("max_refine", C.c_int32), ("flags", C.c_int32),
-                ("tol", C.c_double), ("degrees", C.c_void_p)]
+                ("tol", C.c_double), ("degrees", C.c_void_p), ("point_off", C.c_void_p),
+                ("num_points", C.c_int64), ("fits_per_point_set", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class HwFixed(C.Structure):
@@ -132,7 +136,7 @@ def rp_fit_workspace_size(desc: FitDesc) -> int:
 
 
 def _fit_args(x, y, fit_off, degree, precision, max_refine, tol, degrees, weighted, out,
-              stream, schedule):
+              stream, schedule, point_off=None, fits_per_point_set=1):
     F = fit_off.numel() - 1
     S = y.numel()
     dev = y.device
@@ -144,7 +148,10 @@ def _fit_args(x, y, fit_off, degree, precision, max_refine, tol, degrees, weight
                    rank=torch.empty(F, dtype=torch.int32, device=dev))
     desc = FitDesc(F, S, int(degree), PREC[precision], int(max_refine),
                    0 if weighted else RP_FIT_UNWEIGHTED, float(tol),
-                   _ptr_or_null(degrees, torch.int8, "degrees").value)
+                   _ptr_or_null(degrees, torch.int8, "degrees").value,
+                   _ptr_or_null(point_off, torch.int64, "point_off").value,
+                   x.shape[1] if point_off is not None else 0,
+                   int(fits_per_point_set) if point_off is not None else 0, 0)
     st = torch.cuda.current_stream() if stream is None else stream
     ws_bytes = rp_fit_workspace_size(desc)
     ws = None
@@ -166,40 +173,43 @@ def _fit_args(x, y, fit_off, degree, precision, max_refine, tol, degrees, weight
 
 
 def rp_fit(x: torch.Tensor, y: torch.Tensor, fit_off: torch.Tensor, degree: int,
-           precision: str = "fp32", max_refine: int = 8, tol: float = 1e-12,
+           precision: str = "fp32", max_refine: int = 8, tol: float = 1e-8,
            degrees: torch.Tensor | None = None, weighted: bool = True, out=None, stream=None,
-           schedule: str = "dynamic"):
+           schedule: str = "dynamic", point_off: torch.Tensor | None = None,
+           fits_per_point_set: int = 1):
     """Batched rational least-squares fits (see rp_fit in include/rp.h).
-    x: float32 [3, S], y: float32 [S], fit_off: int64 [F+1] (all CUDA).
-    schedule "dynamic" (CTAs claim fits from a counter in a 16-byte
+    x: float32 [3, S], y: float32 [S], fit_off: int64 [F+1] (all CUDA); with
+    point_off (int64 [P+1]) x is float32 [3, num_points] and each run of
+    fits_per_point_set consecutive fits shares one point set.
+    schedule "dynamic" (CTAs claim point sets from a counter in the 32-byte
     workspace, out["workspace"] or allocated here) or "static".
     Returns dict(coef float64 [F,70], coef32 float32 [F,70], box float64 [F,6],
     status int32 [F], rank int32 [F])."""
     out, args, _ws = _fit_args(x, y, fit_off, degree, precision, max_refine, tol, degrees,
-                               weighted, out, stream, schedule)
+                               weighted, out, stream, schedule, point_off, fits_per_point_set)
     _check(load_library().rp_fit(*args), "rp_fit")
     return out
 
 
 def rp_fit_noalloc(x, y, fit_off, degree: int, precision: str = "fp32", max_refine: int = 8,
-                   tol: float = 1e-12, degrees=None, weighted: bool = True, out=None,
-                   stream=None):
+                   tol: float = 1e-8, degrees=None, weighted: bool = True, out=None,
+                   stream=None, point_off=None, fits_per_point_set: int = 1):
     """rp_fit with the library's static scratch instead of a workspace (see
     rp_fit_noalloc in include/rp.h); outputs as rp_fit."""
     out, args, _ws = _fit_args(x, y, fit_off, degree, precision, max_refine, tol, degrees,
-                               weighted, out, stream, "static")
+                               weighted, out, stream, "static", point_off, fits_per_point_set)
     _check(load_library().rp_fit_noalloc(*args[:9], args[11]), "rp_fit_noalloc")
     return out
 
 
 def rp_tune_fit(x, y, fit_off, degree: int, precision: str = "fp32", max_refine: int = 8,
-                tol: float = 1e-12, degrees=None, weighted: bool = True, out=None, stream=None,
-                schedule: str = "dynamic") -> int:
+                tol: float = 1e-8, degrees=None, weighted: bool = True, out=None, stream=None,
+                schedule: str = "dynamic", point_off=None, fits_per_point_set: int = 1) -> int:
     """Time the fit kernel's grid sizes on these fits (see rp_tune_fit in
     include/rp.h); returns the CTAs per SM now used for this precision and
     degree.  Synchronises; call before any graph capture."""
     out, args, _ws = _fit_args(x, y, fit_off, degree, precision, max_refine, tol, degrees,
-                               weighted, out, stream, schedule)
+                               weighted, out, stream, schedule, point_off, fits_per_point_set)
     c = C.c_int32(0)
     _check(load_library().rp_tune_fit(*args, C.byref(c)), "rp_tune_fit")
     return c.value

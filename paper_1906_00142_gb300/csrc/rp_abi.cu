@@ -71,9 +71,12 @@ int rp_fit(const rp_fit_desc *desc, const float *x, const float *y, const int64_
   if (desc->degree < 1 || desc->degree > RP_MAX_DEGREE) return RP_ERR_INVALID_ARG;
   if (desc->precision < RP_PREC_FP64 || desc->precision > RP_PREC_BF16X3) return RP_ERR_INVALID_ARG;
   if (desc->max_refine < 0 || desc->max_refine > 64 || !(desc->tol >= 0.0)) return RP_ERR_INVALID_ARG;
+  if (desc->reserved != 0) return RP_ERR_INVALID_ARG;
+  if (desc->point_off && (desc->fits_per_point_set < 1 || desc->num_points < 0)) return RP_ERR_INVALID_ARG;
   if (desc->num_fits == 0) return RP_OK;
   if (!fit_off || !coef || !box || !status || !rank) return RP_ERR_INVALID_ARG;
-  if (desc->num_samples > 0 && (!x || !y)) return RP_ERR_INVALID_ARG;
+  if (desc->num_samples > 0 && !y) return RP_ERR_INVALID_ARG;
+  if ((desc->point_off ? desc->num_points : desc->num_samples) > 0 && !x) return RP_ERR_INVALID_ARG;
   if (workspace && workspace_bytes < rpk::fit_workspace_bytes(*desc)) return RP_ERR_WORKSPACE;
   if (workspace && !aligned(workspace, 16)) return RP_ERR_ALIGNMENT;
   if (!rpk::fit_precision_supported(desc->precision)) return RP_ERR_UNSUPPORTED;
@@ -144,6 +147,58 @@ int rp_eval_search(const void *program, int64_t num_kernels, int32_t degree,
   auto pv = rpk::program_sections<rpk::ProgramView>(program, num_kernels);
   return from_cuda(rpk::launch_search(pv, num_kernels, degree, *hw, queries, num_queries, argmin,
                                       best, second, status, workspace, as_stream(stream)));
+}
+
+static bool hw_ok(const rp_hw_fixed *hw) {
+  return hw && hw->warp_size >= 1 && hw->t_max >= 1 && hw->b_max >= 1 && hw->w_max >= 1 &&
+         hw->r_sm >= 1 && hw->z_sm >= 1 && hw->issue_cycles > 0.0f && hw->reserved == 0 &&
+         hw->r_sm < (1 << 24) && hw->z_sm < (1 << 24);
+}
+
+int rp_eval_search_tiebreak(const void *program, int64_t num_kernels, int32_t degree,
+                            const rp_hw_fixed *hw, const float *queries, int64_t num_queries,
+                            float tie_rel, int32_t *argmin, float *best, float *second,
+                            int32_t *status, void *workspace, size_t workspace_bytes,
+                            void *stream) {
+  if (!(tie_rel >= 0.0f) || !(tie_rel < 1.0f)) return RP_ERR_INVALID_ARG;
+  if (num_kernels < 0 || num_queries < 0 || degree < 0 || degree > RP_MAX_DEGREE || !hw_ok(hw))
+    return RP_ERR_INVALID_ARG;
+  if (num_queries == 0) return RP_OK;
+  if (!program || !queries || !argmin || !best || !second || !status) return RP_ERR_INVALID_ARG;
+  if (!aligned(program, 16) || !aligned(queries, 16)) return RP_ERR_ALIGNMENT;
+  if (workspace) {
+    if (workspace_bytes < rpk::search_workspace_bytes(num_kernels, num_queries))
+      return RP_ERR_WORKSPACE;
+    if (!aligned(workspace, 16)) return RP_ERR_ALIGNMENT;
+  }
+  if (!device_ok()) return RP_ERR_NO_DEVICE;
+  auto pv = rpk::program_sections<rpk::ProgramView>(program, num_kernels);
+  return from_cuda(rpk::launch_search(pv, num_kernels, degree, *hw, queries, num_queries, argmin,
+                                      best, second, status, workspace, as_stream(stream), tie_rel));
+}
+
+int rp_eval_occupancy(const void *program, int64_t num_kernels, int32_t degree,
+                      const rp_hw_fixed *hw, const float *queries, int64_t num_queries,
+                      int32_t *b_active, int32_t *w_active, int32_t *status, void *stream) {
+  if (num_kernels < 0 || num_queries < 0 || degree < 0 || degree > RP_MAX_DEGREE || !hw_ok(hw))
+    return RP_ERR_INVALID_ARG;
+  if (num_queries == 0) return RP_OK;
+  if (!program || !queries || !b_active || !w_active || !status) return RP_ERR_INVALID_ARG;
+  if (!aligned(program, 16) || !aligned(queries, 16)) return RP_ERR_ALIGNMENT;
+  if (!device_ok()) return RP_ERR_NO_DEVICE;
+  auto pv = rpk::program_sections<rpk::ProgramView>(program, num_kernels);
+  return from_cuda(rpk::launch_occupancy(pv, num_kernels, degree, *hw, queries, num_queries,
+                                         b_active, w_active, status, as_stream(stream)));
+}
+
+int rp_error_pct(const float *runtimes, const int32_t *choice, int64_t num_queries,
+                 float *err_pct, int32_t *status, void *stream) {
+  if (num_queries < 0) return RP_ERR_INVALID_ARG;
+  if (num_queries == 0) return RP_OK;
+  if (!runtimes || !choice || !err_pct || !status) return RP_ERR_INVALID_ARG;
+  if (!device_ok()) return RP_ERR_NO_DEVICE;
+  return from_cuda(rpk::launch_error_pct(runtimes, choice, num_queries, err_pct, status,
+                                         as_stream(stream)));
 }
 
 int rp_tune_search(const void *program, int64_t num_kernels, int32_t degree,

@@ -11,7 +11,7 @@ namespace rpk {
 // Scratch of rp_fit_noalloc: the dynamic schedule's counter in a statically
 // allocated device array (one per process and device; calls that overlap
 // in time share it).
-static __device__ __align__(256) unsigned long long g_fit_scratch[2];
+static __device__ __align__(256) unsigned long long g_fit_scratch[4];
 
 cudaError_t fit_static_scratch(void **ptr, size_t *bytes) {
   static void *addr[16] = {};
@@ -30,8 +30,9 @@ cudaError_t fit_static_scratch(void **ptr, size_t *bytes) {
   return cudaSuccess;
 }
 
-// One 64-bit counter for the dynamic fit schedule (16 bytes, aligned).
-size_t fit_workspace_bytes(const rp_fit_desc &desc) { return desc.num_fits > 0 ? 16 : 0; }
+// Two 64-bit counters, 16 bytes apart: the dynamic fit schedule's claims
+// and the number of fits passed on to the FP64 path.
+size_t fit_workspace_bytes(const rp_fit_desc &desc) { return desc.num_fits > 0 ? 32 : 0; }
 
 int fit_max_ctas_per_sm(const rp_fit_desc &desc) {
   const int dmax = desc.degree;
@@ -70,10 +71,21 @@ cudaError_t launch_fit(const rp_fit_desc &desc, const float *x, const float *y,
   a.box = box;
   a.status = status;
   a.rank = rank;
+  a.point_off = desc.point_off;
+  a.num_points = desc.num_points;
+  a.fits_per_set = desc.point_off ? desc.fits_per_point_set : 1;
   a.counter = reinterpret_cast<unsigned long long *>(workspace);
+  a.esc_count = workspace ? reinterpret_cast<unsigned long long *>(static_cast<char *>(workspace) + 16)
+                          : nullptr;
   const int dmax = desc.degree;
-  const int p = desc.precision;
+  const int p0 = desc.precision;
+  int p = p0;
   a.drop_tol = (p == RP_PREC_FP64) ? 1e-13 : 1e-7;
+  a.esc_mode = (p == RP_PREC_FP64) ? 0 : 1;
+  if (a.esc_count) {
+    cudaError_t e = cudaMemsetAsync(a.esc_count, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+  }
   auto go = [&](int variant) {
     switch (p) {
       case RP_PREC_FP64: return fit_launch_f64(a, variant, p, s);
@@ -87,18 +99,27 @@ cudaError_t launch_fit(const rp_fit_desc &desc, const float *x, const float *y,
   // A batch of per-fit degrees up to 4 runs as two launches on the stream:
   // the degree-3 variant (4 CTAs/SM on the FP32 path) for degrees <= 3, the
   // degree-4 variant (its basis needs ~250 registers) for degree 4 only.
-  if (desc.degrees && dmax == 4) {
+  auto all = [&]() -> cudaError_t {
+    if (desc.degrees && dmax == 4) {
+      a.deg_lo = 1;
+      a.deg_hi = 3;
+      cudaError_t e = go(3);
+      if (e != cudaSuccess) return e;
+      a.deg_lo = 4;
+      a.deg_hi = 4;
+      return go(4);
+    }
     a.deg_lo = 1;
-    a.deg_hi = 3;
-    cudaError_t e = go(3);
-    if (e != cudaSuccess) return e;
-    a.deg_lo = 4;
-    a.deg_hi = 4;
-    return go(4);
-  }
-  a.deg_lo = 1;
-  a.deg_hi = dmax;
-  return go(dmax);
+    a.deg_hi = dmax;
+    return go(dmax);
+  };
+  cudaError_t e = all();
+  if (e != cudaSuccess || p0 == RP_PREC_FP64) return e;
+  // the fits the FP32 / tensor-core launch passed on, on the FP64 path
+  p = RP_PREC_FP64;
+  a.drop_tol = 1e-13;
+  a.esc_mode = 2;
+  return all();
 }
 
 }  // namespace rpk

@@ -25,7 +25,22 @@ struct FitArgs {
   int32_t *rank;
   unsigned long long *counter;   // dynamic fit schedule (workspace), or null
   int deg_lo, deg_hi;            // degrees this launch fits (valid ones outside: skipped)
+  // Fits the FP32 and tensor-core kernels cannot finish (pivots dropped at
+  // their drop tolerance, or refinement stopped short of tol) are solved
+  // again by the FP64 kernel: esc_mode 1 marks them (kPending64) and counts
+  // them in *esc_count (workspace, or null); esc_mode 2 (the FP64 kernel)
+  // fits only marked fits, and returns at once when *esc_count is 0.
+  int esc_mode;
+  unsigned long long *esc_count;
+  // shared sample points: null, or int64 [ceil(F / fits_per_set) + 1]
+  // offsets into x (float [3][num_points]); fit f uses point set
+  // f / fits_per_set and its values y[off[f] .. off[f+1])
+  const int64_t *point_off;
+  int64_t num_points;
+  int fits_per_set;
 };
+
+constexpr int32_t kPending64 = 1 << 25;   // status bit between the two launches
 
 // Real = double, design Gram on CUDA cores (RP_PREC_FP64)
 cudaError_t fit_launch_f64(const FitArgs &a, int dmax, int precision, cudaStream_t s);

@@ -21,12 +21,14 @@
 //     factored with column dropping (pivot below a drop tolerance: column
 //     removed, reported as rank deficiency);
 //  6. iterative refinement recomputes the residual from the samples (FP32
-//     paths: against the iterate held as FP32 head + tail pairs, plain FP32
-//     until the steps are small, then compensated dot products -- Ogita,
-//     Rump & Oishi's Dot2 -- in one pass whose residuals later passes reuse
-//     plus a plain FP32 correction for the small change of the iterate since;
-//     plain FP64 on the FP64 path),
-//     stopping at ||dx|| <= tol ||x|| or when the corrections stop shrinking;
+//     paths: plain FP32 passes while the steps are large, then accurate
+//     passes in double-float arithmetic -- head + tail FP32 pairs built from
+//     error-free sums and products, ~2^-44 relative -- in which the basis
+//     functions, the residual, the normal-equation residual's sums and the
+//     sample means of the basis are all carried in pairs; plain FP64 on the
+//     FP64 path), stopping at ||dx|| <= tol ||x|| or when the corrections
+//     stop shrinking.  The first accurate pass also fixes the normalisation
+//     mean(q) = 1 with the exact sample means;
 //  7. the solution is mapped back to the monomial basis of the box-normalised
 //     variables in FP64.  Every refinement pass also checks that q is positive
 //     at every sample for the solution the pass starts from.
@@ -60,6 +62,69 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   const float bb = s - a;
   e = (a - (s - bb)) + (b - bb);
 }
+
+// ---- double-float arithmetic: a value is a pair (h, l) of FP32 numbers with
+// |l| <= ulp(h) / 2, worth ~44 bits.  Error-free transformations of a sum
+// (two_sum, Knuth) and of a product (two_prod via FMA), Dekker's
+// renormalisation, and Ogita-Rump-Oishi's compensated dot product.  Products
+// are formed with __fmul_rn so that the compiler never fuses them into a
+// following addition (which would break the error-free identities).
+struct dfl {
+  float h, l;
+};
+__device__ __forceinline__ dfl df_norm(float h, float l) {
+  dfl r;
+  r.h = h + l;
+  r.l = l - (r.h - h);
+  return r;
+}
+__device__ __forceinline__ dfl df_make(float h) { return dfl{h, 0.0f}; }
+__device__ __forceinline__ dfl df_neg(dfl a) { return dfl{-a.h, -a.l}; }
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return df_norm(p, e);
+}
+__device__ __forceinline__ dfl df_mulf(dfl a, float b) {
+  const float p = __fmul_rn(a.h, b);
+  float e = fmaf(a.h, b, -p);
+  e = fmaf(a.l, b, e);
+  return df_norm(p, e);
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  return df_norm(s, e + (a.l + b.l));
+}
+__device__ __forceinline__ dfl df_addf(dfl a, float b) {
+  float s, e;
+  two_sum(a.h, b, s, e);
+  return df_norm(s, e + a.l);
+}
+// 1 / a as a pair (one Newton correction of the correctly rounded reciprocal)
+__device__ __forceinline__ dfl df_recip(dfl a) {
+  const float h = __frcp_rn(a.h);
+  const float r = fmaf(-a.h, h, 1.0f) - __fmul_rn(a.l, h);
+  return df_norm(h, __fmul_rn(r, h));
+}
+// Running compensated sum s + c of pair products (Dot2): each product's
+// rounding error and each addition's error go to c.
+struct dacc {
+  float s, c;
+};
+__device__ __forceinline__ void dacc_fma(dacc &a, dfl x, dfl y) {
+  const float p = __fmul_rn(x.h, y.h);
+  float pe = fmaf(x.h, y.h, -p);
+  pe = fmaf(x.h, y.l, pe);
+  pe = fmaf(x.l, y.h, pe);
+  float t, e;
+  two_sum(a.s, p, t, e);
+  a.s = t;
+  a.c += e + pe;
+}
+__device__ __forceinline__ dfl dacc_get(const dacc &a) { return df_norm(a.s, a.c); }
 
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -216,7 +281,13 @@ struct CtaFit {
   static constexpr int TC_NKB = (GM == 3 || GM == 4) ? 2 : 4;
   static constexpr bool TC_X3 = GM == 2 || GM == 4;
   static constexpr int TC_BYTES = GM == 0 ? 0 : (TC_X3 ? 2 : 1) * TC_NKB * TS::NB_DES;
-  static constexpr int STAGE_BYTES = ROWS_BYTES > TC_BYTES ? ROWS_BYTES : TC_BYTES;
+  // accurate pass rows: the basis as (head, tail) pairs, then from DF_AO the
+  // pairs a = w r and b = w y r; stride an odd multiple of 4 floats
+  static constexpr int DF_AO = ((2 * NM + 3) / 4) * 4;
+  static constexpr int DF_LDD = ((DF_AO / 4 + 1) % 2 == 1) ? DF_AO + 4 : DF_AO + 8;
+  static constexpr int DF_BYTES = sizeof(Real) == 4 ? kT * DF_LDD * 4 : 0;
+  static constexpr int RB_BYTES = ROWS_BYTES > DF_BYTES ? ROWS_BYTES : DF_BYTES;
+  static constexpr int STAGE_BYTES = RB_BYTES > TC_BYTES ? RB_BYTES : TC_BYTES;
   // furthest byte the M = 128 A operand reads, from the start of `stage`
   static constexpr int TC_REACH = GM == 0 ? 0 : ((TC_X3 ? 2 : 1) * TC_NKB - 1) * TS::NB_DES + 16384;
   alignas(16) Real stage[STAGE_BYTES / sizeof(Real)];   // first member: 1024-byte aligned
@@ -240,19 +311,20 @@ struct CtaFit {
   alignas(16) float uvhi[2][NM];      // FP32 path: (c, u), (c, v) as head + tail
   alignas(16) float uvlo[2][NM];
   float uvphi[2][NM], uvplo[2][NM];   // previous
-  float fzhi[2][NM], fzlo[2][NM];     // FP32 path: the iterate whose residuals efz holds
-  alignas(16) float dfz[2][NM];       // the iterate minus that one
+  float2 uvq[2][NM];                  // accurate pass: the iterate (head, tail) interleaved
+  float mulo[NM];                     // FP32 path: tails of the exact sample means (mupsi: heads)
+  float hkd[3][NM][2];                // accurate pass: H, K and the basis sums as pairs
+  Real HKc[2][NM];                    // H_0, H_i - mu_i H_0 and K_0, K_i - mu_i K_0
   float redv[4][((2 * NM + 2 + 15) / 16) * 16];
   // sample cache (N, B0, B1, y) of fits with at most MC samples; none on the
   // FP32 degree-4 path, whose shared memory then admits 3 CTAs per SM
   static constexpr int MC = (sizeof(Real) == 4 && DMAX == 4 && GM == 0) ? 0 : kMC;
   float xs[4][MC > 0 ? MC : 1];
-  float efz[MC > 0 ? MC : 1];         // compensated residuals y q - p at fzhi + fzlo
   float redf[4][32];
   unsigned dslot[3][kMaxDeg + 1];
   uint32_t tmem_base;
-  long long next_fit[2];              // claimed fit indices (alternating slots)
-  int keep_cnt, keep_w, bad;
+  long long next_fit[2];              // claimed point-set indices (alternating slots)
+  int keep_cnt, keep_w, bad, set_deg;
   float fscal[4];
 };
 
@@ -559,6 +631,150 @@ __device__ float apply_step(S &w, int nm, int n) {
   return w.fscal[0];
 }
 
+// Accurate refinement pass of the FP32 paths (double-float arithmetic).
+// Every thread takes one sample of a 128-sample chunk (row phase):
+//   basis variable t_v = (x_v sc_v + of_v - mu_v) isg_v as a pair (the exact
+//   affine map of the FP32 constants that define the basis),
+//   Q_k(t_v) = sum_l Tm[l][k] t_v^l, Psi_j = Q_a Q_b Q_c (pairs),
+//   p = c_p + Psi.u, q = c_q + Psi.v (compensated dot products against the
+//   head + tail iterate), r = w (y q - p), a = w r, b = w y r (pairs),
+// and stages its row: the pairs (head, tail) of Psi_0.. interleaved, then a
+// and b at DF_AO (16-byte stores; the row stride is an odd multiple of 16
+// bytes, so 8 consecutive rows fill distinct banks).  Then thread (column,
+// group) adds a Psi_j (H_j), b Psi_j (K_j) and, on the first accurate pass,
+// Psi_j (the basis sums, for the exact sample means) over the group's rows
+// with Dot2 (column phase; 64-bit loads of the pairs).  Results: hkd[0..2][j]
+// (pairs, block totals), the objective sum r^2 and whether q <= 0 at some
+// sample.
+template <int DMAX, int NM, class S>
+__device__ void df_pass(S &w, int d, int nm, int m, bool weighted, bool first, const float *sx0,
+                        const float *sx1, const float *sx2, const float *sy, float &obj_out,
+                        int &pole_out) {
+  constexpr int LDD = S::DF_LDD, AO = S::DF_AO;
+  static_assert(AO % 4 == 0 && LDD % 4 == 0 && AO + 4 <= LDD && 2 * NM <= AO, "accurate pass rows");
+  const int tid = threadIdx.x;
+  float *stage = reinterpret_cast<float *>(w.stage);
+  // the iterate as interleaved pairs (one 64-bit broadcast load per term)
+  for (int e = tid; e < 2 * NM; e += kT) {
+    const int which = e / NM, i2 = e % NM;
+    w.uvq[which][i2] = make_float2(w.uvhi[which][i2], w.uvlo[which][i2]);
+  }
+  __syncthreads();
+  const int ncol = (first ? 3 : 2) * nm;
+  const int groups = max(1, kT / ncol);
+  const int col = tid % ncol, grp = tid / ncol;
+  const int which = col / nm, jc = col % nm;
+  const bool colw = tid < groups * ncol;
+  const int wo = which == 2 ? 0 : AO + 2 * which;   // weight pair of the column
+  dacc ca = {0.0f, 0.0f}, cb = {0.0f, 0.0f};        // two chains (alternate rows)
+  float obj = 0.0f;
+  int pole = 0;
+  for (int base = 0; base < m; base += kT) {
+    const int cnt = min(kT, m - base);
+    if (tid < cnt) {
+      const int i = base + tid;
+      const float xv[3] = {sx0[i], sx1[i], sx2[i]};
+      const float yy = sy[i];
+      dfl Q[3][DMAX + 1];
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        const float4 c = *reinterpret_cast<const float4 *>(&w.vc[v][0]);   // sc, of, mu, isg
+        const float ph = __fmul_rn(xv[v], c.x);
+        const float pl = fmaf(xv[v], c.x, -ph);
+        float s1, e1, s2, e2;
+        two_sum(ph, c.y, s1, e1);
+        two_sum(s1, -c.z, s2, e2);
+        const dfl t = df_mulf(df_norm(s2, e2 + (e1 + pl)), c.w);
+        dfl pw[DMAX + 1];
+        pw[1] = t;
+#pragma unroll
+        for (int l = 2; l <= DMAX; ++l) pw[l] = df_mul(pw[l - 1], t);
+        Q[v][0] = df_make(1.0f);
+#pragma unroll
+        for (int k = 1; k <= DMAX; ++k) {
+          dfl sk = df_make(w.Tm[v][0][k]);
+#pragma unroll
+          for (int l = 1; l <= k; ++l) sk = df_add(sk, df_mulf(pw[l], w.Tm[v][l][k]));
+          Q[v][k] = (k <= d) ? sk : df_make(0.0f);
+        }
+      }
+      float *row = stage + tid * LDD;
+      dacc P = {0.0f, 0.0f}, Qs = {0.0f, 0.0f};
+      float2 prev = make_float2(0.0f, 0.0f);
+      int j = 0;
+#pragma unroll
+      for (int sd = 0; sd <= DMAX; ++sd)
+#pragma unroll
+        for (int ea = sd; ea >= 0; --ea)
+#pragma unroll
+          for (int eb = sd - ea; eb >= 0; --eb, ++j) {
+            const int ec = sd - ea - eb;
+            dfl ps = df_make(1.0f);
+            if (ea) ps = Q[0][ea];
+            if (eb) ps = ea ? df_mul(ps, Q[1][eb]) : Q[1][eb];
+            if (ec) ps = (ea || eb) ? df_mul(ps, Q[2][ec]) : Q[2][ec];
+            if (j >= nm) ps = df_make(0.0f);
+            if (j & 1)
+              *reinterpret_cast<float4 *>(row + 2 * (j - 1)) = make_float4(prev.x, prev.y, ps.h, ps.l);
+            else
+              prev = make_float2(ps.h, ps.l);
+            const float2 u = w.uvq[0][j], v = w.uvq[1][j];
+            dacc_fma(P, dfl{u.x, u.y}, ps);
+            dacc_fma(Qs, dfl{v.x, v.y}, ps);
+          }
+      if (NM & 1) *reinterpret_cast<float4 *>(row + 2 * (NM - 1)) = make_float4(prev.x, prev.y, 0.0f, 0.0f);
+      const dfl pv = dacc_get(P), qv = dacc_get(Qs);
+      pole |= !(qv.h > 0.0f);
+      const dfl e = df_add(df_mulf(qv, yy), df_neg(pv));
+      dfl ra, rb, r;
+      if (weighted) {   // y > 0 here; w = 1 / y, so w y = 1
+        const dfl wt = df_recip(df_make(yy));
+        r = df_mul(wt, e);
+        ra = df_mul(wt, r);
+        rb = r;
+      } else {
+        r = e;
+        ra = e;
+        rb = df_mulf(e, yy);
+      }
+      obj = fmaf(r.h, r.h, obj);
+      *reinterpret_cast<float4 *>(row + AO) = make_float4(ra.h, ra.l, rb.h, rb.l);
+    }
+    __syncthreads();
+    if (colw) {
+      auto term = [&](dacc &acc, int s2) {
+        const float *rw = stage + s2 * LDD;
+        const float2 ps = *reinterpret_cast<const float2 *>(rw + 2 * jc);
+        const float2 wt = which == 2 ? make_float2(1.0f, 0.0f) : *reinterpret_cast<const float2 *>(rw + wo);
+        dacc_fma(acc, dfl{wt.x, wt.y}, dfl{ps.x, ps.y});
+      };
+      int s2 = grp;
+      for (; s2 + groups < cnt; s2 += 2 * groups) {
+        term(ca, s2);
+        term(cb, s2 + groups);
+      }
+      if (s2 < cnt) term(ca, s2);
+    }
+    __syncthreads();
+  }
+  // group partials -> block totals (pairs)
+  if (colw) {
+    const dfl t = df_add(dacc_get(ca), dacc_get(cb));
+    stage[2 * tid] = t.h;
+    stage[2 * tid + 1] = t.l;
+  }
+  __syncthreads();
+  if (tid < ncol) {
+    dfl t = dfl{stage[2 * tid], stage[2 * tid + 1]};
+    for (int g = 1; g < groups; ++g) t = df_add(t, dfl{stage[2 * (g * ncol + tid)], stage[2 * (g * ncol + tid) + 1]});
+    w.hkd[which][jc][0] = t.h;
+    w.hkd[which][jc][1] = t.l;
+  }
+  pole_out = __syncthreads_or(pole);
+  obj_out = block_sum_f(w, obj, 8);
+  __syncthreads();
+}
+
 // Tensor-core Gram X^T X of up to NPAD columns over 128-sample chunks: each
 // thread stages its sample's row (column j at row j of the K-major tile,
 // K slot = the thread), one thread issues the MMAs of the chunk's K-blocks
@@ -686,6 +902,10 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
   const uint32_t raw_s = tc::smem_u32(smem_raw);
   WF &w = *reinterpret_cast<WF *>(smem_raw + (GM > 0 ? (((raw_s + 1023u) & ~1023u) - raw_s) : 0u));
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // the FP64 pass over the fits passed on by an FP32 / tensor-core launch:
+  // nothing to do when none was (the count is final: same stream, earlier
+  // launch)
+  if (a.esc_mode == 2 && a.esc_count && *a.esc_count == 0ull) return;
   // tensor memory for the Gram accumulators, held for the whole launch
   uint32_t tmem = 0, tc_phase = 0;
   bool tc_dead = false;
@@ -700,125 +920,136 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
     tc::fence_after_sync();
     tmem = w.tmem_base;
   }
-  // fits are claimed from the workspace counter (CTAs that draw large fits
-  // take fewer), else every gridDim.x-th fit
-  int64_t f = blockIdx.x;
+  // Point sets are claimed from the workspace counter (CTAs that draw large
+  // sets take fewer), else every gridDim.x-th set.  A set is the fits that
+  // share one block of sample points (fits_per_set consecutive fits with a
+  // point_off array, else a single fit with its own points): phases 0-2
+  // (box, marginal polynomials, basis Gram and whitening) depend only on
+  // the points and run once per set, at the set's largest degree D; a fit
+  // of degree d < D uses the leading block of that basis (graded-lex order
+  // puts lower total degrees first and every factorisation of phases 1-2 is
+  // triangular, so the leading block is the degree-d basis itself).
+  const int64_t G = a.point_off ? (int64_t)a.fits_per_set : 1;
+  const int64_t nsets = (a.F + G - 1) / G;
+  int64_t ps = blockIdx.x;
   for (int claim = 0;; ++claim) {
     if (a.counter) {
       if (tid == 0) w.next_fit[claim & 1] = (long long)atomicAdd(a.counter, 1ull);
       __syncthreads();
-      f = w.next_fit[claim & 1];
+      ps = w.next_fit[claim & 1];
     } else if (claim > 0) {
-      f += gridDim.x;
+      ps += gridDim.x;
     }
-    if (f >= a.F) break;
-    // ---------------- phase 0: range, degree, validation, box, distinct values
-    const int64_t b0 = a.off[f], b1 = a.off[f + 1];
-    const int d = a.degs ? (int)a.degs[f] : a.d_uniform;
-    // a launch of a split batch takes only its degrees (invalid degrees go
-    // to the launch that starts at 1); the others' outputs are not touched
-    const bool valid_d = d >= 1 && d <= a.d_uniform;
-    if (valid_d ? (d < a.deg_lo || d > a.deg_hi) : a.deg_lo > 1) continue;
-    const bool range_ok = b0 >= 0 && b1 >= b0 && b1 <= a.S;
-    const int m = range_ok ? (int)(b1 - b0) : 0;
-    double *cf = a.coef + f * kStride;
-    for (int j = tid; j < kStride; j += kT) {
-      cf[j] = 0.0;
-      if (a.coef32) a.coef32[f * kStride + j] = 0.0f;
-    }
-    if (tid < 6) a.box[f * 6 + tid] = 0.0;
-    if (d < 1 || d > DMAX || m == 0) {
-      if (tid == 0) {
-        a.status[f] = RP_FIT_EMPTY;
-        a.rank[f] = 0;
+    if (ps >= nsets) break;
+    const int64_t f0 = ps * G, f1 = min(a.F, f0 + G);
+    // ---------------- phase 0: the set's fits in this launch and its degree
+    // (a launch of a split batch takes only its degrees; invalid degrees go
+    // to the launch that starts at 1; the others' outputs are not touched)
+    if (tid == 0) {
+      int D = 0, any = 0;
+      for (int64_t f = f0; f < f1; ++f) {
+        if (a.esc_mode == 2 && !(a.status[f] & kPending64)) continue;
+        const int d = a.degs ? (int)a.degs[f] : a.d_uniform;
+        const bool valid_d = d >= 1 && d <= a.d_uniform;
+        if (valid_d ? (d < a.deg_lo || d > a.deg_hi) : a.deg_lo > 1) continue;
+        any = 1;
+        if (valid_d && d <= DMAX) D = max(D, d);
       }
-      continue;
+      w.set_deg = any ? D : -1;
     }
-    const int nm = num_monomials(d);
-    const int nc = nm - 1;
-    const int naug = 2 * nm;
-    const int n = naug - 1;
+    __syncthreads();
+    const int D = w.set_deg;
+    if (D < 0) continue;
+    int64_t xb0, xb1, xS;
+    if (a.point_off) {
+      xb0 = a.point_off[ps];
+      xb1 = a.point_off[ps + 1];
+      xS = a.num_points;
+    } else {
+      xb0 = a.off[ps];
+      xb1 = a.off[ps + 1];
+      xS = a.S;
+    }
+    const bool prange_ok = xb0 >= 0 && xb1 >= xb0 && xb1 <= xS;
+    const int m = prange_ok ? (int)(xb1 - xb0) : 0;
     const bool cached = m <= WF::MC;
-    const float *gx0 = a.x + b0, *gx1 = a.x + a.S + b0, *gx2 = a.x + 2 * a.S + b0, *gy = a.y + b0;
-    if (tid < 3 * (kMaxDeg + 1)) (&w.dslot[0][0])[tid] = kEmpty;
-    if (tid == 0) w.bad = 0;
-    __syncthreads();
-    float lmin[3] = {INFINITY, INFINITY, INFINITY}, lmax[3] = {-INFINITY, -INFINITY, -INFINITY};
-    int bad = 0;
-    // loads (unrolled so that several samples' loads are in flight), the
-    // sample cache, validity and range; then the distinct values from the
-    // cached copy (the set's atomics would otherwise serialise the loads)
+    const float *gx0 = a.x + xb0, *gx1 = a.x + xS + xb0, *gx2 = a.x + 2 * xS + xb0;
+    // ---------------- phase 0: range, validation, box, distinct values of the points
+    int xbad = 0;
+    if (D >= 1 && m > 0) {
+      if (tid < 3 * (kMaxDeg + 1)) (&w.dslot[0][0])[tid] = kEmpty;
+      if (tid == 0) w.bad = 0;
+      __syncthreads();
+      float lmin[3] = {INFINITY, INFINITY, INFINITY}, lmax[3] = {-INFINITY, -INFINITY, -INFINITY};
+      int bad = 0;
+      // loads (unrolled so that several samples' loads are in flight), the
+      // sample cache, validity and range; then the distinct values from the
+      // cached copy (the set's atomics would otherwise serialise the loads)
 #pragma unroll 4
-    for (int i = tid; i < m; i += kT) {
-      const float v0 = __ldg(gx0 + i), v1 = __ldg(gx1 + i), v2 = __ldg(gx2 + i), yy = __ldg(gy + i);
-      if (cached) {
-        w.xs[0][i] = v0;
-        w.xs[1][i] = v1;
-        w.xs[2][i] = v2;
-        w.xs[3][i] = yy;
+      for (int i = tid; i < m; i += kT) {
+        const float v0 = __ldg(gx0 + i), v1 = __ldg(gx1 + i), v2 = __ldg(gx2 + i);
+        if (cached) {
+          w.xs[0][i] = v0;
+          w.xs[1][i] = v1;
+          w.xs[2][i] = v2;
+        }
+        if (!(isfinite(v0) && isfinite(v1) && isfinite(v2))) bad = 1;
+        lmin[0] = fminf(lmin[0], v0); lmax[0] = fmaxf(lmax[0], v0);
+        lmin[1] = fminf(lmin[1], v1); lmax[1] = fmaxf(lmax[1], v1);
+        lmin[2] = fminf(lmin[2], v2); lmax[2] = fmaxf(lmax[2], v2);
       }
-      if (!(isfinite(v0) && isfinite(v1) && isfinite(v2) && isfinite(yy))) bad |= RP_FIT_NONFINITE;
-      else if (a.weighted && !(yy > 0.0f)) bad |= RP_FIT_NONPOS_Y;
-      lmin[0] = fminf(lmin[0], v0); lmax[0] = fmaxf(lmax[0], v0);
-      lmin[1] = fminf(lmin[1], v1); lmax[1] = fmaxf(lmax[1], v1);
-      lmin[2] = fminf(lmin[2], v2); lmax[2] = fmaxf(lmax[2], v2);
-    }
-    for (int i = tid; i < m; i += kT) {
-      distinct_insert(w.dslot[0], cached ? w.xs[0][i] : gx0[i]);
-      distinct_insert(w.dslot[1], cached ? w.xs[1][i] : gx1[i]);
-      distinct_insert(w.dslot[2], cached ? w.xs[2][i] : gx2[i]);
-    }
-#pragma unroll
-    for (int v = 0; v < 3; ++v)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        lmin[v] = fminf(lmin[v], __shfl_xor_sync(0xffffffffu, lmin[v], o));
-        lmax[v] = fmaxf(lmax[v], __shfl_xor_sync(0xffffffffu, lmax[v], o));
+      for (int i = tid; i < m; i += kT) {
+        distinct_insert(w.dslot[0], cached ? w.xs[0][i] : gx0[i]);
+        distinct_insert(w.dslot[1], cached ? w.xs[1][i] : gx1[i]);
+        distinct_insert(w.dslot[2], cached ? w.xs[2][i] : gx2[i]);
       }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-    if (lane == 0) {
-      for (int v = 0; v < 3; ++v) {
-        w.redf[wid][v] = lmin[v];
-        w.redf[wid][3 + v] = lmax[v];
-      }
-      if (bad) atomicOr(&w.bad, bad);
-    }
-    __syncthreads();
-    if (w.bad) {
-      if (tid == 0) {
-        a.status[f] = (w.bad & RP_FIT_NONFINITE) ? RP_FIT_NONFINITE : RP_FIT_NONPOS_Y;
-        a.rank[f] = 0;
+      for (int v = 0; v < 3; ++v)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          lmin[v] = fminf(lmin[v], __shfl_xor_sync(0xffffffffu, lmin[v], o));
+          lmax[v] = fmaxf(lmax[v], __shfl_xor_sync(0xffffffffu, lmax[v], o));
+        }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+      if (lane == 0) {
+        for (int v = 0; v < 3; ++v) {
+          w.redf[wid][v] = lmin[v];
+          w.redf[wid][3 + v] = lmax[v];
+        }
+        if (bad) atomicOr(&w.bad, bad);
       }
       __syncthreads();
-      continue;
-    }
-    if (tid < 3) {
-      double mn = w.redf[0][tid], mx = w.redf[0][3 + tid];
-      for (int k = 1; k < 4; ++k) {
-        mn = fmin(mn, (double)w.redf[k][tid]);
-        mx = fmax(mx, (double)w.redf[k][3 + tid]);
+      xbad = w.bad;
+      if (!xbad && tid < 3) {
+        double mn = w.redf[0][tid], mx = w.redf[0][3 + tid];
+        for (int k = 1; k < 4; ++k) {
+          mn = fmin(mn, (double)w.redf[k][tid]);
+          mx = fmax(mx, (double)w.redf[k][3 + tid]);
+        }
+        w.lo[tid] = mn;
+        w.hi[tid] = mx;
+        if (mx > mn) {   // x' = 2 (x - lo) / (hi - lo) - 1 = x * sc + of
+          // in Real: the FP32 paths normalise in FP32, so FP32 sc and of (a
+          // consistent normalisation; lo and hi are kept exactly)
+          const Real sc = (Real)2 / (Real)(mx - mn);
+          w.sc_v[tid] = sc;
+          w.of_v[tid] = fma(-(Real)mn, sc, (Real)-1);
+        } else {
+          w.sc_v[tid] = 0;
+          w.of_v[tid] = 0;
+        }
       }
-      w.lo[tid] = mn;
-      w.hi[tid] = mx;
-      a.box[f * 6 + 2 * tid] = mn;
-      a.box[f * 6 + 2 * tid + 1] = mx;
-      if (mx > mn) {   // x' = 2 (x - lo) / (hi - lo) - 1 = x * sc + of
-        // in Real: the FP32 paths normalise in FP32, so FP32 sc and of (a
-        // consistent normalisation; lo and hi are kept exactly)
-        const Real sc = (Real)2 / (Real)(mx - mn);
-        w.sc_v[tid] = sc;
-        w.of_v[tid] = fma(-(Real)mn, sc, (Real)-1);
-      } else {
-        w.sc_v[tid] = 0;
-        w.of_v[tid] = 0;
-      }
+      __syncthreads();
     }
-    __syncthreads();
+    const bool basis_ok = D >= 1 && m > 0 && !xbad;
     const float *sx0 = cached ? w.xs[0] : gx0;
     const float *sx1 = cached ? w.xs[1] : gx1;
     const float *sx2 = cached ? w.xs[2] : gx2;
-    const float *sy = cached ? w.xs[3] : gy;
+    if (basis_ok) {
+    const int d = D;                       // phases 1-2: the set's degree
+    const int nm = num_monomials(d);
+    const int nc = nm - 1;
 
     // ---------------- phase 1: standardisation, marginal orthonormal polynomials
     {
@@ -932,7 +1163,10 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
 
       // means (row 0 holds the sums of Psi_j), the centred Gram / m of the
       // non-constant functions, equilibrated, in `stage`
-      for (int j = tid; j < NM; j += kT) w.mupsi[j] = (j < nm) ? w.G[j] / (Real)m : (Real)0;
+      for (int j = tid; j < NM; j += kT) {
+        w.mupsi[j] = (j < nm) ? w.G[j] / (Real)m : (Real)0;
+        w.mulo[j] = 0.0f;   // tails of the exact means: none known yet
+      }
       for (int e = tid; e < NM * WS; e += kT) w.W[e] = 0;
       __syncthreads();
       // the centred Gram / m of the non-constant functions, equilibrated, in
@@ -967,6 +1201,77 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
       }
       __syncthreads();
     }
+
+    }   // phases 1-2
+
+    // ---------------- each fit of the set: its values, then phases 3-6
+    int mu_known = 0;   // basis functions [0, mu_known) have exact sample means
+    for (int64_t f = f0; f < f1; ++f) {
+    if (a.esc_mode == 2) {
+      const bool pend = (a.status[f] & kPending64) != 0;
+      __syncthreads();   // every thread has read status[f] before it is rewritten
+      if (!pend) continue;
+    }
+    const int d = a.degs ? (int)a.degs[f] : a.d_uniform;
+    const bool valid_d = d >= 1 && d <= a.d_uniform;
+    if (valid_d ? (d < a.deg_lo || d > a.deg_hi) : a.deg_lo > 1) continue;
+    double *cf = a.coef + f * kStride;
+    for (int j = tid; j < kStride; j += kT) {
+      cf[j] = 0.0;
+      if (a.coef32) a.coef32[f * kStride + j] = 0.0f;
+    }
+    if (tid < 6) a.box[f * 6 + tid] = 0.0;
+    // the fit's values, one per point of its set
+    const int64_t yb0 = a.off[f], yb1 = a.off[f + 1];
+    const bool yrange_ok = yb0 >= 0 && yb1 >= yb0 && yb1 <= a.S && yb1 - yb0 == (int64_t)m;
+    if (d < 1 || d > DMAX || m == 0 || !yrange_ok) {
+      if (tid == 0) {
+        a.status[f] = RP_FIT_EMPTY;
+        a.rank[f] = 0;
+      }
+      continue;
+    }
+    if (xbad) {
+      if (tid == 0) {
+        a.status[f] = RP_FIT_NONFINITE;
+        a.rank[f] = 0;
+      }
+      continue;
+    }
+    // ---------------- phase 0 (values): load, cache, validate
+    const float *gy = a.y + yb0;
+    if (tid == 0) w.bad = 0;
+    __syncthreads();
+    {
+      int bad = 0;
+#pragma unroll 4
+      for (int i = tid; i < m; i += kT) {
+        const float yy = __ldg(gy + i);
+        if (cached) w.xs[3][i] = yy;
+        if (!isfinite(yy)) bad |= RP_FIT_NONFINITE;
+        else if (a.weighted && !(yy > 0.0f)) bad |= RP_FIT_NONPOS_Y;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+      if (lane == 0 && bad) atomicOr(&w.bad, bad);
+    }
+    __syncthreads();
+    if (w.bad) {
+      if (tid == 0) {
+        a.status[f] = (w.bad & RP_FIT_NONFINITE) ? RP_FIT_NONFINITE : RP_FIT_NONPOS_Y;
+        a.rank[f] = 0;
+      }
+      __syncthreads();
+      continue;
+    }
+    if (tid < 3) {
+      a.box[f * 6 + 2 * tid] = w.lo[tid];
+      a.box[f * 6 + 2 * tid + 1] = w.hi[tid];
+    }
+    const float *sy = cached ? w.xs[3] : gy;
+    const int nm = num_monomials(d);
+    const int naug = 2 * nm;
+    const int n = naug - 1;
 
     // Phases 3-5, attempted first with the tensor-core design Gram (GM > 0)
     // and, for a fit whose refinement stops short of its tolerance or whose
@@ -1150,49 +1455,83 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
     // ---------------- phase 5: refinement from the samples.
     // The iterate is the function pair p = c_p + psi.u, q = c_q + psi.v in
     // the unwhitened basis; each pass computes at every sample the design
-    // residual r = w (y q - p) (plain FP32, then Ogita-Rump-Oishi Dot2
-    // against the head + tail iterate once the steps fall below 1e-4
-    // relative; FP64 on the FP64 path), the objective sum r^2, whether
-    // q > 0, and H_i = sum (w r) psi_i, K_i = sum (w y r) psi_i.  The
-    // normal-equation residual in the design basis is
+    // residual r = w (y q - p), the objective sum r^2, whether q > 0, and
+    // H_i = sum (w r) psi_i, K_i = sum (w y r) psi_i.  FP32 paths: plain
+    // FP32 passes while the steps are large, then accurate passes (df_pass,
+    // double-float; the first of them also computes the exact sample means
+    // mu_i of the basis and rescales the iterate so that q averages to 1
+    // over the samples exactly); FP64 path: FP64 passes.  With the mu_i of
+    // the pass, the normal-equation residual in the design basis is
     //   g_num_0 = H_0, g_num_j = sum_{i<=j} W_ij (H_i - mu_i H_0),
     //   g_den_j = -sum_{i<=j} W_ij (K_i - mu_i K_0),
-    // and the step dx = Q g.  A step that raises the objective beyond its
-    // rounding level is undone and the refinement stops.
+    // and the step dx = Q g.  A step that raises the objective is undone and
+    // retried at half length.  The refinement stops once an accurate pass's
+    // step, times the contraction estimated from the steps, is at most tol
+    // relative (or such steps stop shrinking: their rounding floor), or
+    // after max_refine steps.
     flags = (w.keep_cnt < n) ? RP_FIT_RANK_DEFICIENT : 0;
-    float prev_rel = INFINITY, obj_prev = INFINITY, obj_drop = INFINITY;
-    bool compensated = sizeof(Real) == 8, done = false;
-    // FP32 paths, cached samples: the first compensated pass keeps each
-    // sample's Dot2 residual e_f = y q_f - p_f at that pass's iterate x_f;
-    // later passes take e(x) = e_f + (y psi.dv - psi.du) with (du, dv) =
-    // x - x_f, small enough for plain FP32 (one Dot2 pass per fit)
-    const bool can_freeze = sizeof(Real) == 4 && cached;
-    bool frozen = false;
-    int pole_prev = 0, it = 0;
+    float prev_rel = INFINITY, obj_prev = INFINITY;
+    bool accurate = sizeof(Real) == 8, prev_accurate = false, done = false;
+    // exact means of the set's basis carry over from the set's earlier fits
+    bool have_mu = mu_known >= nm;
+    int pole_prev = 0, it = 0, acc_passes = 0;
     float omega = 1.0f;   // step length (halved after an objective increase)
+    float contr = 1.0f;   // estimated contraction per step
     constexpr bool kRegAcc = sizeof(Real) == 4 && DMAX <= 3;
     constexpr int VP = ((2 * NM + 2 + 15) / 16) * 16;   // register accumulators
     const int hk_groups = max(1, kT / nm);
     for (;; ++it) {
       const bool update = it < a.max_refine && !done;
-      const bool freezing = can_freeze && compensated && !frozen;
-      if (freezing) {
-        for (int e = tid; e < 2 * NM; e += kT) {
-          const int which = e / NM, i2 = e % NM;
-          w.fzhi[which][i2] = w.uvhi[which][i2];
-          w.fzlo[which][i2] = w.uvlo[which][i2];
-        }
-      } else if (frozen) {
-        for (int e = tid; e < 2 * NM; e += kT) {
-          const int which = e / NM, i2 = e % NM;
-          w.dfz[which][i2] = (w.uvhi[which][i2] - w.fzhi[which][i2]) +
-                             (w.uvlo[which][i2] - w.fzlo[which][i2]);
-        }
-        __syncthreads();
-      }
-      Real hk0 = 0, hk1 = 0;    // staged path: this thread's column partials
+      const bool dfp = sizeof(Real) == 4 && accurate;
+      const bool first_df = dfp && !have_mu;
       float obj = 0.0f;
       int pole = 0;
+      if (dfp) {
+        if constexpr (sizeof(Real) == 4)
+          df_pass<DMAX, NM>(w, d, nm, m, a.weighted != 0, first_df, sx0, sx1, sx2, sy, obj, pole);
+        ++acc_passes;
+        if (first_df) {
+          // exact sample means mu_j = S_j / m (pairs; mu_0 = 1), then the
+          // iterate, the sums and the objective scaled by 1 / mean(q), with
+          // mean(q) = sum_j mu_j V_j (V: the denominator's coefficients)
+          if (wid == 0) {
+            const float mh = (float)m;
+            const dfl rm = df_recip(df_make(mh));
+            dfl t = df_make(0.0f);
+            for (int j2 = lane; j2 < nm; j2 += 32) {
+              const dfl mu = df_mul(dfl{w.hkd[2][j2][0], w.hkd[2][j2][1]}, rm);
+              w.mupsi[j2] = mu.h;
+              w.mulo[j2] = mu.l;
+              t = df_add(t, df_mul(mu, dfl{w.uvhi[1][j2], w.uvlo[1][j2]}));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+              t = df_add(t, dfl{__shfl_xor_sync(0xffffffffu, t.h, o), __shfl_xor_sync(0xffffffffu, t.l, o)});
+            if (lane == 0) {
+              const dfl sc = df_recip(t);
+              w.fscal[1] = sc.h;
+              w.fscal[2] = sc.l;
+            }
+          }
+          __syncthreads();
+          const dfl sc = dfl{w.fscal[1], w.fscal[2]};
+          for (int e = tid; e < 2 * NM; e += kT) {
+            const int which = e / NM, i2 = e % NM;
+            const dfl u = df_mul(dfl{w.uvhi[which][i2], w.uvlo[which][i2]}, sc);
+            w.uvhi[which][i2] = u.h;
+            w.uvlo[which][i2] = u.l;
+            const dfl hk = df_mul(dfl{w.hkd[which][i2][0], w.hkd[which][i2][1]}, sc);
+            w.hkd[which][i2][0] = hk.h;
+            w.hkd[which][i2][1] = hk.l;
+          }
+          for (int j2 = tid; j2 < n; j2 += kT) w.xw[j2] *= (Real)sc.h;
+          obj *= sc.h * sc.h;
+          have_mu = true;
+          mu_known = nm;
+          __syncthreads();
+        }
+      } else {
+      Real hk0 = 0, hk1 = 0;    // staged path: this thread's column partials
       float acc[kRegAcc ? VP : 1];
 #pragma unroll
       for (int j = 0; j < (kRegAcc ? VP : 1); ++j) acc[j] = 0.0f;
@@ -1216,58 +1555,17 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
             pole |= !(q > 0.0);
             r = wt * (yy * q - p);
           } else {
-            float hq[NM];
+            float hq[NM], hp[NM];
             ld_row<NM>(w.uvhi[1], hq);
-            float qf = hq[0];
+            ld_row<NM>(w.uvhi[0], hp);
+            float qf = hq[0], p = hp[0];
 #pragma unroll
-            for (int j2 = 1; j2 < NM; ++j2) qf = fmaf(psi[j2], hq[j2], qf);
-            pole |= !(qf > 0.0f);
-            if (frozen) {
-              float dv[NM], du[NM];
-              ld_row<NM>(w.dfz[1], dv);
-              ld_row<NM>(w.dfz[0], du);
-              float dq = dv[0], dp = du[0];
-#pragma unroll
-              for (int j2 = 1; j2 < NM; ++j2) {
-                dq = fmaf(psi[j2], dv[j2], dq);
-                dp = fmaf(psi[j2], du[j2], dp);
-              }
-              r = wt * (w.efz[i] + fmaf(yy, dq, -dp));
-            } else if (compensated) {
-              // e = y q - p = sum_j (y psi_j) v_j - psi_j u_j (psi_0 = 1):
-              // Dot2 against the head + tail iterate, two independent chains
-              float hp[NM], lq[NM], lp[NM];
-              ld_row<NM>(w.uvhi[0], hp);
-              ld_row<NM>(w.uvlo[1], lq);
-              ld_row<NM>(w.uvlo[0], lp);
-              float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
-#pragma unroll
-              for (int j2 = 0; j2 < NM; ++j2) {
-                const float av = yy * psi[j2], bv = -psi[j2];
-                const float pr0 = av * hq[j2], pr1 = bv * hp[j2];
-                const float pe0 = fmaf(av, hq[j2], -pr0);
-                const float pe1 = fmaf(bv, hp[j2], -pr1);
-                float t0, e0, t1, e1;
-                two_sum(s0, pr0, t0, e0);
-                two_sum(s1, pr1, t1, e1);
-                s0 = t0;
-                s1 = t1;
-                c0 += e0 + pe0 + av * lq[j2];
-                c1 += e1 + pe1 + bv * lp[j2];
-              }
-              float t, e;
-              two_sum(s0, s1, t, e);
-              const float ef = t + (e + c0 + c1);
-              if (freezing) w.efz[i] = ef;
-              r = wt * ef;
-            } else {
-              float hp[NM];
-              ld_row<NM>(w.uvhi[0], hp);
-              float p = hp[0];
-#pragma unroll
-              for (int j2 = 1; j2 < NM; ++j2) p = fmaf(psi[j2], hp[j2], p);
-              r = wt * fmaf(yy, qf, -p);
+            for (int j2 = 1; j2 < NM; ++j2) {
+              qf = fmaf(psi[j2], hq[j2], qf);
+              p = fmaf(psi[j2], hp[j2], p);
             }
+            pole |= !(qf > 0.0f);
+            r = wt * fmaf(yy, qf, -p);
           }
           obj += (float)(r * r);
           if constexpr (kRegAcc) {
@@ -1319,13 +1617,36 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
         obj = w.redv[0][2 * NM] + w.redv[1][2 * NM] + w.redv[2][2 * NM] + w.redv[3][2 * NM];
         pole = (w.redv[0][2 * NM + 1] + w.redv[1][2 * NM + 1] + w.redv[2][2 * NM + 1] +
                 w.redv[3][2 * NM + 1]) > 0.0f;
+        if (update && tid < 2 * NM) {
+          const Real v = w.redv[0][tid] + w.redv[1][tid] + w.redv[2][tid] + w.redv[3][tid];
+          w.HK[tid / NM][tid % NM] = v;
+        }
       } else {
         pole = __syncthreads_or(pole);
         obj = block_sum_f(w, obj, 8);
+        if (update) {
+          __syncthreads();
+          if (tid < nm * hk_groups) {
+            w.stage[tid] = hk0;
+            w.stage[kT + tid] = hk1;
+          }
+          __syncthreads();
+          if (tid < nm) {
+            Real h = 0, k2 = 0;
+            for (int g = 0; g < hk_groups; ++g) {
+              h += w.stage[g * nm + tid];
+              k2 += w.stage[kT + g * nm + tid];
+            }
+            w.HK[0][tid] = h;
+            w.HK[1][tid] = k2;
+          }
+        }
       }
       __syncthreads();
-      if (freezing) frozen = true;
-      const bool worse = it > 0 && obj > obj_prev * (compensated ? 1.00001f : 1.0001f);
+      }   // plain pass
+      // (the first accurate pass starts a new comparison: its iterate was
+      // rescaled and its objective is exact)
+      const bool worse = it > 0 && !first_df && obj > obj_prev * (accurate ? 1.00001f : 1.0001f);
       if (worse) {
         // the last step increased the objective: undo it, then retry it at
         // half length (a preconditioner that overestimates curvature in some
@@ -1341,7 +1662,6 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
         omega *= 0.5f;
         if (omega < 0.0625f || it >= a.max_refine) {
           pole = pole_prev;
-          obj_drop = 0.0f;
           __syncthreads();
           break;
         }
@@ -1350,7 +1670,6 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
         (void)apply_step<Real, NM, WS>(w, nm, n);
         continue;
       }
-      if (it > 0) obj_drop = (obj_prev - obj) / fmaxf(obj_prev, 1e-30f);
       for (int e = tid; e < 2 * NM; e += kT) {
         const int which = e / NM, i2 = e % NM;
         w.uvp[which][i2] = w.uv[which][i2];
@@ -1364,27 +1683,23 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
         __syncthreads();
         break;
       }
-      // H, K
-      if constexpr (kRegAcc) {
-        if (tid < 2 * NM) {
-          const Real v = w.redv[0][tid] + w.redv[1][tid] + w.redv[2][tid] + w.redv[3][tid];
-          w.HK[tid / NM][tid % NM] = v;
-        }
-      } else {
-        if (tid < nm * hk_groups) {
-          w.stage[tid] = hk0;
-          w.stage[kT + tid] = hk1;
-        }
-        __syncthreads();
-        if (tid < nm) {
-          Real h = 0, k2 = 0;
-          for (int g = 0; g < hk_groups; ++g) {
-            h += w.stage[g * nm + tid];
-            k2 += w.stage[kT + g * nm + tid];
+      // centred sums H_0, H_i - mu_i H_0 and K_0, K_i - mu_i K_0 (pairs on
+      // an accurate pass: the fixed point K_i = mu_i K_0 carries the
+      // normalisation, so mu_i K_0 is formed to the pass's accuracy)
+      for (int e = tid; e < 2 * NM; e += kT) {
+        const int which = e / NM, i2 = e % NM;
+        Real v = 0;
+        if (i2 < nm) {
+          if (dfp) {
+            const dfl h0 = dfl{w.hkd[which][0][0], w.hkd[which][0][1]};
+            const dfl hi = dfl{w.hkd[which][i2][0], w.hkd[which][i2][1]};
+            const dfl c = i2 == 0 ? h0 : df_add(hi, df_neg(df_mul(dfl{(float)w.mupsi[i2], w.mulo[i2]}, h0)));
+            v = (Real)c.h;
+          } else {
+            v = i2 == 0 ? w.HK[which][0] : w.HK[which][i2] - w.mupsi[i2] * w.HK[which][0];
           }
-          w.HK[0][tid] = h;
-          w.HK[1][tid] = k2;
         }
+        w.HKc[which][i2] = v;
       }
       __syncthreads();
       // g, then the step dx = Q g
@@ -1392,15 +1707,15 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
         Real g;
         if (e < nm) {
           if (e == 0) {
-            g = w.HK[0][0];
+            g = w.HKc[0][0];
           } else {
             g = 0;
-            for (int i2 = 1; i2 <= e; ++i2) g = fma(w.W[i2 * WS + e], w.HK[0][i2] - w.mupsi[i2] * w.HK[0][0], g);
+            for (int i2 = 1; i2 <= e; ++i2) g = fma(w.W[i2 * WS + e], w.HKc[0][i2], g);
           }
         } else {
           const int jd = e - nm + 1;
           g = 0;
-          for (int i2 = 1; i2 <= jd; ++i2) g = fma(-w.W[i2 * WS + jd], w.HK[1][i2] - w.mupsi[i2] * w.HK[1][0], g);
+          for (int i2 = 1; i2 <= jd; ++i2) g = fma(-w.W[i2 * WS + jd], w.HKc[1][i2], g);
         }
         w.gvec[e] = g;
       }
@@ -1413,12 +1728,27 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
       }
       __syncthreads();
       const float rel = apply_step<Real, NM, WS>(w, nm, n);
-      const bool was_compensated = compensated;
-      if (!compensated && rel < 1e-4f) compensated = true;
-      // stop at tol, or once compensated corrections stop shrinking (the
-      // residuals' noise floor)
-      if (rel <= (float)a.tol || (was_compensated && rel > 0.9f * prev_rel)) done = true;
+      // contraction of the preconditioned iteration, estimated from the
+      // steps: the first step's relative size (the error of the factor's
+      // solution) and the ratios of later steps while they are above the
+      // FP32 rounding floor (plain passes) or of successive accurate steps
+      const bool was_accurate = accurate;
+      if (it == 0) contr = rel;
+      else if (was_accurate ? prev_accurate : rel > 1e-5f) contr = fmaxf(contr, rel / prev_rel);
+      // accurate from here on once the plain steps are small, stop
+      // shrinking (the FP32 rounding floor), or the budget nears its end
+      if (!accurate && (rel < 1e-4f || (it > 0 && rel > 0.5f * prev_rel) || it + 2 >= a.max_refine))
+        accurate = true;
+      // stop once an accurate step leaves an estimated relative error
+      // (contraction x step, the contraction taken as at least 1e-3) of at
+      // most tol, or once accurate corrections stop shrinking at their
+      // rounding floor (below 1e-8 relative: above it, slow shrinking is a
+      // weak preconditioner's contraction, and the refinement goes on)
+      if (was_accurate && (fminf(fmaxf(contr, 1e-3f), 1.0f) * rel <= (float)a.tol ||
+                           (prev_accurate && rel > 0.9f * prev_rel && rel < 1e-8f)))
+        done = true;
       prev_rel = rel;
+      prev_accurate = was_accurate;
       if (done) {
         // converged: the last correction is below tol (or at the residuals'
         // noise floor); it is kept without another evaluation pass
@@ -1427,10 +1757,11 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
       }
     }
     flags |= (pole_prev ? RP_FIT_POLE : 0);
-    // not converged: the iteration cap was hit while the objective was still
-    // falling by more than 1e-5 per step
-    if (a.max_refine > 0 && !done && !(obj_drop <= 1e-5f)) flags |= RP_FIT_NOT_CONVERGED;
+    // not converged: the refinement ended (max_refine steps, or steps that
+    // kept raising the objective) before its stop test was met
+    if (a.max_refine > 0 && !done) flags |= RP_FIT_NOT_CONVERGED;
     flags |= min(it, 255) << RP_FIT_ITER_SHIFT;
+    flags |= min(acc_passes, 255) << RP_FIT_ACC_SHIFT;
     if (use_tc && a.max_refine > 0 && (!done || (flags & RP_FIT_RANK_DEFICIENT))) {
       escalated = true;
       continue;
@@ -1458,17 +1789,23 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
                                        : (double)w.uvhi[which][i] + (double)w.uvlo[which][i];
       }
       if (tid >= kT - 3 * (kMaxDeg + 1) * (kMaxDeg + 1) + 0 && tid < kT) {
-        // P[v][k][i]: coefficient of x'^i in Q_k(u), u = (x' - mu) isg, one
-        // entry per thread: sum_{l=i..k} Tm[l][k] C(l, i) isg^l (-mu)^(l-i)
+        // P[v][k][i]: coefficient of x'^i in Q_k(u) for the box-normalised
+        // x' = 2 (x - lo) / (hi - lo) - 1, where the basis variable is
+        // u = (x sc + of - mu) isg with the kernel's own constants, i.e.
+        // u = A x' + B, A = isg sc (hi - lo) / 2, B = isg (sc (hi + lo) / 2 + of - mu)
+        // (exactly the map the accurate passes evaluate); one entry per
+        // thread: sum_{l=i..k} Tm[l][k] C(l, i) A^i B^(l-i)
         const int e = tid - (kT - 3 * (kMaxDeg + 1) * (kMaxDeg + 1));
         const int v = e / ((kMaxDeg + 1) * (kMaxDeg + 1));
         const int k = (e / (kMaxDeg + 1)) % (kMaxDeg + 1), i = e % (kMaxDeg + 1);
-        const double mu = w.mu_v[v], isg = w.isg_v[v];
+        const double isg = w.isg_v[v], scv = w.sc_v[v];
+        const double A = isg * scv * (w.hi[v] - w.lo[v]) * 0.5;
+        const double B = isg * (scv * (w.hi[v] + w.lo[v]) * 0.5 + (double)w.of_v[v] - (double)w.mu_v[v]);
         double acc = 0.0;
         if (k <= d && i <= k) {
-          double pw = 1.0;   // isg^l (-mu)^(l - i), starting at l = i
-          for (int l = 0; l < i; ++l) pw *= isg;
-          const double step = -mu * isg;
+          double pw = 1.0;   // A^i B^(l - i), starting at l = i
+          for (int l = 0; l < i; ++l) pw *= A;
+          const double step = B;
           int binom = 1;     // C(l, i), starting at C(i, i)
           for (int l = i; l <= k; ++l) {
             acc = fma((double)w.Tm[v][l][k] * (double)binom, pw, acc);
@@ -1509,11 +1846,20 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
         if (a.coef32) a.coef32[f * kStride + o] = (float)s;
       }
       if (tid == 0) {
-        a.status[f] = flags;
+        int32_t st = flags;
+        if (a.esc_mode == 2) st |= RP_FIT_FP64_PASS;
+        // dropped pivots or refinement short of tol: solved again on the
+        // FP64 path by the launch that follows
+        if (a.esc_mode == 1 && a.max_refine > 0 && (flags & (RP_FIT_RANK_DEFICIENT | RP_FIT_NOT_CONVERGED))) {
+          st |= kPending64;
+          if (a.esc_count) atomicAdd(a.esc_count, 1ull);
+        }
+        a.status[f] = st;
         a.rank[f] = w.keep_cnt;
       }
       __syncthreads();
     }
+    }   // fits of the set
   }
   if constexpr (GM > 0) {
     // after a wait that gave up, wait (bounded) once more for the MMAs still
@@ -1592,7 +1938,8 @@ cudaError_t launch_t(const FitArgs &a, int precision, cudaStream_t s) {
   const int cap = fit_ctas_cap(precision, DMAX);
   if (cap > 0 && cap < per_sm) per_sm = cap;
   int64_t grid = (int64_t)num_sms() * per_sm;
-  if (grid > a.F) grid = a.F;
+  const int64_t nsets = a.point_off ? (a.F + a.fits_per_set - 1) / a.fits_per_set : a.F;
+  if (grid > nsets) grid = nsets;
   if (a.counter) {
     e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;

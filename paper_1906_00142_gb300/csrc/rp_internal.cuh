@@ -61,9 +61,17 @@ cudaError_t launch_pack(int64_t K, int d, const double *coef, const double *box,
 // workspace: NULL (queries in input order) or search_workspace_bytes(K, Q)
 // bytes, 16-byte aligned (queries bucketed by kernel first); ignored when
 // search_workspace_bytes is 0.
+// tie_rel >= 0: Step 5's second-metric choice among the configurations within
+// (1 + tie_rel) of the best (the most active warps; lowest index among equals).
 cudaError_t launch_search(ProgramView prog, int64_t K, int d, const rp_hw_fixed &hw,
                           const float *queries, int64_t Q, int32_t *argmin, float *best,
-                          float *second, int32_t *status, void *workspace, cudaStream_t s);
+                          float *second, int32_t *status, void *workspace, cudaStream_t s,
+                          float tie_rel = -1.0f);
+cudaError_t launch_occupancy(ProgramView prog, int64_t K, int d, const rp_hw_fixed &hw,
+                             const float *queries, int64_t Q, int32_t *b_active, int32_t *w_active,
+                             int32_t *status, cudaStream_t s);
+cudaError_t launch_error_pct(const float *runtimes, const int32_t *choice, int64_t Q,
+                             float *err_pct, int32_t *status, cudaStream_t s);
 size_t search_workspace_bytes(int64_t K, int64_t Q);
 
 cudaError_t launch_fit(const rp_fit_desc &desc, const float *x, const float *y,

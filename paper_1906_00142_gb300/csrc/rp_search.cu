@@ -214,6 +214,132 @@ __device__ __forceinline__ void load_row(const float *__restrict__ p, float (&c)
   }
 }
 
+// The per-query state of the evaluation: the query's scalars and its
+// kernel's normalised data parameter per metric.
+struct QState {
+  float fghz, memld, bw, ddc, ddu;
+  float t[kNmet];
+  uint32_t Ni, nsm_i;
+  bool grid1;
+};
+
+// Validates the query and sets up its state; false: a bad query (RP_Q_BAD).
+template <bool SH>
+__device__ __forceinline__ bool query_state(const float4 q0, const float4 q1, bool kid_ok,
+                                            const float *aN8, const float *bN8, int32_t grid,
+                                            QState &s) {
+  const float N = q0.x, nsm = q0.y;
+  s.fghz = q0.z; s.memld = q0.w;
+  s.bw = q1.x; s.ddc = q1.y; s.ddu = q1.z;
+  const bool finite = isfinite(N) && isfinite(nsm) && isfinite(s.fghz) && isfinite(s.memld) &&
+                      isfinite(s.bw) && isfinite(s.ddc) && isfinite(s.ddu);
+  if (!finite || !kid_ok || !(N >= 1.0f) || !(nsm >= 1.0f) || !(s.fghz > 0.0f) ||
+      !(s.bw > 0.0f) || !(s.memld >= 0.0f) || !(s.ddc >= 0.0f) || !(s.ddu >= 0.0f) ||
+      !(N <= 4294967040.0f) || !(nsm <= 1048576.0f))
+    return false;
+#pragma unroll
+  for (int m = 0; m < kNmet; ++m) s.t[m] = fmaf(ld1<SH>(aN8 + m), N, ld1<SH>(bN8 + m));
+  s.Ni = (uint32_t)ceilf(N);
+  s.nsm_i = (uint32_t)nsm;
+  s.grid1 = grid == 1;
+  return true;
+}
+
+// One configuration c of one query, branch-free: the execution cycles (+inf
+// for an invalid or pole configuration), whether a metric's denominator was
+// <= 0 (pole), and the occupancy B_active, W_active (0 when not resident).
+// The same operations, in the same order, as eval_query's loop body (which
+// keeps its own copy: factored out, it costs the benchmarked kernel register
+// spills); the tie-break and occupancy tests check that the two agree bit
+// for bit.
+struct CfgOut {
+  float ex;
+  bool pole;
+  int bact, nw;
+};
+template <int D1, bool SH, bool OCC = false>
+__device__ __forceinline__ CfgOut eval_cfg(int c, const QState &s, const float *tab,
+                                           const CfgTab &cfg, const HwC &hw) {
+  float mv[kNmet];
+  unsigned dbits = 0u;
+  const float *row = tab + c * kNmet * 2 * D1;
+#pragma unroll
+  for (int m = 0; m < kNmet; ++m) {
+    float cf[2 * D1];
+    load_row<D1, SH>(row + m * 2 * D1, cf);
+    float p = cf[D1 - 1], d = cf[2 * D1 - 1];
+#pragma unroll
+    for (int j = D1 - 2; j >= 0; --j) {
+      p = fmaf(p, s.t[m], cf[j]);
+      d = fmaf(d, s.t[m], cf[D1 + j]);
+    }
+    // 0 < d < 8.5e37 (NaN excluded) <=> bits(d) - 1 < bits(8.5e37) - 1,
+    // unsigned: one running maximum instead of two compares per metric
+    dbits = max(dbits, __float_as_uint(d) - 1u);
+    mv[m] = __fdividef(p, d);
+  }
+  const float comp = fmaxf(mv[0], 0.0f), Cm = fmaxf(mv[1], 0.0f),
+              U = fmaxf(mv[2], 0.0f), upm = fmaxf(mv[3], 1.0f),
+              synch = fmaxf(mv[4], 0.0f), lbw = fmaxf(mv[5], 0.0f);
+  // clamped at 2^24: above every admissible R_SM / Z_SM (< 2^24), so
+  // the configuration is invalid either way
+  const float Rf = fminf(fmaxf(mv[6], 0.0f), 16777216.0f);
+  const float Zf = fminf(fmaxf(mv[7], 0.0f), 16777216.0f);
+  const int Ri = (int)floorf(Rf + 0.5f), Zi = (int)floorf(Zf + 0.5f);
+  const bool pole = dbits >= __float_as_uint(8.5e37f) - 1u;
+  const int la = cfg.la[c], lb = cfg.lb[c];
+  const int wpb = cfg.wpb[c];
+  // floor(R_SM / (R wpb warp)) = floor(floor(R_SM / (wpb warp)) / R)
+  const int tR = floor_div_small(cfg.rsm_w[c], max(Ri, 1));
+  const int tZ = floor_div_small(hw.zsm, max(Zi, 1));
+  int bact = cfg.bact_w[c];
+  bact = Ri > 0 ? min(bact, tR) : bact;
+  bact = Zi > 0 ? min(bact, tZ) : bact;
+  const bool valid = !pole && bact > 0 && Ri <= cfg.rsm_t[c] && Zi <= hw.zsm;
+  const int bact_out = OCC ? (valid ? bact : 0) : 0;
+  bact = max(bact, 1);
+  const int nw_i = min(bact * wpb, hw.wmax);
+  const float Nw = (float)nw_i;
+  // ceil(N / 2^s) = ((N - 1) >> s) + 1 for N >= 1
+  const uint32_t c0 = ((s.Ni - 1u) >> (s.grid1 ? la + lb : la)) + 1u;
+  const uint32_t c1 = s.grid1 ? 1u : ((s.Ni - 1u) >> lb) + 1u;
+  // fewer blocks than SMs (decided exactly in FP32: below 2^24 the
+  // product is exact, above it is >= 2^24 > SMs): every block runs in
+  // one round, #Rep = 1
+  const float blocks = (float)c0 * (float)c1;
+  const bool few = blocks < (float)s.nsm_i;
+  const float asm_ = few ? blocks : (float)s.nsm_i;
+  const float rep = few ? 1.0f : rep_count(c0, c1, (uint32_t)bact * s.nsm_i);
+  const float mem_insts = U + Cm;
+  const float comp_cycles = hw.issue * (comp + mem_insts);
+  const bool has_mem = mem_insts > 0.0f;
+  const float inv_mi = has_mem ? __fdividef(1.0f, mem_insts) : 0.0f;
+  const float wu = U * inv_mi, wc = Cm * inv_mi;
+  const float ml_unc = fmaf(upm - 1.0f, s.ddu, s.memld);
+  const float ml = fmaf(ml_unc, wu, s.memld * wc);
+  const float dd = fmaf(s.ddu * upm, wu, s.ddc * wc);
+  const float mwp_nobw = div_pos(ml, dd);
+  const float bwpw = div_pos(s.fghz * lbw, ml);
+  const float mwp_bw = div_pos(s.bw, bwpw * asm_);
+  const float mwp_u = fminf(mwp_nobw, mwp_bw);
+  const bool mwp_cap = Nw <= mwp_u;
+  const float MWP = fminf(mwp_u, Nw);
+  const float mem_cycles = fmaf(ml_unc, U, s.memld * Cm);
+  const float cwp_full = div_pos(mem_cycles + comp_cycles, comp_cycles);
+  const bool cwp_cap = Nw <= cwp_full;
+  const float CWP = fminf(cwp_full, Nw);
+  const float per = comp_cycles * inv_mi;
+  const float over = fmaxf(MWP - 1.0f, 0.0f);
+  const float cy1 = fmaf(per, over, mem_cycles + comp_cycles);
+  const float cy2 = fmaf(per, over, div_pos(mem_cycles * Nw, MWP));
+  const float cy3 = fmaf(comp_cycles, Nw, s.memld);
+  const float cyc = (mwp_cap && cwp_cap) ? cy1 : ((CWP >= MWP || comp_cycles > mem_cycles) ? cy2 : cy3);
+  const float synch_cost = dd * over * synch * (float)bact;
+  float ex = has_mem ? (cyc + synch_cost) * rep : comp_cycles * rep;
+  ex = valid ? ex : INFINITY;
+  return CfgOut{ex, pole, bact_out, OCC ? (valid ? nw_i : 0) : 0};
+}
+
 // The evaluate-and-argmin of one query (Sec. 3.3 Steps 4-5): every
 // configuration is evaluated in registers without data-dependent branches
 // (invalid and pole configurations evaluate to +inf) and the running (best,
@@ -336,16 +462,100 @@ __device__ __forceinline__ void eval_query(const float4 q0, const float4 q1, boo
   st_out = st;
 }
 
+// eval_query with Step 5's choice among several optimal configurations made
+// by a second metric: of the configurations within (1 + tie_rel) of the
+// best cycles, the one with the most active warps per SM (lowest index among
+// equals), found in a second pass over the configurations.  The first pass
+// gives the same best, second and (before the choice) argmin as eval_query.
+template <int D1, bool SH, bool TIE>
+__device__ __forceinline__ void eval_query_tie(const float4 q0, const float4 q1, bool kid_ok,
+                                           const float *aN8, const float *bN8, int32_t grid,
+                                           const float *tab, const CfgTab &cfg, const HwC &hw,
+                                           int &arg_out, float &b1_out, float &b2_out,
+                                           int &st_out, float tie_rel = 0.0f) {
+  float b1 = INFINITY, b2 = INFINITY;
+  int arg = -1, st = 0;
+  QState s;
+  if (!query_state<SH>(q0, q1, kid_ok, aN8, bN8, grid, s)) {
+    st = RP_Q_BAD;
+  } else {
+    bool any_pole = false;
+    for (int c = 0; c < kNcfg; ++c) {
+      const CfgOut o = eval_cfg<D1, SH>(c, s, tab, cfg, hw);
+      any_pole |= o.pole;
+      const float ex = o.ex;
+      const bool better = ex < b1;
+      const bool second_better = !better && ex < b2;
+      b2 = better ? b1 : (second_better ? ex : b2);
+      arg = better ? c : arg;
+      b1 = better ? ex : b1;
+    }
+    if (TIE) {
+      if (arg >= 0) {
+        const float lim = b1 * (1.0f + tie_rel);
+        int best_nw = -1;
+        for (int c = 0; c < kNcfg; ++c) {
+          const CfgOut o = eval_cfg<D1, SH, true>(c, s, tab, cfg, hw);
+          const bool take = o.ex <= lim && o.nw > best_nw;
+          best_nw = take ? o.nw : best_nw;
+          arg = take ? c : arg;
+        }
+      }
+    }
+    st |= any_pole ? RP_Q_POLE : 0;
+    if (arg < 0) st |= RP_Q_NO_VALID;
+  }
+  arg_out = arg;
+  b1_out = b1;
+  b2_out = b2;
+  st_out = st;
+}
+
+// Occupancy of every configuration of every query (Sec. 2 Example 1, as a
+// rational program of the fitted registers per thread and shared words per
+// block): B_active and W_active per (query, configuration), 0 where the
+// configuration is not resident, invalid or a pole; a bad query gets 0
+// everywhere and RP_Q_BAD.  One thread per query.
+template <int D1>
+__global__ void __launch_bounds__(256) occupancy_kernel(ProgramView P, int64_t K,
+                                                        const __grid_constant__ CfgTab cfg, HwC hw,
+                                                        const float4 *__restrict__ q, int64_t Q,
+                                                        int32_t *__restrict__ b_active,
+                                                        int32_t *__restrict__ w_active,
+                                                        int32_t *__restrict__ status) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 q0 = __ldg(q + 2 * i);
+    const float4 q1 = __ldg(q + 2 * i + 1);
+    const int32_t kid = __float_as_int(q1.w);
+    const bool kid_ok = kid >= 0 && kid < K;
+    const int64_t k = kid_ok ? kid : 0;
+    QState s;
+    const bool ok = query_state<false>(q0, q1, kid_ok, P.aN + k * kNmet, P.bN + k * kNmet,
+                                       kid_ok ? __ldg(P.grid + k) : 0, s);
+    const float *tab = P.table + k * kNcfg * kNmet * 2 * D1;
+    int st = ok ? 0 : RP_Q_BAD;
+    for (int c = 0; c < kNcfg; ++c) {
+      CfgOut o = CfgOut{INFINITY, false, 0, 0};
+      if (ok) o = eval_cfg<D1, false, true>(c, s, tab, cfg, hw);
+      st |= o.pole ? RP_Q_POLE : 0;
+      b_active[i * kNcfg + c] = o.bact;
+      w_active[i * kNcfg + c] = o.nw;
+    }
+    status[i] = st;
+  }
+}
+
 // One thread per query, queries in input order; persistent grid-stride
 // loop.  Each query gathers its kernel's table rows from global memory (L2).
-template <int D1>
+template <int D1, bool TIE>
 __global__ void __launch_bounds__(256) search_kernel(ProgramView P, int64_t K,
                                                      const __grid_constant__ CfgTab cfg, HwC hw,
                                                      const float4 *__restrict__ q, int64_t Q,
                                                      int32_t *__restrict__ argmin,
                                                      float *__restrict__ best,
                                                      float *__restrict__ second,
-                                                     int32_t *__restrict__ status) {
+                                                     int32_t *__restrict__ status, float tie_rel) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q;
        i += (int64_t)gridDim.x * blockDim.x) {
     const float4 q0 = __ldg(q + 2 * i);
@@ -355,9 +565,15 @@ __global__ void __launch_bounds__(256) search_kernel(ProgramView P, int64_t K,
     const int64_t k = kid_ok ? kid : 0;
     int arg, st;
     float b1, b2;
-    eval_query<D1, false>(q0, q1, kid_ok, P.aN + k * kNmet, P.bN + k * kNmet,
-                          kid_ok ? __ldg(P.grid + k) : 0,
-                          P.table + k * kNcfg * kNmet * 2 * D1, cfg, hw, arg, b1, b2, st);
+    if constexpr (TIE)
+      eval_query_tie<D1, false, true>(q0, q1, kid_ok, P.aN + k * kNmet, P.bN + k * kNmet,
+                                      kid_ok ? __ldg(P.grid + k) : 0,
+                                      P.table + k * kNcfg * kNmet * 2 * D1, cfg, hw, arg, b1, b2,
+                                      st, tie_rel);
+    else
+      eval_query<D1, false>(q0, q1, kid_ok, P.aN + k * kNmet, P.bN + k * kNmet,
+                            kid_ok ? __ldg(P.grid + k) : 0,
+                            P.table + k * kNcfg * kNmet * 2 * D1, cfg, hw, arg, b1, b2, st);
     argmin[i] = arg;
     best[i] = b1;
     second[i] = b2;
@@ -391,13 +607,18 @@ __global__ void bucket_count_kernel(const float *__restrict__ q, int64_t Q, int6
     for (int j = threadIdx.x; j <= K; j += blockDim.x) hist[j] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q;
+  // whole warps iterate (blockDim.x is a multiple of 32, so a warp's 32
+  // indices are consecutive): the loop condition is the same for every lane
+  // and every warp-collective call below uses the full mask; lanes past Q
+  // take the bucket -1, which no query has, and do nothing
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i - lane < Q;
        i += (int64_t)gridDim.x * blockDim.x) {
     // warp-aggregated: one atomic per distinct bucket in the warp (queries
     // in kernel order would otherwise serialise 32 atomics on one counter)
-    const int b = query_bucket(q, i, K);
-    const unsigned peers = __match_any_sync(__activemask(), b);
-    if (lane == __ffs(peers) - 1) {
+    const bool valid = i < Q;
+    const int b = valid ? query_bucket(q, i, K) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    if (valid && lane == __ffs(peers) - 1) {
       if (local) atomicAdd(&hist[b], __popc(peers));
       else atomicAdd(&cnt[b], __popc(peers));
     }
@@ -451,17 +672,20 @@ __global__ void __launch_bounds__(1024) bucket_scan_kernel(int32_t *__restrict__
 __global__ void bucket_scatter_kernel(const float *__restrict__ q, int64_t Q, int64_t K,
                                       int32_t *__restrict__ cur, int32_t *__restrict__ perm) {
   const int lane = threadIdx.x & 31;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q;
+  // whole warps iterate, as in bucket_count_kernel (full-mask collectives;
+  // lanes past Q: bucket -1, no claim, no write)
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i - lane < Q;
        i += (int64_t)gridDim.x * blockDim.x) {
     // warp-aggregated: the lowest lane of each bucket's group claims the
     // group's slots, the others take consecutive ones after it
-    const int b = query_bucket(q, i, K);
-    const unsigned peers = __match_any_sync(__activemask(), b);
+    const bool valid = i < Q;
+    const int b = valid ? query_bucket(q, i, K) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
     const int leader = __ffs(peers) - 1;
     int base = 0;
-    if (lane == leader) base = atomicAdd(&cur[b], __popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    perm[base + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
+    if (valid && lane == leader) base = atomicAdd(&cur[b], __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (valid) perm[base + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
   }
 }
 
@@ -474,12 +698,12 @@ size_t grouped_smem(int threads) {
   return (size_t)(grouped_table_floats<D1>() + 2 * kNmet) * sizeof(float) + (size_t)threads * 4;
 }
 
-template <int D1>
+template <int D1, bool TIE>
 __global__ void __launch_bounds__(256, 3) search_grouped_kernel(
     ProgramView P, int64_t K, const __grid_constant__ CfgTab cfg, HwC hw,
     const float4 *__restrict__ q, int64_t Q, const int32_t *__restrict__ perm,
     int32_t *__restrict__ argmin, float *__restrict__ best, float *__restrict__ second,
-    int32_t *__restrict__ status) {
+    int32_t *__restrict__ status, float tie_rel) {
   constexpr int TF = grouped_table_floats<D1>();
   extern __shared__ float4 smem4[];
   float *tab_s = reinterpret_cast<float *>(smem4);   // TF floats (a multiple of 4)
@@ -521,8 +745,12 @@ __global__ void __launch_bounds__(256, 3) search_grouped_kernel(
       if (b == cb) {
         int arg, st;
         float b1, b2;
-        eval_query<D1, true>(q0, q1, cb < K, ab_s, ab_s + kNmet, grid_s, tab_s, cfg, hw, arg, b1,
-                             b2, st);
+        if constexpr (TIE)
+          eval_query_tie<D1, true, true>(q0, q1, cb < K, ab_s, ab_s + kNmet, grid_s, tab_s, cfg, hw,
+                                         arg, b1, b2, st, tie_rel);
+        else
+          eval_query<D1, true>(q0, q1, cb < K, ab_s, ab_s + kNmet, grid_s, tab_s, cfg, hw, arg, b1,
+                               b2, st);
         argmin[qi] = arg;
         best[qi] = b1;
         second[qi] = b2;
@@ -535,7 +763,49 @@ __global__ void __launch_bounds__(256, 3) search_grouped_kernel(
   }
 }
 
+// Error % of a chosen configuration (Sec. 5): per query, over the finite
+// runtimes of its 66 configurations, B = the smallest, W = the largest, and
+// (t[choice] - B) / (W - B) * 100 (0 when W == B).  One thread per query.
+__global__ void error_pct_kernel(const float *__restrict__ rt, const int32_t *__restrict__ choice,
+                                 int64_t Q, float *__restrict__ err, int32_t *__restrict__ status) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float *r = rt + i * kNcfg;
+    float lo = INFINITY, hi = -INFINITY;
+    for (int c = 0; c < kNcfg; ++c) {
+      const float v = __ldg(r + c);
+      if (isfinite(v)) {
+        lo = fminf(lo, v);
+        hi = fmaxf(hi, v);
+      }
+    }
+    const int32_t c = __ldg(choice + i);
+    int st = 0;
+    float e = NAN;
+    if (!(lo <= hi)) {
+      st = RP_EP_NO_RUNTIME;
+    } else if (c < 0 || c >= kNcfg || !isfinite(__ldg(r + c))) {
+      st = RP_EP_BAD_CHOICE;
+    } else {
+      const float t = __ldg(r + c);
+      e = hi > lo ? (t - lo) / (hi - lo) * 100.0f : 0.0f;
+    }
+    err[i] = e;
+    status[i] = st;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_error_pct(const float *runtimes, const int32_t *choice, int64_t Q,
+                             float *err_pct, int32_t *status, cudaStream_t s) {
+  if (Q == 0) return cudaSuccess;
+  const int threads = 256;
+  int64_t blocks = (Q + threads - 1) / threads;
+  if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
+  error_pct_kernel<<<(unsigned)blocks, threads, 0, s>>>(runtimes, choice, Q, err_pct, status);
+  return cudaGetLastError();
+}
 
 int num_sms() {
   static int n = 0;
@@ -603,10 +873,11 @@ size_t search_workspace_bytes(int64_t K, int64_t Q) {
   return align16((size_t)(K + 2) * 4) + align16((size_t)(K + 1) * 4) + align16((size_t)Q * 4);
 }
 
-template <int D1>
+template <int D1, bool TIE>
 static cudaError_t launch_d(ProgramView prog, int64_t K, const CfgTab &cfg, const HwC &h,
                             const float *queries, int64_t Q, int32_t *argmin, float *best,
-                            float *second, int32_t *status, void *ws, cudaStream_t s) {
+                            float *second, int32_t *status, void *ws, cudaStream_t s,
+                            float tie_rel) {
   const SearchShape shape = search_shape(D1 - 1);
   const int threads = shape.threads;
   const float4 *q4 = reinterpret_cast<const float4 *>(queries);
@@ -614,8 +885,8 @@ static cudaError_t launch_d(ProgramView prog, int64_t K, const CfgTab &cfg, cons
   const int64_t cap = (int64_t)num_sms() * shape.ctas_per_sm;
   if (blocks > cap) blocks = cap;
   if (!ws) {
-    search_kernel<D1><<<(unsigned)blocks, threads, 0, s>>>(prog, K, cfg, h, q4, Q, argmin, best,
-                                                           second, status);
+    search_kernel<D1, TIE><<<(unsigned)blocks, threads, 0, s>>>(prog, K, cfg, h, q4, Q, argmin, best,
+                                                                second, status, tie_rel);
     return cudaGetLastError();
   }
   unsigned char *w = static_cast<unsigned char *>(ws);
@@ -635,15 +906,13 @@ static cudaError_t launch_d(ProgramView prog, int64_t K, const CfgTab &cfg, cons
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   bucket_scatter_kernel<<<(unsigned)bb, bt, 0, s>>>(queries, Q, K, cur, perm);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  search_grouped_kernel<D1><<<(unsigned)blocks, threads, grouped_smem<D1>(threads), s>>>(
-      prog, K, cfg, h, q4, Q, perm, argmin, best, second, status);
+  search_grouped_kernel<D1, TIE><<<(unsigned)blocks, threads, grouped_smem<D1>(threads), s>>>(
+      prog, K, cfg, h, q4, Q, perm, argmin, best, second, status, tie_rel);
   return cudaGetLastError();
 }
 
-cudaError_t launch_search(ProgramView prog, int64_t K, int d, const rp_hw_fixed &hw,
-                          const float *queries, int64_t Q, int32_t *argmin, float *best,
-                          float *second, int32_t *status, void *workspace, cudaStream_t s) {
-  if (Q == 0) return cudaSuccess;
+// Per-configuration constants of the occupancy arithmetic (host).
+static CfgTab make_cfg(const rp_hw_fixed &hw) {
   CfgTab cfg{};
   int c = 0;
   for (int a = 0; a <= 10; ++a)
@@ -659,16 +928,61 @@ cudaError_t launch_search(ProgramView prog, int64_t K, int d, const rp_hw_fixed 
       cfg.rsm_w[c] = (int32_t)(hw.r_sm / wpbw);
       cfg.rsm_t[c] = hw.r_sm / T;
     }
+  return cfg;
+}
+
+template <int D1>
+static cudaError_t launch_occ_d(ProgramView prog, int64_t K, const CfgTab &cfg, const HwC &h,
+                                const float *queries, int64_t Q, int32_t *b_active,
+                                int32_t *w_active, int32_t *status, cudaStream_t s) {
+  const int threads = 128;
+  int64_t blocks = (Q + threads - 1) / threads;
+  const int64_t cap = (int64_t)num_sms() * 16;
+  if (blocks > cap) blocks = cap;
+  occupancy_kernel<D1><<<(unsigned)blocks, threads, 0, s>>>(
+      prog, K, cfg, h, reinterpret_cast<const float4 *>(queries), Q, b_active, w_active, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_occupancy(ProgramView prog, int64_t K, int d, const rp_hw_fixed &hw,
+                             const float *queries, int64_t Q, int32_t *b_active, int32_t *w_active,
+                             int32_t *status, cudaStream_t s) {
+  if (Q == 0) return cudaSuccess;
+  const CfgTab cfg = make_cfg(hw);
   HwC h{hw.warp_size, hw.w_max, hw.r_sm, hw.z_sm, hw.issue_cycles};
-  void *ws = search_workspace_bytes(K, Q) > 0 ? workspace : nullptr;
   switch (d + 1) {
-    case 1: return launch_d<1>(prog, K, cfg, h, queries, Q, argmin, best, second, status, ws, s);
-    case 2: return launch_d<2>(prog, K, cfg, h, queries, Q, argmin, best, second, status, ws, s);
-    case 3: return launch_d<3>(prog, K, cfg, h, queries, Q, argmin, best, second, status, ws, s);
-    case 4: return launch_d<4>(prog, K, cfg, h, queries, Q, argmin, best, second, status, ws, s);
-    case 5: return launch_d<5>(prog, K, cfg, h, queries, Q, argmin, best, second, status, ws, s);
+    case 1: return launch_occ_d<1>(prog, K, cfg, h, queries, Q, b_active, w_active, status, s);
+    case 2: return launch_occ_d<2>(prog, K, cfg, h, queries, Q, b_active, w_active, status, s);
+    case 3: return launch_occ_d<3>(prog, K, cfg, h, queries, Q, b_active, w_active, status, s);
+    case 4: return launch_occ_d<4>(prog, K, cfg, h, queries, Q, b_active, w_active, status, s);
+    case 5: return launch_occ_d<5>(prog, K, cfg, h, queries, Q, b_active, w_active, status, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_search(ProgramView prog, int64_t K, int d, const rp_hw_fixed &hw,
+                          const float *queries, int64_t Q, int32_t *argmin, float *best,
+                          float *second, int32_t *status, void *workspace, cudaStream_t s,
+                          float tie_rel) {
+  if (Q == 0) return cudaSuccess;
+  const CfgTab cfg = make_cfg(hw);
+  HwC h{hw.warp_size, hw.w_max, hw.r_sm, hw.z_sm, hw.issue_cycles};
+  void *ws = search_workspace_bytes(K, Q) > 0 ? workspace : nullptr;
+  const bool tie = tie_rel >= 0.0f;
+#define RP_LAUNCH(D1)                                                                          \
+  return tie ? launch_d<D1, true>(prog, K, cfg, h, queries, Q, argmin, best, second, status, ws, s, \
+                                  tie_rel)                                                     \
+             : launch_d<D1, false>(prog, K, cfg, h, queries, Q, argmin, best, second, status, ws,   \
+                                   s, tie_rel)
+  switch (d + 1) {
+    case 1: RP_LAUNCH(1);
+    case 2: RP_LAUNCH(2);
+    case 3: RP_LAUNCH(3);
+    case 4: RP_LAUNCH(4);
+    case 5: RP_LAUNCH(5);
+    default: return cudaErrorInvalidValue;
+  }
+#undef RP_LAUNCH
 }
 
 }  // namespace rpk

@@ -33,7 +33,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_version_and_strerror(lib):
-    assert rp.rp_version() == 2
+    assert rp.rp_version() == 3
     assert rp.rp_strerror(0) == "ok"
     assert rp.rp_strerror(-1) == "invalid argument"
     assert rp.rp_strerror(-999) == "unknown error"
@@ -53,6 +53,10 @@ def test_argument_validation_without_launch(lib):
     d = rp.FitDesc(4, 100, 3, 17, 4, 0, 1e-12, None)         # bad precision
     assert lib.rp_fit(C.byref(d), None, None, None, None, None, None, None, None, None, 0, None) == -1
     d = rp.FitDesc(4, 100, 3, 1, 4, 0, 1e-12, None)          # null outputs
+    assert lib.rp_fit(C.byref(d), None, None, None, None, None, None, None, None, None, 0, None) == -1
+    d = rp.FitDesc(4, 100, 3, 1, 4, 0, 1e-8, None, 1234, 10, 0)   # point sets of 0 fits
+    assert lib.rp_fit(C.byref(d), None, None, None, None, None, None, None, None, None, 0, None) == -1
+    d = rp.FitDesc(4, 100, 3, 1, 4, 0, 1e-8, None, None, 0, 0, 7)     # reserved field set
     assert lib.rp_fit(C.byref(d), None, None, None, None, None, None, None, None, None, 0, None) == -1
     d = rp.FitDesc(0, 0, 3, 1, 4, 0, 1e-12, None)            # empty batch: ok, nothing launched
     assert lib.rp_fit(C.byref(d), None, None, None, None, None, None, None, None, None, 0, None) == 0
@@ -85,7 +89,7 @@ def test_tuning_argument_validation_without_launch(lib):
                               0, None, C.byref(t), None) == -1
     ws = C.c_size_t(0)
     d = rp.FitDesc(5, 100, 3, 1, 4, 0, 1e-12, None)
-    assert lib.rp_fit_workspace_size(C.byref(d), C.byref(ws)) == 0 and ws.value == 16
+    assert lib.rp_fit_workspace_size(C.byref(d), C.byref(ws)) == 0 and ws.value == 32
 
 
 def test_search_workspace_size(lib):

@@ -20,7 +20,8 @@ import torch
 import oracle
 import paper_1906_00142_gb300 as rp
 import workloads as W
-from gpu_util import HW, dev, eval_coef_at, host, lin_objective, need_gpu, per_fit_max, predictions
+from gpu_util import HW, dev, eval_coef_at, host, need_gpu
+from test_gpu_fit import compare
 
 pytestmark = pytest.mark.gpu
 
@@ -147,21 +148,8 @@ def test_uneven_batch_graph_captured(precision):
     sub = dict(x=np.ascontiguousarray(np.concatenate(xs, 1)), y=np.concatenate(ys),
                fit_off=np.array(offs, np.int64), degree=inst["degree"][pick])
     ref = oracle.fit(sub["x"], sub["y"], sub["fit_off"], sub["degree"])
-    sens = oracle.fit_sensitivity(sub["x"], sub["y"], sub["fit_off"], sub["degree"], base=ref)
-    gcoef, gbox = host(fit_out["coef"])[pick], host(fit_out["box"])[pick]
-    for i, f in enumerate(pick):
-        a, b = sub["fit_off"][i], sub["fit_off"][i + 1]
-        pts = sub["x"][:, a:b].T.astype(np.float64)
-        yy = sub["y"][a:b].astype(np.float64)
-        dgi = int(sub["degree"][i])
-        og = lin_objective(gcoef[i], gbox[i], dgi, pts, yy)
-        oo = lin_objective(ref["coef"][i], ref["box"][i], dgi, pts, yy)
-        assert og <= oo * (1 + 1e-4) + (1e-10 + (30 * sens[i]) ** 2) * (b - a), (int(f), og, oo)
-    pg = predictions(gcoef, gbox, sub["degree"], sub["x"], sub["fit_off"])
-    po = oracle.predict_samples(ref, sub["x"], sub["fit_off"])
-    err = per_fit_max(np.abs(pg - po) / np.abs(po), sub["fit_off"])
-    ok = sens < 1e-2
-    assert (err[ok] <= np.maximum(1e-4, 30 * sens[ok])).all(), (err, sens)
+    gsub = {k: host(v)[pick] for k, v in fit_out.items()}
+    compare(sub, gsub, ref)
     # the argmin of the graph's search against the oracle's own program
     # (oracle fits of sampled kernels), where both are decisive.  Only
     # kernels with >= 1024 samples: with fewer, a degree-4 fit (69 unknowns)
@@ -192,6 +180,17 @@ def test_uneven_batch_graph_captured(precision):
     gb = host(s_out["best"])[sel]
     gap_o = (so["second"] - so["best"]) / so["best"]
     gap_g = (host(s_out["second"])[sel] - gb) / gb
-    decisive = (gap_o > 1e-3) & (gap_g > 1e-3)
-    assert decisive.sum() > 500
-    assert (ga[decisive] == so["argmin"][decisive]).mean() > 0.99
+    # the graph's program comes from the GPU's fits, which agree with the
+    # oracle's to 1e-4: identical argmins wherever the oracle's top-two gap
+    # is decisive at 1e-3, and on all but a few queries at 1e-5
+    # (queries whose best or second configuration is FP32-ill-conditioned or
+    # within 1e-5 of a case boundary excluded, as in the search tests)
+    ev = oracle.evaluate(prog_o, HW, qs)
+    rows = np.arange(len(qs))
+    sec = np.argsort(ev["exec"], axis=1)[:, 1]
+    ill = ((ev["margin"][rows, so["argmin"]] < 1e-5) | (ev["cond"][rows, so["argmin"]] > 30) |
+           (ev["margin"][rows, sec] < 1e-5) | (ev["cond"][rows, sec] > 30))
+    d3, d5 = (gap_o > 1e-3) & ~ill, (gap_o > 1e-5) & ~ill
+    assert d3.sum() > 500
+    assert (ga[d3] == so["argmin"][d3]).all()
+    assert (ga[d5] == so["argmin"][d5]).mean() > 0.999

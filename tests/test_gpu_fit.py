@@ -1,19 +1,14 @@
-"""GPU rational fits (rp_fit) against the FP64 oracle.
-
-Two checks per fit:
- 1. The linearised least-squares objective (Sec. 4.2) of the GPU's p/q,
-    evaluated in FP64 with mean(q) = 1, is within 1e-4 relative of the
-    oracle's optimum: the GPU solved the same problem.
- 2. Predictions at every sample within 1e-4 relative of the oracle's.  The
-    FP64 path ("fp64", design built in FP64) is held to that on every fit.
-    The FP32 paths build the design in FP32; for a fit whose oracle
-    predictions themselves move by sens when every design entry is
-    perturbed by one FP32 rounding (the oracle's sensitivity check), no
-    FP32-data method can do better than ~sens.  A GPU design entry carries
-    ~10 roundings (normalisation, marginal polynomials, products,
-    whitening), so the gate there is max(1e-4, 30 sens); fits with
-    sens >= 1e-2 are compared on the objective only.  The number of fits
-    with sens >= 1e-5 is reported.
+"""GPU rational fits (rp_fit) against the FP64 oracle, every precision held
+to the same bar on every fit:
+ 1. box, input-validation statuses and the pole flag (q <= 0 at a sample)
+    equal to the oracle's;
+ 2. the linearised least-squares objective (Sec. 4.2) of the GPU's p/q,
+    evaluated in FP64 with mean(q) = 1, within 1e-6 relative of the oracle's
+    optimum: the GPU solved the same problem;
+ 3. predictions p/q at every sample within 1e-4 relative of the oracle's
+    (the stated fit tolerance), except on fits the oracle itself reports as
+    rank deficient, whose least-squares solution (hence p/q) is not unique:
+    those are compared on the objective only.
 """
 import numpy as np
 import pytest
@@ -26,66 +21,59 @@ from gpu_util import dev, host, lin_objective, need_gpu, per_fit_max, prediction
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
+OBJ_TOL = 1e-6
 
 
-def gpu_fit(inst, precision, degree=None, max_refine=8, degrees=True):
+def gpu_fit(inst, precision, degree=None, max_refine=8, degrees=True, tol=1e-8):
     d = int(inst["degree"].max()) if degree is None else degree
     out = rp.rp_fit(dev(inst["x"]), dev(inst["y"]), dev(inst["fit_off"]), d,
-                    precision=precision, max_refine=max_refine,
+                    precision=precision, max_refine=max_refine, tol=tol,
                     degrees=dev(inst["degree"]) if degrees else None)
     return {k: host(v) for k, v in out.items()}
 
 
-def compare(inst, g, ref=None, sens=None, all_fits=False):
+def compare(inst, g, ref=None, weighted=True):
+    """Checks 1-3 of the module docstring; returns the per-fit maximum
+    relative prediction error."""
     x, off, deg = inst["x"], inst["fit_off"], inst["degree"]
     if ref is None:
-        ref = oracle.fit(x, inst["y"], off, deg)
+        ref = oracle.fit(x, inst["y"], off, deg, weighted=weighted)
     np.testing.assert_array_equal(g["box"], ref["box"])
     hard = oracle.FS_EMPTY | oracle.FS_NONFINITE | oracle.FS_NONPOS_Y
     np.testing.assert_array_equal(g["status"] & hard, ref["status"] & hard)
     ok = (ref["status"] & hard) == 0
-    if sens is None:
-        sens = oracle.fit_sensitivity(x, inst["y"], off, deg, base=ref)
-    # 1. same least-squares optimum.  Slack: relative 1e-4, plus what a
-    # prediction error of 1e-5 at every sample adds (exact data), plus for the
-    # FP32 paths what prediction changes of 10 sens add
-    # (sum_i (10 sens q_i)^2, q ~ 1 on average)
+    pole_g = (g["status"] & rp.RP_FIT_POLE) != 0
+    pole_o = (ref["status"] & oracle.FS_POLE) != 0
+    assert (pole_g[ok] == pole_o[ok]).all(), np.where(ok & (pole_g != pole_o))[0][:10]
     for f in np.where(ok)[0]:
         a, b = off[f], off[f + 1]
         pts = x[:, a:b].T.astype(np.float64)
         yy = inst["y"][a:b].astype(np.float64)
-        og = lin_objective(g["coef"][f], g["box"][f], int(deg[f]), pts, yy)
-        oo = lin_objective(ref["coef"][f], ref["box"][f], int(deg[f]), pts, yy)
-        slack = 1e-10 + (0.0 if all_fits else (30.0 * sens[f]) ** 2)
-        assert og <= oo * (1 + 1e-4) + slack * (b - a), (int(f), og, oo, float(sens[f]))
-    # 2. predictions
+        og = lin_objective(g["coef"][f], g["box"][f], int(deg[f]), pts, yy, weighted=weighted)
+        oo = lin_objective(ref["coef"][f], ref["box"][f], int(deg[f]), pts, yy, weighted=weighted)
+        # absolute slack: an interpolating (zero-residual) fit leaves rounding only
+        scale = (b - a) if weighted else float(np.sum(yy ** 2))
+        assert og <= oo * (1 + OBJ_TOL) + 1e-12 * scale, (int(f), og, oo)
     p_o = oracle.predict_samples(ref, x, off)
     p_g = predictions(g["coef"], g["box"], deg, x, off)
     rel = np.abs(p_g - p_o) / np.abs(p_o)
     err = per_fit_max(rel, off)
-    gate = np.full(len(err), TOL) if all_fits else np.maximum(TOL, 30.0 * sens)
-    # a fit whose own predictions move by more than 1% under one FP32 rounding
-    # of its data has no FP32-determined predictions: only its objective
-    # (checked above) is compared
-    checked = ok if all_fits else ok & (sens < 1e-2)
-    bad = np.where(checked & ~(err <= gate))[0]
-    assert len(bad) == 0, [(int(f), float(err[f]), float(sens[f]), int(g["status"][f])) for f in bad[:10]]
-    well = ok & (sens < 1e-5)
-    print(f"fits {ok.sum()}: well-posed at FP32 data precision {well.sum()}, "
-          f"objective-only {(ok & ~checked).sum()}, "
-          f"median err {np.median(err[ok]):.2e}, max err on well-posed "
-          f"{(err[well].max() if well.any() else 0):.2e}")
+    checked = ok & ((ref["status"] & oracle.FS_RANK_DEFICIENT) == 0)
+    bad = np.where(checked & ~(err <= TOL))[0]
+    assert len(bad) == 0, [(int(f), float(err[f]), int(g["status"][f])) for f in bad[:10]]
+    print(f"fits {ok.sum()} (rank deficient in the oracle: {(ok & ~checked).sum()}), "
+          f"prediction error median {np.median(err[checked]) if checked.any() else 0:.2e} "
+          f"max {err[checked].max() if checked.any() else 0:.2e}")
     # coef32 is coef rounded to float
     np.testing.assert_array_equal(g["coef32"], g["coef"].astype(np.float32))
-    return err, sens
+    return err
 
 
 @pytest.fixture(scope="module")
 def batched():
     inst = W.batched_instance(16, seed=31, m=512, d=3)
     ref = oracle.fit(inst["x"], inst["y"], inst["fit_off"], inst["degree"])
-    sens = oracle.fit_sensitivity(inst["x"], inst["y"], inst["fit_off"], inst["degree"], base=ref)
-    return inst, ref, sens
+    return inst, ref
 
 
 @pytest.mark.parametrize("precision", ["fp32", "tf32", "tf32x3", "bf16", "bf16x3"])
@@ -94,28 +82,35 @@ def test_fit_fp32_data_batched(batched, precision):
     cores (tf32: one TF32 pass for the design Gram; tf32x3: split TF32,
     three passes)."""
     need_gpu()
-    inst, ref, sens = batched
-    g = gpu_fit(inst, precision, max_refine=16 if precision == "bf16" else 8)
+    inst, ref = batched
+    g = gpu_fit(inst, precision, max_refine=16 if precision.startswith("bf16") else 8)
     assert not (g["status"] & rp.RP_FIT_TIMEOUT).any()
-    err, _ = compare(inst, g, ref, sens)
+    compare(inst, g, ref)
     iters = (g["status"] & rp.RP_FIT_ITER_MASK) >> rp.RP_FIT_ITER_SHIFT
-    print(precision, "refinement iterations: median", np.median(iters), "max", iters.max())
-    assert ((g["status"] & rp.RP_FIT_NOT_CONVERGED) == 0).mean() > 0.95, np.unique(g["status"])
+    acc = (g["status"] & rp.RP_FIT_ACC_MASK) >> rp.RP_FIT_ACC_SHIFT
+    fp64 = (g["status"] & rp.RP_FIT_FP64_PASS) != 0
+    print(precision, "refinement iterations: median", np.median(iters), "max", iters.max(),
+          "accurate passes: median", np.median(acc), "solved again in FP64:", int(fp64.sum()))
+    # every fit of the FP32 design's own solve ends on accurate (double-float)
+    # residual passes; few are passed on to the FP64 path
+    assert (acc[~fp64] >= 1).all()
+    assert fp64.mean() <= 0.1, np.unique(g["status"])
+    assert ((g["status"] & rp.RP_FIT_NOT_CONVERGED) == 0).all(), np.unique(g["status"])
 
 
 def test_fit_fp64_batched(batched):
     need_gpu()
-    inst, ref, sens = batched
+    inst, ref = batched
     g = gpu_fit(inst, "fp64")
-    compare(inst, g, ref, sens, all_fits=True)
+    compare(inst, g, ref)
 
 
 def test_fit_uniform_degree_argument(batched):
     """degrees=NULL uses desc.degree for every fit."""
     need_gpu()
-    inst, ref, sens = batched
+    inst, ref = batched
     g = gpu_fit(inst, "fp32", degree=3, degrees=False)
-    compare(inst, g, ref, sens)
+    compare(inst, g, ref)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "tf32", "tf32x3", "bf16", "bf16x3", "fp64"])
@@ -123,8 +118,8 @@ def test_fit_tiny_exact_data(precision):
     """Noise-free integer-coefficient rationals (plain FP64 tiny case)."""
     need_gpu()
     inst = W.tiny_instance()
-    g = gpu_fit(inst, precision, max_refine=16 if precision == "bf16" else 8)
-    compare(inst, g, all_fits=(precision == "fp64"))
+    g = gpu_fit(inst, precision, max_refine=16 if precision.startswith("bf16") else 8)
+    compare(inst, g)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "tf32", "fp64"])
@@ -134,7 +129,7 @@ def test_fit_uneven_degrees_and_counts(precision):
     need_gpu()
     inst = W.batched_instance(6, seed=41, degree_choices=(2, 3, 4), m_range=(64, 2048))
     g = gpu_fit(inst, precision, degree=4)
-    compare(inst, g, all_fits=(precision == "fp64"))
+    compare(inst, g)
 
 
 def test_fit_edge_cases():
@@ -172,22 +167,17 @@ def test_fit_edge_cases():
             assert np.max(np.abs(pg[a:b] - po[a:b]) / po[a:b]) < TOL
 
 
+# The benchmarked launch and its settings (the ones bench.py times rp_fit with)
+from bench import BENCH_MAX_REFINE, BENCH_TOL  # noqa: E402
+
+
 @pytest.mark.parametrize("precision", ["fp32", "tf32"])
-def test_fit_full_size_sampled(precision):
-    """The benchmarked launch: 1024 kernels x 8 metrics, 512 samples, d=3;
-    64 fits re-solved by the oracle."""
+def test_fit_full_size_all_fits(precision):
+    """The benchmarked fit: 1024 kernels x 8 metrics, 512 samples, d = 3,
+    at the bench's tol and max_refine; all 8192 fits against the oracle."""
     need_gpu()
     inst = W.batched_instance(1024, seed=20190602, m=512, d=3)
-    g = gpu_fit(inst, precision)
+    g = gpu_fit(inst, precision, tol=BENCH_TOL, max_refine=BENCH_MAX_REFINE)
     assert not (g["status"] & rp.RP_FIT_TIMEOUT).any()
-    F = len(inst["fit_off"]) - 1
-    pick = np.sort(np.random.default_rng(1).choice(F, 64, replace=False))
-    xs, ys, offs = [], [], [0]
-    for f in pick:
-        a, b = inst["fit_off"][f], inst["fit_off"][f + 1]
-        xs.append(inst["x"][:, a:b]); ys.append(inst["y"][a:b]); offs.append(offs[-1] + b - a)
-    sub = dict(x=np.ascontiguousarray(np.concatenate(xs, 1)), y=np.concatenate(ys),
-               fit_off=np.array(offs, np.int64), degree=inst["degree"][pick])
-    gs = {k: v[pick] for k, v in g.items()}
-    compare(sub, gs)
-    assert ((g["status"] & (rp.RP_FIT_POLE | rp.RP_FIT_EMPTY)) == 0).mean() > 0.95
+    oracle.set_threads(__import__("os").cpu_count() or 1)
+    compare(inst, g)

@@ -6,7 +6,7 @@ import torch
 import oracle
 import paper_1906_00142_gb300 as rp
 import workloads as W
-from gpu_util import HW, dev, host, need_gpu
+from gpu_util import HW, dev, host, need_gpu, program_to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -52,15 +52,22 @@ def test_pack_absent_metric_and_degree_mix():
 
 
 def test_pipeline_fit_pack_search():
-    """GPU fit -> GPU pack -> GPU search; the search result is checked
-    against the oracle's evaluation of the same GPU-packed program is NOT
-    used: instead the oracle builds its own program from its own fits, and
-    the chosen configurations must agree where both programs are decisive."""
+    """GPU fit -> GPU pack -> GPU search, checked two ways.
+    1. The search on the same input as the oracle: the GPU evaluates the
+       oracle's own program (oracle fits, oracle pack); argmin identical
+       wherever the oracle's top-two gap exceeds 1e-5 relative, except
+       queries whose best or second configuration is FP32-ill-conditioned
+       or within 1e-5 of a case boundary (the exclusions of the search
+       tests, counted).
+    2. End to end: the GPU's program (from the GPU's fits) against the
+       oracle's; the fits agree to 1e-4, so the argmins agree wherever the
+       oracle's gap is decisive at 1e-3, and on all but a few queries at
+       1e-5."""
     need_gpu()
     inst = W.batched_instance(8, seed=53, m=512, d=3)
     K = 8
     g = rp.rp_fit(dev(inst["x"]), dev(inst["y"]), dev(inst["fit_off"]), 3, precision="fp32",
-                  degrees=dev(inst["degree"]))
+                  degrees=dev(inst["degree"]), tol=1e-8)
     gd = torch.full((K,), 2, dtype=torch.int32, device="cuda")
     buf = rp.rp_program_pack(g["coef"], g["box"], dev(inst["degree"]), dev(inst["metric_map"]), gd, 3)
     q = W.queries(4000, K, seed=54, n_log2=(6, 12))      # inside the fitted range of N
@@ -69,11 +76,22 @@ def test_pipeline_fit_pack_search():
     prog = oracle.pack(ref["coef"], ref["box"], ref["degree"], inst["metric_map"], 3)
     prog["grid_dims"] = np.full(K, 2, np.int32)
     s = oracle.search(prog, HW, q)
-    ga = host(out["argmin"])
     gap = (s["second"] - s["best"]) / s["best"]
-    decisive = gap > 1e-3
-    assert decisive.sum() > 1000
-    assert (ga[decisive] == s["argmin"][decisive]).mean() > 0.99
+    # 1. same program on both sides
+    same = rp.rp_eval_search(program_to_device(prog), K, 3, dev(q))
+    ev = oracle.evaluate(prog, HW, q)
+    rows = np.arange(len(q))
+    second = np.argsort(ev["exec"], axis=1)[:, 1]
+    ill = ((ev["margin"][rows, s["argmin"]] < 1e-5) | (ev["cond"][rows, s["argmin"]] > 30) |
+           (ev["margin"][rows, second] < 1e-5) | (ev["cond"][rows, second] > 30))
+    dec = (gap > 1e-5) & ~ill
+    assert dec.sum() > 2000, (dec.sum(), ill.sum())
+    assert (host(same["argmin"])[dec] == s["argmin"][dec]).all()
+    # 2. end to end (same exclusions)
+    ga = host(out["argmin"])
+    d3 = (gap > 1e-3) & ~ill
+    assert (ga[d3] == s["argmin"][d3]).all()
+    assert (ga[dec] == s["argmin"][dec]).mean() > 0.999
 
 
 def test_relmse_forward_backward(fitted):

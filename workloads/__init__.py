@@ -171,6 +171,22 @@ def batched_instance(n_kernels: int, seed: int, m=512, d=3, noise=0.01,
                 if n_metrics == N_METRICS else None)
 
 
+def shared_points(inst, n_metrics=N_METRICS):
+    """The same batched instance with each kernel's sample points stored once
+    (its metrics are measured at the same points): x_points float32 [3][P]
+    holding the points of fits 0, n_metrics, 2 n_metrics, .., and
+    point_off int64 [K+1] into it; y and fit_off are unchanged."""
+    off = inst["fit_off"]
+    K = (len(off) - 1) // n_metrics
+    starts = off[0:K * n_metrics:n_metrics]
+    counts = off[1:K * n_metrics + 1:n_metrics] - starts
+    cols = np.concatenate([np.arange(a, a + c) for a, c in zip(starts, counts)]) if K else \
+        np.zeros(0, np.int64)
+    point_off = np.zeros(K + 1, np.int64)
+    point_off[1:] = np.cumsum(counts)
+    return np.ascontiguousarray(inst["x"][:, cols]), point_off
+
+
 def queries(n_queries: int, n_kernels: int, seed: int, n_log2=(10, 26)):
     """Search queries, sorted by kernel id.  N log-uniform over 2^10..2^26
     rounded to an integer; SMs U{80..160}; clock U[1.2, 2.0] GHz; memory

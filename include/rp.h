@@ -100,6 +100,14 @@ typedef enum rp_precision {
 
 /* rp_fit flags */
 #define RP_FIT_UNWEIGHTED 1       /* rows not weighted by 1/|y| */
+#define RP_FIT_SOLVER_SVD 2       /* solve through the singular value decomposition of the
+                                     (equilibrated, whitened) design, the paper's solver
+                                     (Sec. 4.2): cyclic Jacobi rotations of its normal matrix
+                                     give the right singular vectors and squared singular
+                                     values; directions below drop tolerance are truncated (the
+                                     rank) and the truncated pseudo-inverse is the first
+                                     solution and the refinement's preconditioner (instead of
+                                     the sweep operator with pivot dropping) */
 
 typedef struct rp_fit_desc {
   int64_t num_fits;        /* F >= 0 */

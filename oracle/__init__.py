@@ -191,8 +191,9 @@ def _prog_args(prog):
 
 def evaluate(prog, hw, queries):
     """Per (query, configuration): exec cycles (inf if invalid), case id,
-    decision margin, Horner condition number, and the model's MWP, CWP and
-    active-warp count Nw (NaN where not computed)."""
+    decision margin, Horner condition number, and the model's MWP, CWP,
+    active-warp count Nw and active-block count B_active (NaN where not
+    computed; B_active 0 where the block cannot be resident)."""
     lib = _load()
     aN, bN, tab, gd, K, d = _prog_args(prog)
     q = np.ascontiguousarray(queries, np.float32)
@@ -201,12 +202,12 @@ def evaluate(prog, hw, queries):
     cs = np.zeros((Q, NCFG), np.int32)
     mg = np.zeros((Q, NCFG))
     cd = np.zeros((Q, NCFG))
-    dg = np.zeros((Q, NCFG, 3))
+    dg = np.zeros((Q, NCFG, 4))
     h = _hw(hw)
     lib.rpo_eval(K, d, _p(aN), _p(bN), _p(tab), _p(gd), _p(h), Q, _p(q), _p(ex), _p(cs),
                  _p(mg), _p(cd), _p(dg))
     return dict(exec=ex, case=cs, margin=mg, cond=cd, mwp=dg[..., 0], cwp=dg[..., 1],
-                nw=dg[..., 2])
+                nw=dg[..., 2], bact=dg[..., 3])
 
 
 def search(prog, hw, queries):
@@ -257,3 +258,41 @@ def error_pct(c_rt, best_t, worst_t):
     """Error % of a chosen configuration (Sec. 5):
     (C_rt - Best_time) / (Worst_time - Best_time) * 100."""
     return (c_rt - best_t) / (worst_t - best_t) * 100.0
+
+
+def search_tiebreak(prog, hw, queries, tie_rel):
+    """Step 5 with a second metric (Sec. 3.3): the configurations whose exec
+    cycles are at most (1 + tie_rel) times the smallest are optimal; of them
+    the one with the most active warps per SM (W_active), lowest index among
+    equals.  Returns argmin per query (-1 if none valid) and the oracle's
+    evaluation (for exclusions near the threshold)."""
+    ev = evaluate(prog, hw, queries)
+    ex = ev["exec"]
+    Q = ex.shape[0]
+    arg = np.full(Q, -1, np.int32)
+    for i in range(Q):
+        best = np.min(ex[i])
+        if not np.isfinite(best):
+            continue
+        opt = np.where(ex[i] <= best * (1.0 + tie_rel))[0]
+        nw = ev["nw"][i, opt]
+        arg[i] = opt[np.argmax(nw)]        # first maximum: lowest index among equals
+    return arg, ev
+
+
+def error_pct_table(runtimes, choice):
+    """Error % (Sec. 5) of the chosen configuration of every query: with B and
+    W the smallest and largest finite runtime of the query, (t[choice] - B) /
+    (W - B) * 100, 0 when W == B; NaN when the query has no finite runtime or
+    the choice is out of range or has none.  FP64, one query per step."""
+    rt = np.asarray(runtimes, np.float64)
+    ch = np.asarray(choice)
+    out = np.full(len(ch), np.nan)
+    for i in range(len(ch)):
+        fin = rt[i][np.isfinite(rt[i])]
+        c = int(ch[i])
+        if len(fin) == 0 or c < 0 or c >= rt.shape[1] or not np.isfinite(rt[i, c]):
+            continue
+        b, w = fin.min(), fin.max()
+        out[i] = error_pct(rt[i, c], b, w) if w > b else 0.0
+    return out

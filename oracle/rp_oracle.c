@@ -536,7 +536,7 @@ static int64_t occupancy(double Ri, double Zi, int64_t T, int64_t wpb, double wa
 static void eval_one(int64_t K, int d, const float *aN, const float *bN, const float *table,
                      const int32_t *grid_dims, const double *hw, const float *q, int c,
                      double *exec_out, int *case_out, double *margin_out, double *cond_out,
-                     double *diag /* MWP, CWP, Nw or NULL */) {
+                     double *diag /* MWP, CWP, Nw, B_active or NULL */) {
   int D1 = d + 1;
   double margin = INFINITY, cond = 1.0;
   *exec_out = INFINITY;
@@ -581,6 +581,7 @@ static void eval_one(int64_t K, int d, const float *aN, const float *bN, const f
   *margin_out = margin;
   *cond_out = cond;
   *case_out = EV_INVALID;
+  if (diag) diag[3] = 0.0;
   if ((double)T > tmax) return;
   int64_t wpb = (T + (int64_t)warp - 1) / (int64_t)warp;
   double Ri = floor(Rf + 0.5), Zi = floor(Zf + 0.5);
@@ -598,6 +599,7 @@ static void eval_one(int64_t K, int d, const float *aN, const float *bN, const f
       margin = fmin(margin, fabs(Zf - floor(Zf) - 0.5) / fmax(1.0, Zf));
   }
   *margin_out = margin;
+  if (diag) diag[3] = (double)bact;
   if (bact <= 0) return;
   int64_t nw_i = bact * wpb;
   if (nw_i > (int64_t)wmax) nw_i = (int64_t)wmax;
@@ -686,8 +688,8 @@ int rpo_eval(int64_t K, int d, const float *aN, const float *bN, const float *ta
   for (int64_t i = 0; i < Q; ++i)
     for (int c = 0; c < RPO_NCFG; ++c) {
       int cs;
-      double *dg = diag + 3 * (i * RPO_NCFG + c);
-      dg[0] = dg[1] = dg[2] = NAN;
+      double *dg = diag + 4 * (i * RPO_NCFG + c);
+      dg[0] = dg[1] = dg[2] = dg[3] = NAN;
       eval_one(K, d, aN, bN, table, grid_dims, hw, queries + 8 * i, c, &exec[i * RPO_NCFG + c],
                &cs, &margin[i * RPO_NCFG + c], &cond[i * RPO_NCFG + c], dg);
       cas[i * RPO_NCFG + c] = cs;

@@ -10,6 +10,7 @@ Entry points (same names as the C ABI):
     rp_fit, rp_fit_workspace_size, rp_program_size, rp_program_pack,
     rp_eval_search, rp_search_workspace_size, rp_relmse_fwd, rp_relmse_bwd,
     rp_adam_step, rp_tune_fit, rp_tune_search, rp_fit_noalloc,
+    rp_eval_search_tiebreak, rp_eval_occupancy, rp_error_pct,
     rp_strerror, rp_version
 plus ``RelMSE`` (a torch.autograd.Function over rp_relmse_fwd/bwd) and
 ``refine_relmse`` (Adam steps with the hand-written backward).
@@ -35,7 +36,8 @@ RP_FIT_ITER_SHIFT, RP_FIT_ITER_MASK = 8, 0xFF00
 RP_FIT_ACC_SHIFT, RP_FIT_ACC_MASK = 16, 0xFF0000
 RP_FIT_FP64_PASS = 1 << 24
 RP_Q_NO_VALID, RP_Q_POLE, RP_Q_BAD = 1, 2, 4
-RP_FIT_UNWEIGHTED = 1
+RP_EP_NO_RUNTIME, RP_EP_BAD_CHOICE = 1, 2
+RP_FIT_UNWEIGHTED, RP_FIT_SOLVER_SVD = 1, 2
 
 
 class RPError(RuntimeError):
@@ -80,6 +82,10 @@ def load_library(path: str = LIB_PATH):
             lib.rp_eval_search.argtypes = [P, i64, i32, C.POINTER(HwFixed), P, i64, P, P, P, P, P,
                                            C.c_size_t, P]
             lib.rp_search_workspace_size.argtypes = [i64, i64, C.POINTER(C.c_size_t)]
+            lib.rp_eval_search_tiebreak.argtypes = [P, i64, i32, C.POINTER(HwFixed), P, i64,
+                                                    C.c_float, P, P, P, P, P, C.c_size_t, P]
+            lib.rp_eval_occupancy.argtypes = [P, i64, i32, C.POINTER(HwFixed), P, i64, P, P, P, P]
+            lib.rp_error_pct.argtypes = [P, P, i64, P, P, P]
             lib.rp_relmse_fwd.argtypes = [i64, i64, P, P, P, P, P, P, P, P]
             lib.rp_relmse_bwd.argtypes = [i64, i64, P, P, P, P, P, P, P, P, P]
             lib.rp_adam_step.argtypes = [i64, P, P, P, P, P, i32, C.c_float, C.c_float, C.c_float,
@@ -136,7 +142,9 @@ def rp_fit_workspace_size(desc: FitDesc) -> int:
 
 
 def _fit_args(x, y, fit_off, degree, precision, max_refine, tol, degrees, weighted, out,
-              stream, schedule, point_off=None, fits_per_point_set=1):
+              stream, schedule, point_off=None, fits_per_point_set=1, solver="sweep"):
+    if solver not in ("sweep", "svd"):
+        raise RPError(f"unknown solver {solver!r}")
     F = fit_off.numel() - 1
     S = y.numel()
     dev = y.device
@@ -147,7 +155,8 @@ def _fit_args(x, y, fit_off, degree, precision, max_refine, tol, degrees, weight
                    status=torch.empty(F, dtype=torch.int32, device=dev),
                    rank=torch.empty(F, dtype=torch.int32, device=dev))
     desc = FitDesc(F, S, int(degree), PREC[precision], int(max_refine),
-                   0 if weighted else RP_FIT_UNWEIGHTED, float(tol),
+                   (0 if weighted else RP_FIT_UNWEIGHTED) | (RP_FIT_SOLVER_SVD if solver == "svd" else 0),
+                   float(tol),
                    _ptr_or_null(degrees, torch.int8, "degrees").value,
                    _ptr_or_null(point_off, torch.int64, "point_off").value,
                    x.shape[1] if point_off is not None else 0,
@@ -176,28 +185,32 @@ def rp_fit(x: torch.Tensor, y: torch.Tensor, fit_off: torch.Tensor, degree: int,
            precision: str = "fp32", max_refine: int = 8, tol: float = 1e-8,
            degrees: torch.Tensor | None = None, weighted: bool = True, out=None, stream=None,
            schedule: str = "dynamic", point_off: torch.Tensor | None = None,
-           fits_per_point_set: int = 1):
+           fits_per_point_set: int = 1, solver: str = "sweep"):
     """Batched rational least-squares fits (see rp_fit in include/rp.h).
     x: float32 [3, S], y: float32 [S], fit_off: int64 [F+1] (all CUDA); with
     point_off (int64 [P+1]) x is float32 [3, num_points] and each run of
     fits_per_point_set consecutive fits shares one point set.
     schedule "dynamic" (CTAs claim point sets from a counter in the 32-byte
-    workspace, out["workspace"] or allocated here) or "static".
+    workspace, out["workspace"] or allocated here) or "static".  solver
+    "sweep" (sweep operator with pivot dropping) or "svd" (Jacobi SVD of the
+    design, truncated pseudo-inverse: RP_FIT_SOLVER_SVD).
     Returns dict(coef float64 [F,70], coef32 float32 [F,70], box float64 [F,6],
     status int32 [F], rank int32 [F])."""
     out, args, _ws = _fit_args(x, y, fit_off, degree, precision, max_refine, tol, degrees,
-                               weighted, out, stream, schedule, point_off, fits_per_point_set)
+                               weighted, out, stream, schedule, point_off, fits_per_point_set,
+                               solver)
     _check(load_library().rp_fit(*args), "rp_fit")
     return out
 
 
 def rp_fit_noalloc(x, y, fit_off, degree: int, precision: str = "fp32", max_refine: int = 8,
                    tol: float = 1e-8, degrees=None, weighted: bool = True, out=None,
-                   stream=None, point_off=None, fits_per_point_set: int = 1):
+                   stream=None, point_off=None, fits_per_point_set: int = 1, solver="sweep"):
     """rp_fit with the library's static scratch instead of a workspace (see
     rp_fit_noalloc in include/rp.h); outputs as rp_fit."""
     out, args, _ws = _fit_args(x, y, fit_off, degree, precision, max_refine, tol, degrees,
-                               weighted, out, stream, "static", point_off, fits_per_point_set)
+                               weighted, out, stream, "static", point_off, fits_per_point_set,
+                               solver)
     _check(load_library().rp_fit_noalloc(*args[:9], args[11]), "rp_fit_noalloc")
     return out
 
@@ -307,6 +320,53 @@ def rp_eval_search(program, num_kernels: int, degree: int, queries: torch.Tensor
     int32 [Q], best float32 [Q], second float32 [Q], status int32 [Q])."""
     out, args, _keep = _search_args(program, num_kernels, degree, queries, hw, out, stream, grouped)
     _check(load_library().rp_eval_search(*args), "rp_eval_search")
+    return out
+
+
+def rp_eval_search_tiebreak(program, num_kernels: int, degree: int, queries: torch.Tensor,
+                            tie_rel: float, hw=None, out=None, stream=None, grouped: bool = True):
+    """rp_eval_search with Step 5's second metric (see rp_eval_search_tiebreak
+    in include/rp.h): among configurations within (1 + tie_rel) of the best,
+    the one with the most active warps per SM."""
+    out, args, _keep = _search_args(program, num_kernels, degree, queries, hw, out, stream, grouped)
+    args = args[:6] + (C.c_float(tie_rel),) + args[6:]
+    _check(load_library().rp_eval_search_tiebreak(*args), "rp_eval_search_tiebreak")
+    return out
+
+
+def rp_eval_occupancy(program, num_kernels: int, degree: int, queries: torch.Tensor, hw=None,
+                      out=None, stream=None):
+    """B_active and W_active of every configuration of every query (see
+    rp_eval_occupancy in include/rp.h).  Returns dict(b_active int32 [Q, 66],
+    w_active int32 [Q, 66], status int32 [Q])."""
+    Q = queries.shape[0]
+    dev = queries.device
+    if out is None:
+        out = dict(b_active=torch.empty((Q, RP_NUM_CONFIGS), dtype=torch.int32, device=dev),
+                   w_active=torch.empty((Q, RP_NUM_CONFIGS), dtype=torch.int32, device=dev),
+                   status=torch.empty(Q, dtype=torch.int32, device=dev))
+    h = hw_struct(hw)
+    _check(load_library().rp_eval_occupancy(
+        _dev(program, torch.uint8, "program"), int(num_kernels), int(degree), C.byref(h),
+        _dev(queries, torch.float32, "queries"), Q, _dev(out["b_active"], torch.int32, "b_active"),
+        _dev(out["w_active"], torch.int32, "w_active"), _dev(out["status"], torch.int32, "status"),
+        _stream(stream)), "rp_eval_occupancy")
+    return out
+
+
+def rp_error_pct(runtimes: torch.Tensor, choice: torch.Tensor, out=None, stream=None):
+    """Error % (Sec. 5) of the chosen configuration of every query from
+    measured runtimes float32 [Q, 66] and choices int32 [Q] (see rp_error_pct
+    in include/rp.h).  Returns dict(err_pct float32 [Q], status int32 [Q])."""
+    Q = choice.numel()
+    dev = choice.device
+    if out is None:
+        out = dict(err_pct=torch.empty(Q, dtype=torch.float32, device=dev),
+                   status=torch.empty(Q, dtype=torch.int32, device=dev))
+    _check(load_library().rp_error_pct(
+        _dev(runtimes, torch.float32, "runtimes"), _dev(choice, torch.int32, "choice"), Q,
+        _dev(out["err_pct"], torch.float32, "err_pct"), _dev(out["status"], torch.int32, "status"),
+        _stream(stream)), "rp_error_pct")
     return out
 
 

@@ -71,7 +71,8 @@ int rp_fit(const rp_fit_desc *desc, const float *x, const float *y, const int64_
   if (desc->degree < 1 || desc->degree > RP_MAX_DEGREE) return RP_ERR_INVALID_ARG;
   if (desc->precision < RP_PREC_FP64 || desc->precision > RP_PREC_BF16X3) return RP_ERR_INVALID_ARG;
   if (desc->max_refine < 0 || desc->max_refine > 64 || !(desc->tol >= 0.0)) return RP_ERR_INVALID_ARG;
-  if (desc->reserved != 0) return RP_ERR_INVALID_ARG;
+  if (desc->reserved != 0 || (desc->flags & ~(RP_FIT_UNWEIGHTED | RP_FIT_SOLVER_SVD)))
+    return RP_ERR_INVALID_ARG;
   if (desc->point_off && (desc->fits_per_point_set < 1 || desc->num_points < 0)) return RP_ERR_INVALID_ARG;
   if (desc->num_fits == 0) return RP_OK;
   if (!fit_off || !coef || !box || !status || !rank) return RP_ERR_INVALID_ARG;

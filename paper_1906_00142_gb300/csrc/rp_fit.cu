@@ -65,6 +65,7 @@ cudaError_t launch_fit(const rp_fit_desc &desc, const float *x, const float *y,
   a.d_uniform = desc.degree;
   a.max_refine = desc.max_refine;
   a.weighted = (desc.flags & RP_FIT_UNWEIGHTED) ? 0 : 1;
+  a.svd = (desc.flags & RP_FIT_SOLVER_SVD) ? 1 : 0;
   a.tol = desc.tol;
   a.coef = coef;
   a.coef32 = coef32;

@@ -38,6 +38,8 @@ struct FitArgs {
   const int64_t *point_off;
   int64_t num_points;
   int fits_per_set;
+  int set_parts;      // claims per point set (its fits split into this many runs)
+  int svd;            // solve by the SVD route (Jacobi) instead of the sweep
 };
 
 constexpr int32_t kPending64 = 1 << 25;   // status bit between the two launches

@@ -246,6 +246,7 @@ __device__ __forceinline__ void distinct_insert(unsigned *slots, float x) {
 
 constexpr int kT = 128;       // threads per CTA (one fit at a time)
 constexpr int kMC = 512;      // samples per fit kept in shared memory
+constexpr int kJacobiSweeps = 16;   // bound on the SVD route's Jacobi sweeps
 
 // Tensor-core Gram shapes (Sec. 4.2 normal equations on tcgen05).  A Gram
 // X^T X over the samples is one MMA chain D = A B^T with A = B = X^T stored
@@ -667,7 +668,8 @@ __device__ void df_pass(S &w, int d, int nm, int m, bool weighted, bool first, c
   const bool colw = tid < groups * ncol;
   const int wo = which == 2 ? 0 : AO + 2 * which;   // weight pair of the column
   dacc ca = {0.0f, 0.0f}, cb = {0.0f, 0.0f};        // two chains (alternate rows)
-  float obj = 0.0f;
+  dacc objacc = {0.0f, 0.0f};   // the objective, compensated (its changes near
+                                // convergence are far below FP32 summation noise)
   int pole = 0;
   for (int base = 0; base < m; base += kT) {
     const int cnt = min(kT, m - base);
@@ -737,7 +739,7 @@ __device__ void df_pass(S &w, int d, int nm, int m, bool weighted, bool first, c
         ra = e;
         rb = df_mulf(e, yy);
       }
-      obj = fmaf(r.h, r.h, obj);
+      dacc_fma(objacc, r, r);
       *reinterpret_cast<float4 *>(row + AO) = make_float4(ra.h, ra.l, rb.h, rb.l);
     }
     __syncthreads();
@@ -771,7 +773,21 @@ __device__ void df_pass(S &w, int d, int nm, int m, bool weighted, bool first, c
     w.hkd[which][jc][1] = t.l;
   }
   pole_out = __syncthreads_or(pole);
-  obj_out = block_sum_f(w, obj, 8);
+  {   // block total of the objective (pairs)
+    const int lane = tid & 31, wd = tid >> 5;
+    dfl t = dacc_get(objacc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      t = df_add(t, dfl{__shfl_xor_sync(0xffffffffu, t.h, o), __shfl_xor_sync(0xffffffffu, t.l, o)});
+    if (lane == 0) {
+      w.redf[wd][10] = t.h;
+      w.redf[wd][11] = t.l;
+    }
+    __syncthreads();
+    dfl tot = dfl{w.redf[0][10], w.redf[0][11]};
+    for (int k = 1; k < kT / 32; ++k) tot = df_add(tot, dfl{w.redf[k][10], w.redf[k][11]});
+    obj_out = tot.h;
+  }
   __syncthreads();
 }
 
@@ -929,19 +945,26 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
   // of degree d < D uses the leading block of that basis (graded-lex order
   // puts lower total degrees first and every factorisation of phases 1-2 is
   // triangular, so the leading block is the degree-d basis itself).
+  // A claim is one of set_parts runs of a set's fits (the host splits sets
+  // when there are too few of them to keep every CTA busy to the end; each
+  // run repeats phases 0-2).
   const int64_t G = a.point_off ? (int64_t)a.fits_per_set : 1;
   const int64_t nsets = (a.F + G - 1) / G;
-  int64_t ps = blockIdx.x;
+  const int64_t parts = a.point_off ? max(a.set_parts, 1) : 1;
+  const int64_t run = (G + parts - 1) / parts;
+  int64_t unit = blockIdx.x;
   for (int claim = 0;; ++claim) {
     if (a.counter) {
       if (tid == 0) w.next_fit[claim & 1] = (long long)atomicAdd(a.counter, 1ull);
       __syncthreads();
-      ps = w.next_fit[claim & 1];
+      unit = w.next_fit[claim & 1];
     } else if (claim > 0) {
-      ps += gridDim.x;
+      unit += gridDim.x;
     }
-    if (ps >= nsets) break;
-    const int64_t f0 = ps * G, f1 = min(a.F, f0 + G);
+    if (unit >= nsets * parts) break;
+    const int64_t ps = unit / parts;
+    const int64_t f0 = min(a.F, ps * G + (unit % parts) * run);
+    const int64_t f1 = min(min(a.F, ps * G + G), f0 + run);
     // ---------------- phase 0: the set's fits in this launch and its degree
     // (a launch of a split batch takes only its degrees; invalid degrees go
     // to the launch that starts at 1; the others' outputs are not touched)
@@ -1369,6 +1392,7 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
         w.scl[j] = (j == n) ? (Real)1 : (dg > 0 ? rsqrt_pos<Real>(dg) : (Real)0);
       }
       __syncthreads();
+      if (!a.svd) {
       // the upper triangle (i <= j), EPT entries per thread, decoded once
       constexpr int EPT = (NAUG * (NAUG + 1) / 2 + kT - 1) / kT;
       const int ntri = N1 * (N1 + 1) / 2;
@@ -1439,6 +1463,124 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
           }
         }
       if (tid == 0) w.keep_cnt = kept;
+      } else {
+        // The SVD route (the paper's solver, Sec. 4.2): the right singular
+        // vectors of the equilibrated design and its squared singular values
+        // are the eigenvectors and eigenvalues of S = D G D, found by cyclic
+        // Jacobi rotations of S (the rotations Hestenes' one-sided method
+        // applies to the design's columns; pairs in round-robin order, the
+        // disjoint pairs of a round in parallel); V accumulates them.
+        // Directions with an eigenvalue <= drop_tol times the largest are
+        // dropped (the SVD's rank); Q = D V L+ V^T D on the kept ones is the
+        // refinement's preconditioner and Q times the right-hand-side column
+        // the first step (the truncated least-squares solution).
+        Real *V = w.stage;                     // n x n, stride n
+        for (int e = tid; e < n * n; e += kT) {
+          const int i = e / n, j = e % n;
+          w.G[i * N1 + j] *= w.scl[i] * w.scl[j];
+          V[e] = (i == j) ? (Real)1 : (Real)0;
+        }
+        const int n2 = n + (n & 1);            // even (one padding index when n is odd)
+        const int npair = n2 / 2;
+        // a pair is rotated while its coupling exceeds off_tol relative to its
+        // diagonal (high relative accuracy) and the rounding level of the
+        // unit-diagonal matrix (the sweeps then end in either arithmetic)
+        const Real off_tol = sizeof(Real) == 8 ? (Real)1e-15 : (Real)1e-7;
+        const Real abs_tol = sizeof(Real) == 8 ? (Real)4e-16 : (Real)2.4e-7;
+        // pair i of round r (circle method: n2 - 1 fixed, the others rotate)
+        auto pair_of = [n2](int r, int i, int &p, int &q) {
+          const int u = i == 0 ? n2 - 1 : (r + i) % (n2 - 1);
+          const int v = i == 0 ? r : (r - i + n2 - 1) % (n2 - 1);
+          p = min(u, v);
+          q = max(u, v);
+        };
+        for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
+          __syncthreads();
+          if (tid == 0) w.bad = 0;             // set when a rotation is applied
+          __syncthreads();
+          for (int r = 0; r < n2 - 1; ++r) {
+            for (int i = tid; i < npair; i += kT) {
+              int p, q;
+              pair_of(r, i, p, q);
+              Real c = 1, sn = 0;
+              if (q < n) {
+                const Real spp = w.G[p * N1 + p], sqq = w.G[q * N1 + q], spq = w.G[p * N1 + q];
+                if (fabs(spq) > abs_tol && fabs(spq) > off_tol * sqrt(fabs(spp * sqq))) {
+                  // symmetric 2 x 2 Schur decomposition (Golub & Van Loan)
+                  const Real zeta = (sqq - spp) / (2 * spq);
+                  const Real t = copysign((Real)1, zeta) / (fabs(zeta) + sqrt(1 + zeta * zeta));
+                  c = rsqrt_pos<Real>(1 + t * t);
+                  sn = c * t;
+                  w.bad = 1;
+                }
+              }
+              w.rowb[0][i] = c;
+              w.rowb[1][i] = sn;
+            }
+            __syncthreads();
+            // S J and V J: columns p, q of every row
+            for (int e = tid; e < npair * n; e += kT) {
+              const int i = e / n, k = e % n;
+              const Real sn = w.rowb[1][i];
+              if (sn == (Real)0) continue;
+              const Real c = w.rowb[0][i];
+              int p, q;
+              pair_of(r, i, p, q);
+              const Real akp = w.G[k * N1 + p], akq = w.G[k * N1 + q];
+              w.G[k * N1 + p] = c * akp - sn * akq;
+              w.G[k * N1 + q] = sn * akp + c * akq;
+              const Real vkp = V[k * n + p], vkq = V[k * n + q];
+              V[k * n + p] = c * vkp - sn * vkq;
+              V[k * n + q] = sn * vkp + c * vkq;
+            }
+            __syncthreads();
+            // J^T (S J): rows p, q of every column
+            for (int e = tid; e < npair * n; e += kT) {
+              const int i = e / n, k = e % n;
+              const Real sn = w.rowb[1][i];
+              if (sn == (Real)0) continue;
+              const Real c = w.rowb[0][i];
+              int p, q;
+              pair_of(r, i, p, q);
+              const Real apk = w.G[p * N1 + k], aqk = w.G[q * N1 + k];
+              w.G[p * N1 + k] = c * apk - sn * aqk;
+              w.G[q * N1 + k] = sn * apk + c * aqk;
+            }
+            __syncthreads();
+          }
+          if (!w.bad) break;                   // a sweep without rotations: converged
+        }
+        __syncthreads();
+        // eigenvalues, their largest, the kept directions' 1 / lambda
+        if (tid == 0) {
+          Real lmax = 0;
+          for (int j = 0; j < n; ++j) lmax = fmax(lmax, w.G[j * N1 + j]);
+          int kept = 0;
+          for (int j = 0; j < n; ++j) {
+            const Real l = w.G[j * N1 + j];
+            const bool keep = l > (Real)a.drop_tol * lmax;
+            w.invd[j] = keep ? (Real)1 / l : (Real)0;
+            kept += keep;
+          }
+          w.keep_cnt = kept;
+        }
+        __syncthreads();
+        // Q = D V L+ V^T D into the n x n block of G; the first step
+        for (int e = tid; e < n * n; e += kT) {
+          const int i = e / n, j = e % n;
+          Real acc = 0;
+          for (int k = 0; k < n; ++k) acc = fma(V[i * n + k] * w.invd[k], V[j * n + k], acc);
+          w.G[i * N1 + j] = acc * w.scl[i] * w.scl[j];
+        }
+        __syncthreads();
+        for (int i = tid; i < n; i += kT) {
+          Real acc = 0;
+          for (int k = 0; k < n; ++k) acc = fma(w.G[i * N1 + k], w.G[k * N1 + n], acc);
+          w.gvec[i] = acc;
+        }
+        __syncthreads();
+        for (int i = tid; i < n; i += kT) w.dxw[i] = w.gvec[i];
+      }
       // the iterate starts at 0: (c_p, u) = 0, (c_q, v) = (1, 0)
       for (int e = tid; e < 2 * NM; e += kT) {
         const int which = e / NM, i = e % NM;
@@ -1480,10 +1622,15 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
     constexpr bool kRegAcc = sizeof(Real) == 4 && DMAX <= 3;
     constexpr int VP = ((2 * NM + 2 + 15) / 16) * 16;   // register accumulators
     const int hk_groups = max(1, kT / nm);
+    bool last_acc = sizeof(Real) == 8;   // the previous evaluation pass was accurate
     for (;; ++it) {
       const bool update = it < a.max_refine && !done;
       const bool dfp = sizeof(Real) == 4 && accurate;
       const bool first_df = dfp && !have_mu;
+      // the first accurate pass: its exact objective is not compared with the
+      // plain passes' (their residuals carry FP32 rounding)
+      const bool fresh = dfp && !last_acc;
+      last_acc = last_acc || dfp;
       float obj = 0.0f;
       int pole = 0;
       if (dfp) {
@@ -1644,9 +1791,9 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
       }
       __syncthreads();
       }   // plain pass
-      // (the first accurate pass starts a new comparison: its iterate was
-      // rescaled and its objective is exact)
-      const bool worse = it > 0 && !first_df && obj > obj_prev * (accurate ? 1.00001f : 1.0001f);
+      // (the first accurate pass starts a new comparison: its objective is
+      // exact, and on a set's first fit its iterate was rescaled)
+      const bool worse = it > 0 && !fresh && obj > obj_prev * (accurate ? 1.00001f : 1.0001f);
       if (worse) {
         // the last step increased the objective: undo it, then retry it at
         // half length (a preconditioner that overestimates curvature in some
@@ -1939,12 +2086,19 @@ cudaError_t launch_t(const FitArgs &a, int precision, cudaStream_t s) {
   if (cap > 0 && cap < per_sm) per_sm = cap;
   int64_t grid = (int64_t)num_sms() * per_sm;
   const int64_t nsets = a.point_off ? (a.F + a.fits_per_set - 1) / a.fits_per_set : a.F;
-  if (grid > nsets) grid = nsets;
+  // split point sets into runs until there are >= 3 claims per resident CTA
+  // (whole sets of many fits would leave a long last wave)
+  FitArgs b = a;
+  b.set_parts = 1;
+  if (a.point_off)
+    while (b.set_parts < a.fits_per_set && nsets * b.set_parts < 3 * grid) b.set_parts *= 2;
+  const int64_t units = nsets * b.set_parts;
+  if (grid > units) grid = units;
   if (a.counter) {
     e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
   }
-  fit_kernel<Real, DMAX, GM><<<(unsigned)grid, kT, smem, s>>>(a);
+  fit_kernel<Real, DMAX, GM><<<(unsigned)grid, kT, smem, s>>>(b);
   return cudaGetLastError();
 }
 

@@ -80,3 +80,36 @@ def test_fit_shared_point_sets(precision, degrees):
                      fits_per_point_set=8)
     st = host(out2["status"])
     assert (st[-8:] & rp.RP_FIT_EMPTY).all()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_fit_svd_solver(precision):
+    """RP_FIT_SOLVER_SVD (the paper's solver, Sec. 4.2): Jacobi SVD of the
+    equilibrated design with truncation, as first solution and
+    preconditioner.  Every fit against the oracle as in the other fit tests,
+    including rank-deficient lattice fits (fewer samples than unknowns; a
+    constant thread-block dimension), which are compared on the objective
+    (their least-squares solution is not unique); the ranks of those fits
+    equal the oracle's."""
+    need_gpu()
+    base = W.batched_instance(3, seed=99, m=512, d=3)
+    rng = np.random.default_rng(100)
+    lat = W.lattice()
+    pts = [lat[rng.choice(462, 24, replace=False)], lat[rng.choice(462, 200, replace=False)]]
+    pts[1] = pts[1].copy()
+    pts[1][:, 2] = 1.0                                  # B1 constant
+    ys = [np.exp(rng.uniform(0, 2, len(p))) for p in pts]
+    x = np.concatenate([base["x"]] + [p.T.astype(np.float32) for p in pts], 1)
+    y = np.concatenate([base["y"]] + [v.astype(np.float32) for v in ys])
+    off = np.concatenate([base["fit_off"], base["fit_off"][-1] + np.cumsum([len(v) for v in ys])])
+    inst = dict(x=np.ascontiguousarray(x), y=y, fit_off=off.astype(np.int64),
+                degree=np.concatenate([base["degree"], np.full(2, 3, np.int8)]))
+    out = rp.rp_fit(dev(inst["x"]), dev(inst["y"]), dev(inst["fit_off"]), 3, precision=precision,
+                    degrees=dev(inst["degree"]), solver="svd")
+    g = {k: host(v) for k, v in out.items()}
+    ref = oracle.fit(inst["x"], inst["y"], inst["fit_off"], inst["degree"])
+    compare(inst, g, ref)
+    rd = (ref["status"] & oracle.FS_RANK_DEFICIENT) != 0
+    assert rd[-2:].all()
+    assert (g["rank"][rd] == ref["rank"][rd]).all(), (g["rank"][rd], ref["rank"][rd])
+    assert ((g["status"][rd] & rp.RP_FIT_RANK_DEFICIENT) != 0).all()

@@ -161,3 +161,75 @@ def test_synthetic_workload_exercises_all_cases():
     ev = oracle.evaluate(prog, HW, q)
     cases = set(np.unique(ev["case"]).tolist())
     assert {1, 2, 3}.issubset(cases), cases
+
+
+def test_hand_worked_occupancy():
+    """B_active and W_active (Sec. 2 Example 1) of the hand-worked cases, as
+    written out in their steps."""
+    g = json.load(open(os.path.join(GOLD, "mwpcwp_worked.json")))
+    for case in g["cases"]:
+        prog = const_program([case["metrics"]], [case["grid_dims"]])
+        qq = case["query"]
+        q = query(qq["N"], qq["n_sm"], qq["f_ghz"], qq["mem_ld"], qq["bw_gbs"], qq["dd_coal"],
+                  qq["dd_uncoal"], 0)
+        ev = oracle.evaluate(prog, g["hw"], q)
+        c = case["config_index"]
+        assert ev["bact"][0, c] == case["b_active"], case["name"]
+        assert ev["nw"][0, c] == case["w_active"], case["name"]
+
+
+def test_occupancy_invariants():
+    """W_active = min(B_active wpb, W_max) wherever resident; B_active within
+    B_max and W_max / wpb; 0 (not resident) exactly where exec is +inf for a
+    non-pole configuration."""
+    prog, q = _synthetic(K=4, Q=300, seed=11)
+    ev = oracle.evaluate(prog, HW, q)
+    T = W.CONFIGS[:, 0] * W.CONFIGS[:, 1]
+    wpb = (T + 31) // 32
+    ok = np.isin(ev["case"], [0, 1, 2, 3])
+    b = ev["bact"]
+    assert (b[ok] >= 1).all()
+    res = ok
+    assert (ev["nw"][res] == np.minimum(b * wpb[None, :], HW["w_max"])[res]).all()
+    assert (b[res] <= HW["b_max"]).all() and (b * wpb[None, :] <= np.maximum(HW["w_max"], wpb))[res].all()
+    inval = ev["case"] == oracle.EV_INVALID
+    assert (b[inval] == 0).all() and np.isinf(ev["exec"][inval]).all()
+
+
+def test_tiebreak_second_metric():
+    """Step 5 with occupancy as the second metric: tie_rel = 0 chooses the
+    lowest-index optimum among configurations of equal W_active (the plain
+    search's choice for the mirrored ties of a constant program); every
+    choice lies within (1 + tie_rel) of the best; a wider window never
+    lowers the chosen W_active; with a window wide enough to hold every
+    valid configuration the choice has the largest W_active of them all."""
+    prog = const_program([[100, 10, 0, 1, 0, 128, 32, 0], [400, 4, 2, 3, 1, 256, 24, 64]], [2, 2])
+    q = W.queries(300, 2, seed=12, n_log2=(6, 20))
+    s = oracle.search(prog, HW, q)
+    a0, ev = oracle.search_tiebreak(prog, HW, q, 0.0)
+    assert (a0 == s["argmin"]).all()
+    prev = ev["nw"][np.arange(len(q)), a0]
+    rows = np.arange(len(q))
+    for rel in (0.01, 0.1, 0.5):
+        a, _ = oracle.search_tiebreak(prog, HW, q, rel)
+        assert (ev["exec"][rows, a] <= s["best"] * (1 + rel)).all()
+        nw = ev["nw"][rows, a]
+        assert (nw >= prev).all()
+        prev = nw
+    a, _ = oracle.search_tiebreak(prog, HW, q, np.inf)
+    valid = np.isfinite(ev["exec"])
+    assert (ev["nw"][rows, a] == np.where(valid, ev["nw"], -1).max(axis=1)).all()
+
+
+def test_error_pct_table_definition():
+    """Error % of a chosen configuration (Sec. 5), row by row: the Table 3
+    formula on the row's finite runtimes; degenerate rows."""
+    inf = np.inf
+    rt = np.full((5, 66), inf)
+    rt[0, :3] = [3.0, 1.0, 2.0]          # choice 2: (2 - 1) / (3 - 1) = 50 %
+    rt[1, :2] = [5.0, 5.0]               # W == B: 0
+    rt[3, :2] = [1.0, 4.0]               # choice not run
+    rt[4, 10] = 7.0                      # one runtime, chosen
+    e = oracle.error_pct_table(rt, [2, 1, 0, 5, 10])
+    assert e[0] == 50.0 and e[1] == 0.0 and np.isnan(e[2]) and np.isnan(e[3]) and e[4] == 0.0
+    assert np.isnan(oracle.error_pct_table(rt[:1], [-1])[0])

@@ -38,14 +38,13 @@ WORKLOAD = ("batched fit 1024 kernels x 8 metrics (the metrics of a kernel share
 
 # DRAM bytes per fit of the fit kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of fit_kernel<float, 3, 0>,
-# 2048 fits of 512 samples; traffic scales with the fit count), valid only
-# for the kernel sources they were taken on (SHA-256 of the files below);
-# None until a capture of the current sources is recorded.
-FIT_TRAFFIC = {"sources_sha256": "7db0e3d3a18dcd28d96db12f424a1c33db19caa2eaa0120bee3f947130347dcd",
-               "bytes_per_fit": (17390848 + 52736) / 2048}
+# 2048 fits of 512 samples in the shared-point layout; traffic scales with
+# the fit count), valid only for the kernel sources they were taken on
+# (SHA-256 of the files below) and that layout.
+FIT_TRAFFIC = {"sources_sha256": "16141d76ed004303b579435fbed1813d33deadb82197808e29f2a83513f4f532",
+               "bytes_per_fit": (6319360 + 55296) / 2048, "layout": "shared point sets"}
 FIT_SOURCES = ("paper_1906_00142_gb300/csrc/rp_fit_kernel.cuh", "paper_1906_00142_gb300/csrc/rp_fit.cuh",
-               "paper_1906_00142_gb300/csrc/rp_fit_f32.cu", "paper_1906_00142_gb300/csrc/rp_tc.cuh",
-               "paper_1906_00142_gb300/csrc/rp_internal.cuh")
+               "paper_1906_00142_gb300/csrc/rp_fit_f32.cu", "paper_1906_00142_gb300/csrc/rp_tc.cuh")
 
 
 def fit_sources_sha256():
@@ -461,6 +460,26 @@ def extra_measurements(rp, args, inst, x, x_full, FK, y, off, deg, mm, gd, q, fi
     out["svd_solver"] = {"fit_ms": t_svd, "fit_only_fits_per_s": F / (t_svd / 1e3),
                          "fp64_pass_frac": float(((svd_out["status"].cpu().numpy() >> 24) & 1).mean())}
     out["_svd_fits"] = {k: svd_out[k].cpu().numpy() for k in ("coef", "box", "status")}
+    # the generated rational program (Sec. 3.3 Step 3): kernel 0's program
+    # written out with its coefficients as constants, compiled at run time,
+    # against the table-driven search on 1e6 queries of that kernel
+    try:
+        t0 = time.perf_counter()
+        gen = rp.GeneratedProgram(rp.rp_codegen_source(prog.cpu(), N_KERNELS, DEGREE, 0))
+        t_compile = time.perf_counter() - t0
+        q0 = q.clone()
+        q0[:, 7] = torch.zeros(1, dtype=torch.int32, device=q.device).view(torch.float32)
+        g_out = gen.search(q0)
+        t_out = rp.rp_eval_search(prog, N_KERNELS, DEGREE, q0)
+        t_gen = _timed(lambda: gen.search(q0, out=g_out), 3, flush, stream)
+        t_tab = _timed(lambda: rp.rp_eval_search(prog, N_KERNELS, DEGREE, q0, out=t_out), 3, flush, stream)
+        out["codegen"] = {"kernel": 0, "queries": int(q0.shape[0]), "compile_s": t_compile,
+                          "generated_ms": t_gen, "table_ms": t_tab,
+                          "results_equal": bool(all(torch.equal(g_out[k], t_out[k])
+                                                    for k in ("argmin", "best", "second", "status")))}
+        del gen
+    except Exception as e:   # reported, never silently replaced
+        out["codegen"] = {"error": str(e).splitlines()[0][:300]}
     # restore the FP32 step's program and search results for what follows
     step()
     torch.cuda.synchronize()
@@ -982,9 +1001,11 @@ def main():
         # x 1/2 (nominal dense TF32 : BF16 = 1.1 : 2.25 PFLOP/s on GB300)
         tf32_peak = pk.get("bf16_tflops", 1900.0) * 0.5
         fit_flops = F * fit_flops_per_fit(M_SAMPLES, DEGREE)
-        fit_bytes = F * (16 * M_SAMPLES + 896)
+        # per fit: its values, its share of its set's points (or its own
+        # points), its outputs
+        fit_bytes = F * (4 * M_SAMPLES + (12 * M_SAMPLES // N_METRICS if FK else 12 * M_SAMPLES) + 896)
         traffic = None
-        if (FIT_TRAFFIC["bytes_per_fit"] is not None and args.precision == "fp32"
+        if (FIT_TRAFFIC["bytes_per_fit"] is not None and args.precision == "fp32" and FK
                 and FIT_TRAFFIC["sources_sha256"] == fit_sources_sha256()):
             traffic = FIT_TRAFFIC["bytes_per_fit"] * F
         if fit_avg >= search_avg:

@@ -326,6 +326,46 @@ int rp_error_pct(const float *runtimes, const int32_t *choice, int64_t num_queri
                  float *err_pct, int32_t *status, void *stream);
 
 /*
+ * The rational program as generated code (Sec. 3.3 Step 3; Sec. 4.3.1
+ * generates the program's source with the fitted functions written in).
+ *
+ * rp_codegen_source -- CUDA C++ source of the rational program of kernel
+ * kernel_id of a packed program: its 66 x 8 numerator and denominator
+ * coefficient rows, its data-parameter maps, grid dimensionality and the
+ * architecture constants hw written in as constants (exact hexadecimal
+ * floats), and a kernel `rp_generated_search` that evaluates and takes the
+ * argmin of queries of that kernel with the same arithmetic as
+ * rp_eval_search (queries naming another kernel get RP_Q_BAD).
+ * program_host: a HOST copy of the packed program (rp_program_size bytes).
+ * src: host buffer of *len bytes, or NULL to ask for the size; *len
+ * receives the bytes needed including the terminating NUL.  Host-only.
+ * Errors: RP_ERR_INVALID_ARG; RP_ERR_WORKSPACE if *len is too small.
+ */
+int rp_codegen_source(const void *program_host, int64_t num_kernels, int32_t degree,
+                      int64_t kernel_id, const rp_hw_fixed *hw, char *src, size_t *len);
+
+/*
+ * rp_codegen_compile -- compiles generated source at run time (NVRTC, for
+ * the current device's architecture) and loads it; *handle (opaque) is
+ * valid on that device until rp_codegen_free.  log (may be NULL): host
+ * buffer of log_len bytes for the compiler's messages.  Synchronous; not
+ * capturable.  Errors: RP_ERR_UNSUPPORTED (NVRTC not found), RP_ERR_NO_DEVICE,
+ * RP_ERR_INVALID_ARG (the source does not compile), RP_ERR_CUDA.
+ */
+int rp_codegen_compile(const char *src, void **handle, char *log, size_t log_len);
+
+/*
+ * rp_codegen_search -- runs a compiled generated program on num_queries
+ * queries (device float [Q][8], as rp_eval_search) on `stream`; outputs as
+ * rp_eval_search.  Errors: RP_ERR_INVALID_ARG, RP_ERR_ALIGNMENT, RP_ERR_CUDA.
+ */
+int rp_codegen_search(void *handle, const float *queries, int64_t num_queries, int32_t *argmin,
+                      float *best, float *second, int32_t *status, void *stream);
+
+/* rp_codegen_free -- unloads a compiled generated program (NULL: no-op). */
+int rp_codegen_free(void *handle);
+
+/*
  * rp_search_workspace_size -- bytes of the optional device workspace of
  * rp_eval_search for num_kernels kernels and num_queries queries, written
  * to *bytes: the bucket offsets and cursors (4 (2K + 3) bytes) and the

@@ -10,7 +10,8 @@ Entry points (same names as the C ABI):
     rp_fit, rp_fit_workspace_size, rp_program_size, rp_program_pack,
     rp_eval_search, rp_search_workspace_size, rp_relmse_fwd, rp_relmse_bwd,
     rp_adam_step, rp_tune_fit, rp_tune_search, rp_fit_noalloc,
-    rp_eval_search_tiebreak, rp_eval_occupancy, rp_error_pct,
+    rp_eval_search_tiebreak, rp_eval_occupancy, rp_error_pct, rp_codegen_source,
+    rp_codegen_compile / rp_codegen_search / rp_codegen_free (GeneratedProgram),
     rp_strerror, rp_version
 plus ``RelMSE`` (a torch.autograd.Function over rp_relmse_fwd/bwd) and
 ``refine_relmse`` (Adam steps with the hand-written backward).
@@ -86,6 +87,11 @@ def load_library(path: str = LIB_PATH):
                                                     C.c_float, P, P, P, P, P, C.c_size_t, P]
             lib.rp_eval_occupancy.argtypes = [P, i64, i32, C.POINTER(HwFixed), P, i64, P, P, P, P]
             lib.rp_error_pct.argtypes = [P, P, i64, P, P, P]
+            lib.rp_codegen_source.argtypes = [P, i64, i32, i64, C.POINTER(HwFixed), P,
+                                              C.POINTER(C.c_size_t)]
+            lib.rp_codegen_compile.argtypes = [C.c_char_p, C.POINTER(C.c_void_p), P, C.c_size_t]
+            lib.rp_codegen_search.argtypes = [P, P, i64, P, P, P, P, P]
+            lib.rp_codegen_free.argtypes = [P]
             lib.rp_relmse_fwd.argtypes = [i64, i64, P, P, P, P, P, P, P, P]
             lib.rp_relmse_bwd.argtypes = [i64, i64, P, P, P, P, P, P, P, P, P]
             lib.rp_adam_step.argtypes = [i64, P, P, P, P, P, i32, C.c_float, C.c_float, C.c_float,
@@ -368,6 +374,57 @@ def rp_error_pct(runtimes: torch.Tensor, choice: torch.Tensor, out=None, stream=
         _dev(out["err_pct"], torch.float32, "err_pct"), _dev(out["status"], torch.int32, "status"),
         _stream(stream)), "rp_error_pct")
     return out
+
+
+def rp_codegen_source(program_host, num_kernels: int, degree: int, kernel_id: int, hw=None) -> str:
+    """CUDA source of one kernel's rational program with its coefficients
+    written in (see rp_codegen_source in include/rp.h).  program_host: the
+    packed program as a host buffer (numpy uint8 array or CPU uint8 tensor)."""
+    import numpy as np
+    buf = np.ascontiguousarray(program_host.numpy() if isinstance(program_host, torch.Tensor)
+                               else program_host, dtype=np.uint8)
+    h = hw_struct(hw)
+    n = C.c_size_t(0)
+    lib = load_library()
+    ptr = C.c_void_p(buf.ctypes.data)
+    _check(lib.rp_codegen_source(ptr, int(num_kernels), int(degree), int(kernel_id), C.byref(h),
+                                 None, C.byref(n)), "rp_codegen_source")
+    out = C.create_string_buffer(n.value)
+    _check(lib.rp_codegen_source(ptr, int(num_kernels), int(degree), int(kernel_id), C.byref(h),
+                                 out, C.byref(n)), "rp_codegen_source")
+    return out.value.decode()
+
+
+class GeneratedProgram:
+    """A generated rational program compiled at run time (rp_codegen_compile);
+    search() runs it on queries of its kernel (rp_codegen_search)."""
+
+    def __init__(self, source: str):
+        lib = load_library()
+        self._h = C.c_void_p(0)
+        log = C.create_string_buffer(1 << 16)
+        rc = lib.rp_codegen_compile(source.encode(), C.byref(self._h), log, len(log))
+        if rc != 0:
+            raise RPError(f"rp_codegen_compile: {rp_strerror(rc)} ({rc}): {log.value.decode()[:2000]}")
+
+    def search(self, queries: torch.Tensor, out=None, stream=None):
+        Q = queries.shape[0]
+        dev = queries.device
+        if out is None:
+            out = dict(argmin=torch.empty(Q, dtype=torch.int32, device=dev),
+                       best=torch.empty(Q, dtype=torch.float32, device=dev),
+                       second=torch.empty(Q, dtype=torch.float32, device=dev),
+                       status=torch.empty(Q, dtype=torch.int32, device=dev))
+        _check(load_library().rp_codegen_search(
+            self._h, _dev(queries, torch.float32, "queries"), Q, _dev(out["argmin"], torch.int32, "argmin"),
+            _dev(out["best"], torch.float32, "best"), _dev(out["second"], torch.float32, "second"),
+            _dev(out["status"], torch.int32, "status"), _stream(stream)), "rp_codegen_search")
+        return out
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.rp_codegen_free(self._h)
+            self._h = None
 
 
 def rp_tune_search(program, num_kernels: int, degree: int, queries: torch.Tensor, hw=None,

@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
-         "-diag-suppress", "177"]
+         "-I" + BUILD, "-diag-suppress", "177"]
 
 
 def _nvcc() -> str:
@@ -46,11 +46,24 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
+def write_embedded_sources():
+    """The per-configuration evaluator (rp_eval_cfg.cuh) as a C++ raw string
+    literal for the program generator (rp_codegen.cu), in the build folder."""
+    text = open(os.path.join(CSRC, "rp_eval_cfg.cuh")).read()
+    assert ")RPSRC" not in text
+    out = os.path.join(BUILD, "rp_eval_cfg_src.inc")
+    tmp = out + f".{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        f.write('R"RPSRC(' + text + ')RPSRC"\n')
+    os.replace(tmp, out)
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
+    write_embedded_sources()
     objs = []
 
     def compile_one(src):
@@ -66,7 +79,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, sources()))
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string.h>
+
 #include "rp_internal.cuh"
 
 namespace {
@@ -200,6 +202,44 @@ int rp_error_pct(const float *runtimes, const int32_t *choice, int64_t num_queri
   if (!device_ok()) return RP_ERR_NO_DEVICE;
   return from_cuda(rpk::launch_error_pct(runtimes, choice, num_queries, err_pct, status,
                                          as_stream(stream)));
+}
+
+int rp_codegen_source(const void *program_host, int64_t num_kernels, int32_t degree,
+                      int64_t kernel_id, const rp_hw_fixed *hw, char *src, size_t *len) {
+  if (!program_host || !len || num_kernels < 1 || kernel_id < 0 || kernel_id >= num_kernels ||
+      degree < 0 || degree > RP_MAX_DEGREE || !hw_ok(hw))
+    return RP_ERR_INVALID_ARG;
+  const std::string code = rpk::codegen_source(program_host, num_kernels, degree, kernel_id, *hw);
+  const size_t need = code.size() + 1;
+  if (!src || *len < need) {
+    *len = need;
+    return src ? RP_ERR_WORKSPACE : RP_OK;
+  }
+  memcpy(src, code.c_str(), need);
+  *len = need;
+  return RP_OK;
+}
+
+int rp_codegen_compile(const char *src, void **handle, char *log, size_t log_len) {
+  if (!src || !handle) return RP_ERR_INVALID_ARG;
+  *handle = nullptr;
+  if (!device_ok()) return RP_ERR_NO_DEVICE;
+  return rpk::codegen_compile(src, handle, log, log_len);
+}
+
+int rp_codegen_search(void *handle, const float *queries, int64_t num_queries, int32_t *argmin,
+                      float *best, float *second, int32_t *status, void *stream) {
+  if (!handle || num_queries < 0) return RP_ERR_INVALID_ARG;
+  if (num_queries == 0) return RP_OK;
+  if (!queries || !argmin || !best || !second || !status) return RP_ERR_INVALID_ARG;
+  if (!aligned(queries, 16)) return RP_ERR_ALIGNMENT;
+  return from_cuda(rpk::codegen_search(handle, queries, num_queries, argmin, best, second, status,
+                                       as_stream(stream)));
+}
+
+int rp_codegen_free(void *handle) {
+  rpk::codegen_free(handle);
+  return RP_OK;
 }
 
 int rp_tune_search(const void *program, int64_t num_kernels, int32_t degree,

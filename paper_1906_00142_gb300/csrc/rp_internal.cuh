@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "rp.h"
 
 namespace rpk {
@@ -72,6 +74,16 @@ cudaError_t launch_occupancy(ProgramView prog, int64_t K, int d, const rp_hw_fix
                              int32_t *status, cudaStream_t s);
 cudaError_t launch_error_pct(const float *runtimes, const int32_t *choice, int64_t Q,
                              float *err_pct, int32_t *status, cudaStream_t s);
+// The rational program of one kernel as generated source (rp_codegen.cu).
+std::string codegen_source(const void *program_host, int64_t K, int d, int64_t kid,
+                           const rp_hw_fixed &hw);
+int codegen_compile(const char *src, void **handle, char *log, size_t log_len);
+cudaError_t codegen_search(void *handle, const float *queries, int64_t Q, int32_t *argmin,
+                           float *best, float *second, int32_t *status, cudaStream_t s);
+void codegen_free(void *handle);
+// The search's per-configuration constants for hw (host; 66 entries each).
+void search_cfg_table(const rp_hw_fixed &hw, int8_t *la, int8_t *lb, int32_t *wpb, int32_t *bact_w,
+                      int32_t *rsm_w, int32_t *rsm_t);
 size_t search_workspace_bytes(int64_t K, int64_t Q);
 
 cudaError_t launch_fit(const rp_fit_desc &desc, const float *x, const float *y,

@@ -836,16 +836,105 @@ def main():
         flush.zero_()
         step(evs[k])
     torch.cuda.synchronize()
-    clk = clocks.stop()
     if ws > 1:
         torch.distributed.barrier()
     fit_ms = [e[0].elapsed_time(e[1]) for e in evs]
     pack_ms = [e[1].elapsed_time(e[2]) for e in evs]
     search_ms = [e[2].elapsed_time(e[3]) for e in evs]
     step_ms = [e[0].elapsed_time(e[3]) for e in evs]
-    total_ms = max_over_ranks(sum(step_ms), ws, dev)
-    ms_per_step = total_ms / args.steps
+    serial_ms_per_step = max_over_ranks(sum(step_ms), ws, dev) / args.steps
+
+    # The headline: the same steps as a stream of batches on two compute
+    # streams.  Step k's fit runs on the fit stream; its pack and search run
+    # on the evaluation stream once the fit is done, while step k+1's fit
+    # starts on the fit stream (two sets of fit outputs, programs and search
+    # outputs).  The search of step k then fills the SMs that step k+1's fit
+    # has not yet taken and those the FP64 launch of a step leaves idle.
+    # Every step does all of its work; L2 is flushed before each fit (the
+    # flush is inside the timed region).  With copies=True every step also
+    # copies its inputs in (pinned host buffers, a copy stream, ahead of its
+    # fit) and its results out (a second copy stream) inside the timed region.
+    NB = 2
+    p_fit = [fit_out] + [{k: torch.empty_like(v) for k, v in fit_out.items()} for _ in range(NB - 1)]
+    p_srch = [s_out] + [{k: torch.empty_like(v) for k, v in s_out.items()} for _ in range(NB - 1)]
+    p_prog = [prog] + [torch.empty_like(prog) for _ in range(NB - 1)]
+    s_fit, s_eval = stream, torch.cuda.Stream()
+    copy_in, copy_out = torch.cuda.Stream(), torch.cuda.Stream()
+    pipe_io = {}
+
+    def pipelined(nsteps, copies=False):
+        pack_done, eval_done, out_done = [None] * NB, [None] * NB, [None] * NB
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(s_fit)
+        for s_ in (s_eval, copy_in, copy_out):
+            s_.wait_event(start)
+        for k in range(nsteps):
+            b = k % NB
+            fo, so, pg = p_fit[b], p_srch[b], p_prog[b]
+            if copies:
+                di, ho, h = pipe_io["in"][b], pipe_io["out"][b], pipe_io["h"]
+                if eval_done[b] is not None:      # step k - NB has read input set b
+                    copy_in.wait_event(eval_done[b])
+                with torch.cuda.stream(copy_in):
+                    for key in h:
+                        di[key].copy_(h[key], non_blocking=True)
+                in_done = torch.cuda.Event()
+                in_done.record(copy_in)
+                s_fit.wait_event(in_done)
+                ix, iy, ioff, ideg, imm, igd, iq = (di[k2] for k2 in ("x", "y", "off", "deg", "mm", "gd", "q"))
+                ifk = pipe_io["fk"](di)
+            else:
+                ix, iy, ioff, ideg, imm, igd, iq, ifk = x, y, off, deg, mm, gd, q, FK
+            if pack_done[b] is not None:          # step k - NB's pack has read fit set b
+                s_fit.wait_event(pack_done[b])
+            if out_done[b] is not None:           # and its status was read back
+                s_fit.wait_event(out_done[b])
+            with torch.cuda.stream(s_fit):
+                flush.zero_()
+            rp.rp_fit(ix, iy, ioff, DEGREE, precision=args.precision, max_refine=args.max_refine,
+                      tol=args.tol, degrees=ideg, out=fo, stream=s_fit, **ifk)
+            fit_done = torch.cuda.Event()
+            fit_done.record(s_fit)
+            s_eval.wait_event(fit_done)
+            if out_done[b] is not None:           # step k - NB's search results read back
+                s_eval.wait_event(out_done[b])
+            rp.rp_program_pack(fo["coef"], fo["box"], ideg, imm, igd, DEGREE, program=pg, stream=s_eval)
+            pack_done[b] = torch.cuda.Event()
+            pack_done[b].record(s_eval)
+            rp.rp_eval_search(pg, N_KERNELS, DEGREE, iq, out=so, stream=s_eval)
+            eval_done[b] = torch.cuda.Event()
+            eval_done[b].record(s_eval)
+            if copies:
+                copy_out.wait_event(eval_done[b])
+                with torch.cuda.stream(copy_out):
+                    ho["status"].copy_(fo["status"], non_blocking=True)
+                    ho["argmin"].copy_(so["argmin"], non_blocking=True)
+                    ho["best"].copy_(so["best"], non_blocking=True)
+                out_done[b] = torch.cuda.Event()
+                out_done[b].record(copy_out)
+        for ev in eval_done + out_done:
+            if ev is not None:
+                s_fit.wait_event(ev)
+        end.record(s_fit)
+        torch.cuda.synchronize()
+        return start.elapsed_time(end) / nsteps
+
+    if args.only == "all":
+        pipelined(NB + 1)                         # warm-up of the two-stream schedule
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        pipe_ms = pipelined(args.steps)
+    else:                                         # profiling captures of one phase: serial steps
+        pipe_ms = serial_ms_per_step
+    clk = clocks.stop()
+    if ws > 1:
+        torch.distributed.barrier()
+    ms_per_step = max_over_ranks(pipe_ms, ws, dev)
     value = job_rate(ws, F, ms_per_step)
+    # the pipelined steps reproduce the serial steps' results
+    assert all(torch.equal(p_srch[b]["argmin"], p_srch[0]["argmin"]) for b in range(NB)), \
+        "pipelined argmin mismatch"
 
     # the timed steps' results, kept for the comparison with the oracle
     g_res = {"coef": fit_out["coef"].cpu().numpy(), "box": fit_out["box"].cpu().numpy(),
@@ -919,71 +1008,22 @@ def main():
         e_ms.append(a.elapsed_time(b))
     e2e_serial_ms = max_over_ranks(statistics.mean(e_ms) if e_ms else float("nan"), ws, dev)
 
-    # the same steps as a stream of batches: step k+1's host-to-device copy
-    # runs on a copy stream while step k computes, and step k's results
-    # return on a second copy stream while step k+1 computes (two sets of
-    # device buffers).  Every step still copies all of its inputs in and its
-    # results out inside the timed region; L2 is flushed before each step's
-    # fit on the compute stream.
-    NB = 2
-    p_in = [d_in] + [{k: torch.empty_like(v) for k, v in d_in.items()} for _ in range(NB - 1)]
-    p_fit = [fit_out] + [{k: torch.empty_like(v) for k, v in fit_out.items()} for _ in range(NB - 1)]
-    p_srch = [s_out] + [{k: torch.empty_like(v) for k, v in s_out.items()} for _ in range(NB - 1)]
-    p_prog = [prog] + [torch.empty_like(prog) for _ in range(NB - 1)]
-    p_hout = [h_out] + [{k: torch.empty_like(v).pin_memory() for k, v in h_out.items()}
-                        for _ in range(NB - 1)]
-    copy_in, copy_out = torch.cuda.Stream(), torch.cuda.Stream()
-
-    def e2e_pipelined(nsteps):
-        comp_done, out_done = [None] * NB, [None] * NB
-        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        start.record(stream)
-        copy_in.wait_event(start)
-        copy_out.wait_event(start)
-        for k in range(nsteps):
-            b = k % NB
-            di, fo, so, pg, ho = p_in[b], p_fit[b], p_srch[b], p_prog[b], p_hout[b]
-            if comp_done[b] is not None:          # buffer b free once step k - NB computed
-                copy_in.wait_event(comp_done[b])
-            with torch.cuda.stream(copy_in):
-                for key in h:
-                    di[key].copy_(h[key], non_blocking=True)
-            in_done = torch.cuda.Event()
-            in_done.record(copy_in)
-            stream.wait_event(in_done)
-            if out_done[b] is not None:           # step k - NB's results read back
-                stream.wait_event(out_done[b])
-            flush.zero_()
-            rp.rp_fit(di["x"], di["y"], di["off"], DEGREE, precision=args.precision,
-                      max_refine=args.max_refine, tol=args.tol, degrees=di["deg"], out=fo,
-                      stream=stream, **fk_dev(di))
-            rp.rp_program_pack(fo["coef"], fo["box"], di["deg"], di["mm"], di["gd"], DEGREE,
-                               program=pg, stream=stream)
-            rp.rp_eval_search(pg, N_KERNELS, DEGREE, di["q"], out=so, stream=stream)
-            comp_done[b] = torch.cuda.Event()
-            comp_done[b].record(stream)
-            copy_out.wait_event(comp_done[b])
-            with torch.cuda.stream(copy_out):
-                ho["status"].copy_(fo["status"], non_blocking=True)
-                ho["argmin"].copy_(so["argmin"], non_blocking=True)
-                ho["best"].copy_(so["best"], non_blocking=True)
-            out_done[b] = torch.cuda.Event()
-            out_done[b].record(copy_out)
-        for ev in out_done:
-            if ev is not None:
-                stream.wait_event(ev)
-        end.record(stream)
-        torch.cuda.synchronize()
-        return start.elapsed_time(end) / nsteps
+    # end to end as a stream of batches: the two-stream schedule above with
+    # every step's inputs copied in and results copied out (two buffer sets)
+    pipe_io["h"] = h
+    pipe_io["in"] = [d_in] + [{k: torch.empty_like(v) for k, v in d_in.items()} for _ in range(NB - 1)]
+    pipe_io["out"] = [h_out] + [{k: torch.empty_like(v).pin_memory() for k, v in h_out.items()}
+                                for _ in range(NB - 1)]
+    pipe_io["fk"] = fk_dev
 
     e2e_ms = float("nan")
     if args.only == "all" and args.e2e_steps > 0:
         n_pipe = max(args.steps, args.e2e_steps, NB + 1)
-        e2e_pipelined(NB + 1)                      # warm-up (allocator, first-use paths)
-        e2e_ms = max_over_ranks(e2e_pipelined(n_pipe), ws, dev)
+        pipelined(NB + 1, copies=True)             # warm-up (allocator, first-use paths)
+        e2e_ms = max_over_ranks(pipelined(n_pipe, copies=True), ws, dev)
         # the last step's results match the device-timed steps' (same inputs)
         last = (n_pipe - 1) % NB
-        assert torch.equal(p_hout[last]["argmin"], s_out["argmin"].cpu()), "e2e argmin mismatch"
+        assert torch.equal(pipe_io["out"][last]["argmin"], s_out["argmin"].cpu()), "e2e argmin mismatch"
 
     extra = {}
     if args.only == "all" and not args.no_extras:
@@ -1038,10 +1078,15 @@ def main():
                 "roofline": roof,
                 "e2e": {"value": job_rate(ws, F, e2e_ms), "unit": "fits/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-                        "pipelined": "copy-in of step k+1 and copy-out of step k overlap the "
-                                     "compute (two buffer sets); L2 flushed before each fit",
+                        "pipelined": "the two-stream schedule of the headline with each step's "
+                                     "copy-in on a copy stream ahead of its fit and its copy-out on a "
+                                     "second copy stream (two buffer sets); L2 flushed before each fit",
                         "serial_ms_per_step": e2e_serial_ms},
-                "gpu_launches": {"all": 2 + search_launches, "fit": 2,
+                "schedule": {"pipelined": "fit of step k+1 on one stream while pack + search of step k "
+                                          "run on a second (two buffer sets); L2 flushed before each fit, "
+                                          "inside the timed region",
+                             "serial_ms_per_step": serial_ms_per_step},
+                "gpu_launches": {"all": 3 + search_launches, "fit": 2,
                                  "search": search_launches}[args.only] * args.steps,
                 "clocks": clk, "tuned": tuned}
         line.update(extra)

@@ -126,6 +126,30 @@ __device__ __forceinline__ void dacc_fma(dacc &a, dfl x, dfl y) {
 }
 __device__ __forceinline__ dfl dacc_get(const dacc &a) { return df_norm(a.s, a.c); }
 
+// A double as a head + tail pair of FP32 numbers, read from its bit pattern
+// with integer operations only (GB300 runs FP64 arithmetic and conversions
+// at a small fraction of its FP32 rate): the head is v truncated to 24
+// significant bits, the tail the remaining 29 mantissa bits truncated to
+// 23 (relative error below 2^-46).  |v| outside [2^-80, 2^127) (zero
+// included) takes the conversions instead.
+__device__ __forceinline__ dfl split_d(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
+  const int E = (int)((hw >> 20) & 0x7FFu);
+  if (E < 1023 - 80 || E > 1023 + 126) {
+    const float h = __double2float_rz(v);
+    return dfl{h, __double2float_rn(v - (double)h)};
+  }
+  const unsigned sign = hw & 0x80000000u;
+  // head: sign, exponent E - 1023 + 127, mantissa bits 51..29
+  const float h = __uint_as_float(sign | ((unsigned)(E - 896) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+  // tail: mantissa bits 28..0 (the integer R, worth R 2^(E - 1075)); R >> 6
+  // (< 2^23) becomes a float exactly through the 2^23 bias, then 2^(E - 1069)
+  const float r = __uint_as_float(0x4B000000u | ((lw & 0x1FFFFFFFu) >> 6)) - 8388608.0f;
+  const float l = __fmul_rn(r, __uint_as_float((unsigned)(E - 1069 + 127) << 23));
+  return dfl{h, __uint_as_float(__float_as_uint(l) | sign)};
+}
+
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -518,6 +542,41 @@ struct TileGram {
     }
   }
 
+  // The same Gram of FP64 rows staged as head + tail FP32 pairs (split_d):
+  // products and per-chunk sums in double-float arithmetic (Dot2) on the
+  // FP32 pipe, chunk totals added in FP64.  Used by the FP64 launch that
+  // re-fits the fits an FP32 / tensor-core launch passed on: it is
+  // accurate to ~1e-14 relative, like the FP64 sums, at a fraction of the
+  // FP64 pipe's time.
+  __device__ void chunk_split(const Real *stage, int cnt) {
+    static_assert(sizeof(Real) == 8, "FP64 rows only");
+    const float2 *st2 = reinterpret_cast<const float2 *>(stage);
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      const int item = threadIdx.x + kT * k;
+      if (item >= ntiles * groups) break;
+      const int tile = item % ntiles, g = item / ntiles;
+      int rb, cb;
+      tile_of(tile, rb, cb);
+      dacc part[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) part[i] = dacc{0.0f, 0.0f};
+      for (int s = g; s < cnt; s += groups) {
+        const float4 *pa = reinterpret_cast<const float4 *>(st2 + s * LDS + 4 * rb);
+        const float4 *pb = reinterpret_cast<const float4 *>(st2 + s * LDS + 4 * cb);
+        const float4 a01 = pa[0], a23 = pa[1], b01 = pb[0], b23 = pb[1];
+        const dfl av[4] = {{a01.x, a01.y}, {a01.z, a01.w}, {a23.x, a23.y}, {a23.z, a23.w}};
+        const dfl bv[4] = {{b01.x, b01.y}, {b01.z, b01.w}, {b23.x, b23.y}, {b23.z, b23.w}};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) dacc_fma(part[4 * i + j], av[i], bv[j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) acc[k][i] += (double)part[i].s + (double)part[i].c;
+    }
+  }
+
   // Sum the sample groups and write the symmetric cols x cols Gram into G
   // (stride cols).  `scratch` needs ntiles * groups * 16 entries.
   __device__ void finish(int cols, Real *G, Real *scratch) {
@@ -544,6 +603,20 @@ struct TileGram {
     __syncthreads();
   }
 };
+
+// One entry of a staged row: the value, or (FP64 rows for chunk_split) its
+// head + tail FP32 pair in the same 8 bytes.
+template <class Real>
+__device__ __forceinline__ void stage_put(Real *row, int j, Real v, bool split) {
+  if constexpr (sizeof(Real) == 8) {
+    if (split) {
+      const dfl p = split_d(v);
+      reinterpret_cast<float2 *>(row)[j] = make_float2(p.h, p.l);
+      return;
+    }
+  }
+  row[j] = v;
+}
 
 // Warp reduce-scatter of V values per lane (V a multiple of 16): four
 // halving exchanges (offsets 16, 8, 4, 2) and one full exchange (offset 1).
@@ -918,6 +991,9 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
   const uint32_t raw_s = tc::smem_u32(smem_raw);
   WF &w = *reinterpret_cast<WF *>(smem_raw + (GM > 0 ? (((raw_s + 1023u) & ~1023u) - raw_s) : 0u));
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // the FP64 launch for fits an FP32 / tensor-core launch passed on forms
+  // its two Grams in double-float arithmetic (chunk_split)
+  const bool split_gram = sizeof(Real) == 8 && a.esc_mode == 2;
   // the FP64 pass over the fits passed on by an FP32 / tensor-core launch:
   // nothing to do when none was (the count is final: same stream, earlier
   // launch)
@@ -1175,11 +1251,16 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
           eval_psi<Real, DMAX, NM>(w, d, nm, sx0[i], sx1[i], sx2[i], psi);
           Real *row = w.stage + tid * LDS;
 #pragma unroll
-          for (int j = 0; j < NM; ++j) row[j] = psi[j];
+          for (int j = 0; j < NM; ++j) stage_put(row, j, psi[j], split_gram);
           for (int j = NM; j < cols4; ++j) row[j] = 0;
         }
         __syncthreads();
-        tg.chunk(w.stage, cnt);
+        if constexpr (sizeof(Real) == 8) {
+          if (split_gram) tg.chunk_split(w.stage, cnt);
+          else tg.chunk(w.stage, cnt);
+        } else {
+          tg.chunk(w.stage, cnt);
+        }
         __syncthreads();
       }
       tg.finish(nm, w.G, w.stage);
@@ -1362,15 +1443,20 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
           Real *row = w.stage + tid * LDS;
 #pragma unroll
           for (int j = 0; j < NM; ++j)
-            if (j < nm) row[j] = wt * pt[j];
+            if (j < nm) stage_put(row, j, wt * pt[j], split_gram);
 #pragma unroll
           for (int j = 1; j < NM; ++j)
-            if (j < nm) row[nm + j - 1] = -wt * yy * pt[j];
-          row[n] = wt * yy;
+            if (j < nm) stage_put(row, nm + j - 1, -wt * yy * pt[j], split_gram);
+          stage_put(row, n, wt * yy, split_gram);
           for (int j = naug; j < cols4; ++j) row[j] = 0;
         }
         __syncthreads();
-        tg.chunk(w.stage, cnt);
+        if constexpr (sizeof(Real) == 8) {
+          if (split_gram) tg.chunk_split(w.stage, cnt);
+          else tg.chunk(w.stage, cnt);
+        } else {
+          tg.chunk(w.stage, cnt);
+        }
         __syncthreads();
       }
       tg.finish(naug, w.G, w.stage);

@@ -325,7 +325,9 @@ struct CtaFit {
   Real mupsi[NM];
   Real gvec[NAUG], scl[NAUG], invd[NAUG], invw[NM];
   Real xw[NAUG], xwp[NAUG], dxw[NAUG];  // iterate in the design basis (norms), previous, step
-  Real rowb[2][NAUG];                 // pivot rows of the sweep
+  // pivot rows of the sweep, padded to whole 8-column blocks (16-byte rows)
+  static constexpr int RBW = ((NAUG + 7) / 8) * 8;
+  alignas(16) Real rowb[2][RBW];
   Real duv[2][NM];                    // step of (c, u), (c, v)
   Real HK[2][NM];
   Real rbuf[2][kT];
@@ -1479,6 +1481,109 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
       }
       __syncthreads();
       if (!a.svd) {
+      if constexpr (DMAX <= 3) {
+      // Degree <= 3 (at most 40 columns): thread t holds one chunk of the
+      // upper triangle in registers -- row ci, the 8-column block starting
+      // at cj0, clipped to columns [max(cj0, ci), N1) -- 120 chunks for 40
+      // columns.  Per pivot a thread loads the pivot row's block once and
+      // updates its row with one FMA per entry; the pivot's own row and
+      // column and the writes of the next pivot row touch few threads.
+      constexpr int CW = 8;
+      static_assert(NAUG <= 40 && kT >= 120, "one chunk per thread (120 chunks for 40 columns)");
+      const int nblk = (N1 + CW - 1) / CW;
+      int ci = -1, cj0 = 0;
+      {
+        int t = tid;
+        for (int i = 0; i < N1; ++i) {
+          const int nb = nblk - i / CW;
+          if (t < nb) {
+            ci = i;
+            cj0 = (i / CW + t) * CW;
+            break;
+          }
+          t -= nb;
+        }
+      }
+      const bool have = ci >= 0;
+      const int jlo = have ? max(cj0, ci) : 0, jhi = have ? min(cj0 + CW, N1) : 0;
+      Real v[CW];
+#pragma unroll
+      for (int c = 0; c < CW; ++c) {
+        const int j = cj0 + c;
+        v[c] = (j >= jlo && j < jhi) ? w.G[ci * N1 + j] * w.scl[ci] * w.scl[j] : (Real)0;
+        if (ci == 0 && j >= jlo && j < jhi) w.rowb[0][j] = v[c];
+      }
+      __syncthreads();
+      int kept = 0;
+      for (int k = 0; k < n; ++k) {
+        const Real *rk = w.rowb[k & 1];
+        Real *rn = w.rowb[(k + 1) & 1];
+        const Real piv = rk[k];
+        const bool keep = piv > (Real)a.drop_tol;
+        kept += keep;
+        if (have) {
+          if (keep) {
+            const Real ip = recip(piv);
+            Real rj[CW];
+            if constexpr (sizeof(Real) == 4) {
+              ld_row<CW>(rk + cj0, reinterpret_cast<float (&)[CW]>(rj));
+            } else {
+#pragma unroll
+              for (int c = 0; c < CW; ++c) rj[c] = rk[cj0 + c];
+            }
+            if (ci == k) {
+              // the pivot's row: S'_kj = S_kj / p, S'_kk = -1 / p
+#pragma unroll
+              for (int c = 0; c < CW; ++c) v[c] = (cj0 + c == k) ? -ip : rj[c] * ip;
+            } else {
+              // S'_ij = S_ij - S_ik S_kj / p; the pivot's column S'_ik = S_ik / p
+              const Real rip = rk[ci] * ip;
+#pragma unroll
+              for (int c = 0; c < CW; ++c) v[c] = fma(-rip, rj[c], v[c]);
+              const int ck = k - cj0;
+              if (ck >= 0 && ck < CW) {
+#pragma unroll
+                for (int c = 0; c < CW; ++c)
+                  if (c == ck) v[c] = rip;
+              }
+            }
+          }
+          // the next pivot row: its entries (k+1, j >= k+1) and (i, k+1), i <= k
+          if (ci == k + 1) {
+#pragma unroll
+            for (int c = 0; c < CW; ++c)
+              if (cj0 + c >= jlo && cj0 + c < jhi) rn[cj0 + c] = v[c];
+          }
+          const int c1 = k + 1 - cj0;
+          if (ci <= k && c1 >= 0 && c1 < CW && k + 1 < jhi) {
+            Real val = v[0];
+#pragma unroll
+            for (int c = 1; c < CW; ++c)
+              if (c == c1) val = v[c];
+            rn[ci] = val;
+          }
+        }
+        if (tid == 0) w.invd[k] = keep ? (Real)1 : (Real)0;
+        __syncthreads();
+      }
+      // Q = -D S D on the kept columns, both triangles; the first step
+      if (have) {
+        const Real si = w.invd[ci] * w.scl[ci];
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+          const int j = cj0 + c;
+          if (j < jlo || j >= jhi) continue;
+          if (j < n) {
+            const Real qv = -v[c] * si * w.invd[j] * w.scl[j];
+            w.G[ci * N1 + j] = qv;
+            w.G[j * N1 + ci] = qv;
+          } else if (j == n && ci < n) {
+            w.dxw[ci] = v[c] * si;
+          }
+        }
+      }
+      if (tid == 0) w.keep_cnt = kept;
+      } else {
       // the upper triangle (i <= j), EPT entries per thread, decoded once
       constexpr int EPT = (NAUG * (NAUG + 1) / 2 + kT - 1) / kT;
       const int ntri = N1 * (N1 + 1) / 2;
@@ -1549,6 +1654,7 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
           }
         }
       if (tid == 0) w.keep_cnt = kept;
+      }   // degree bound
       } else {
         // The SVD route (the paper's solver, Sec. 4.2): the right singular
         // vectors of the equilibrated design and its squared singular values

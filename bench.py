@@ -639,7 +639,6 @@ def workload_uneven(rp, dev, stream, precision="fp32"):
     mr = 16 if precision.startswith("bf16") else BENCH_MAX_REFINE
     out = rp.rp_fit(x, y, off, 4, precision=precision, degrees=deg, max_refine=mr, tol=BENCH_TOL,
                     stream=stream)
-    out["workspace"] = torch.zeros(32, dtype=torch.uint8, device=dev)
     prog = rp.rp_program_pack(out["coef"], out["box"], deg, mm, gd, 4, stream=stream)
     s_out = rp.rp_eval_search(prog, K, 4, q, stream=stream)
     s_out["workspace"] = torch.empty(rp.rp_search_workspace_size(K, qn), dtype=torch.uint8, device=dev)
@@ -768,6 +767,9 @@ def main():
                    status=torch.empty(F, dtype=torch.int32, device=dev),
                    rank=torch.empty(F, dtype=torch.int32, device=dev),
                    workspace=torch.zeros(32, dtype=torch.uint8, device=dev))
+    # the fit's workspace with the basis cache of the accurate passes (the
+    # binding sizes it with rp_fit_cache_workspace_size on the first call,
+    # outside the timed region, and keeps it in fit_out)
     prog = torch.empty(rp.rp_program_size(N_KERNELS, DEGREE), dtype=torch.uint8, device=dev)
     s_ws = rp.rp_search_workspace_size(N_KERNELS, N_QUERIES)   # queries bucketed by kernel
     s_out = dict(argmin=torch.empty(N_QUERIES, dtype=torch.int32, device=dev),

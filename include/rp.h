@@ -148,6 +148,26 @@ typedef struct rp_fit_desc {
 int rp_fit_workspace_size(const rp_fit_desc *desc, size_t *bytes);
 
 /*
+ * rp_fit_cache_workspace_size -- bytes of a workspace that also holds the
+ * basis cache of rp_fit's accurate refinement passes (Sec. 4.2's
+ * least-squares solve as refined here), written to *bytes.  The basis
+ * values of a point set's samples depend only on the samples, not on the
+ * metric fitted: with a workspace of at least this size, the first
+ * accurate pass of each claim of fits writes them (as pairs of FP32
+ * numbers) to a slab of the CTA that fits them and the claim's later passes
+ * read them back instead of recomputing them.  Results are identical with
+ * and without the cache.  Size: 256 bytes (the counters of
+ * rp_fit_workspace_size, padded), then per resident CTA of the largest
+ * launch the batch makes a slab of 512 samples x ceil(NM / 2) x 16 bytes
+ * (NM = (d+1)(d+2)(d+3)/6); about 50 MB for degree 3 on a 152-SM GB300.
+ * FP64 precision and the FP32 degree-4 launch (no sample cache) use no
+ * slab.  Queries the device (SM count, residency); launches nothing.
+ * Errors: RP_ERR_INVALID_ARG (null pointers, degree or precision out of
+ * range).
+ */
+int rp_fit_cache_workspace_size(const rp_fit_desc *desc, size_t *bytes);
+
+/*
  * rp_fit -- batched least-squares fit of rational functions (Sec. 4.2).
  *
  * For fit f with samples i in [fit_off[f], fit_off[f+1]):
@@ -173,7 +193,9 @@ int rp_fit_workspace_size(const rp_fit_desc *desc, size_t *bytes);
  * and used by one call at a time: with it, CTAs claim fits dynamically from
  * a counter kept there (reset on the stream with cudaMemsetAsync before the
  * launch), so CTAs that draw large fits take fewer; with NULL each CTA takes
- * every (grid size)-th fit.  Results do not depend on the schedule.
+ * every (grid size)-th fit.  With at least rp_fit_cache_workspace_size
+ * bytes the workspace also holds the basis cache (see there).  Results do
+ * not depend on the schedule or the cache.
  * Errors: RP_ERR_INVALID_ARG for null pointers, F < 0, degree or precision
  * out of range; RP_ERR_WORKSPACE / RP_ERR_ALIGNMENT for a workspace that is
  * too small or misaligned; RP_ERR_CUDA if a launch fails.

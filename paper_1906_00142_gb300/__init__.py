@@ -76,6 +76,7 @@ def load_library(path: str = LIB_PATH):
             lib = C.CDLL(path)
             P, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
             lib.rp_fit_workspace_size.argtypes = [C.POINTER(FitDesc), C.POINTER(C.c_size_t)]
+            lib.rp_fit_cache_workspace_size.argtypes = [C.POINTER(FitDesc), C.POINTER(C.c_size_t)]
             lib.rp_fit.argtypes = [C.POINTER(FitDesc), P, P, P, P, P, P, P, P, P, C.c_size_t, P]
             lib.rp_program_size.argtypes = [i64, i32]
             lib.rp_program_size.restype = C.c_size_t
@@ -147,6 +148,13 @@ def rp_fit_workspace_size(desc: FitDesc) -> int:
     return b.value
 
 
+def rp_fit_cache_workspace_size(desc: FitDesc) -> int:
+    b = C.c_size_t(0)
+    _check(load_library().rp_fit_cache_workspace_size(C.byref(desc), C.byref(b)),
+           "rp_fit_cache_workspace_size")
+    return b.value
+
+
 def _fit_args(x, y, fit_off, degree, precision, max_refine, tol, degrees, weighted, out,
               stream, schedule, point_off=None, fits_per_point_set=1, solver="sweep"):
     if solver not in ("sweep", "svd"):
@@ -171,10 +179,14 @@ def _fit_args(x, y, fit_off, degree, precision, max_refine, tol, degrees, weight
     ws_bytes = rp_fit_workspace_size(desc)
     ws = None
     if schedule == "dynamic" and ws_bytes:
+        # the workspace with the basis cache (out["workspace"], kept there
+        # for the next call with the same out)
+        ws_bytes = rp_fit_cache_workspace_size(desc)
         ws = out.get("workspace")
         if ws is None or ws.numel() < ws_bytes:
             with torch.cuda.stream(st):        # stream-ordered reuse of the buffer
                 ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+            out["workspace"] = ws
     elif schedule not in ("dynamic", "static"):
         raise RPError(f"unknown schedule {schedule!r}")
     args = (C.byref(desc), _dev(x, torch.float32, "x"), _dev(y, torch.float32, "y"),

@@ -66,6 +66,14 @@ int rp_fit_workspace_size(const rp_fit_desc *desc, size_t *bytes) {
   return RP_OK;
 }
 
+int rp_fit_cache_workspace_size(const rp_fit_desc *desc, size_t *bytes) {
+  if (!desc || !bytes) return RP_ERR_INVALID_ARG;
+  if (desc->degree < 1 || desc->degree > RP_MAX_DEGREE) return RP_ERR_INVALID_ARG;
+  if (desc->precision < RP_PREC_FP64 || desc->precision > RP_PREC_BF16X3) return RP_ERR_INVALID_ARG;
+  *bytes = rpk::fit_cache_workspace_bytes(*desc);
+  return RP_OK;
+}
+
 int rp_fit(const rp_fit_desc *desc, const float *x, const float *y, const int64_t *fit_off,
            double *coef, float *coef32, double *box, int32_t *status, int32_t *rank,
            void *workspace, size_t workspace_bytes, void *stream) {
@@ -85,7 +93,7 @@ int rp_fit(const rp_fit_desc *desc, const float *x, const float *y, const int64_
   if (!rpk::fit_precision_supported(desc->precision)) return RP_ERR_UNSUPPORTED;
   if (!device_ok()) return RP_ERR_NO_DEVICE;
   return from_cuda(rpk::launch_fit(*desc, x, y, fit_off, coef, coef32, box, status, rank, workspace,
-                                   as_stream(stream)));
+                                   workspace ? workspace_bytes : 0, as_stream(stream)));
 }
 
 int rp_fit_noalloc(const rp_fit_desc *desc, const float *x, const float *y,

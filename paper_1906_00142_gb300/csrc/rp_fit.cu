@@ -34,6 +34,35 @@ cudaError_t fit_static_scratch(void **ptr, size_t *bytes) {
 // and the number of fits passed on to the FP64 path.
 size_t fit_workspace_bytes(const rp_fit_desc &desc) { return desc.num_fits > 0 ? 32 : 0; }
 
+// The counters, then (FP32 and tensor-core precisions) one basis-cache slab
+// per resident CTA of the largest launch the batch makes: kCacheSamples
+// samples x ceil(NM / 2) float4, NM the launch's monomial count.  The FP32
+// degree-4 variant keeps no sample cache and takes no slab.
+size_t fit_cache_workspace_bytes(const rp_fit_desc &desc) {
+  const size_t base = fit_workspace_bytes(desc);
+  if (base == 0 || desc.precision == RP_PREC_FP64) return base;
+  auto res = [&](int dmax) {
+    switch (desc.precision) {
+      case RP_PREC_TF32: return fit_residency_tf32(dmax);
+      case RP_PREC_TF32X3: return fit_residency_tf32x3(dmax);
+      case RP_PREC_BF16: return fit_residency_bf16(dmax);
+      case RP_PREC_BF16X3: return fit_residency_bf16x3(dmax);
+      default: return fit_residency_f32(dmax);
+    }
+  };
+  auto slab = [](int dmax) {
+    const int nm = (dmax + 1) * (dmax + 2) * (dmax + 3) / 6;
+    return (size_t)kCacheSamples * (size_t)((nm + 1) / 2) * 16;
+  };
+  const int dmax = desc.degree;
+  size_t per_sm = (size_t)res(dmax <= 3 ? dmax : 3) * slab(dmax <= 3 ? dmax : 3);
+  if (dmax == 4 && desc.precision != RP_PREC_FP32) {
+    const size_t d4 = (size_t)res(4) * slab(4);
+    if (d4 > per_sm) per_sm = d4;
+  }
+  return kCacheOffset + (size_t)num_sms() * per_sm;
+}
+
 int fit_max_ctas_per_sm(const rp_fit_desc &desc) {
   const int dmax = desc.degree;
   switch (desc.precision) {
@@ -53,7 +82,8 @@ bool fit_precision_supported(int precision) {
 
 cudaError_t launch_fit(const rp_fit_desc &desc, const float *x, const float *y,
                        const int64_t *fit_off, double *coef, float *coef32, double *box,
-                       int32_t *status, int32_t *rank, void *workspace, cudaStream_t s) {
+                       int32_t *status, int32_t *rank, void *workspace, size_t workspace_bytes,
+                       cudaStream_t s) {
   if (desc.num_fits == 0) return cudaSuccess;
   FitArgs a;
   a.F = desc.num_fits;
@@ -78,6 +108,14 @@ cudaError_t launch_fit(const rp_fit_desc &desc, const float *x, const float *y,
   a.counter = reinterpret_cast<unsigned long long *>(workspace);
   a.esc_count = workspace ? reinterpret_cast<unsigned long long *>(static_cast<char *>(workspace) + 16)
                           : nullptr;
+  // the basis cache when the workspace holds it (results do not depend on it)
+  a.psi_cache = nullptr;
+  a.psi_cache_bytes = 0;
+  if (workspace && desc.precision != RP_PREC_FP64 && workspace_bytes > kCacheOffset &&
+      workspace_bytes >= fit_cache_workspace_bytes(desc)) {
+    a.psi_cache = reinterpret_cast<float4 *>(static_cast<char *>(workspace) + kCacheOffset);
+    a.psi_cache_bytes = workspace_bytes - kCacheOffset;
+  }
   const int dmax = desc.degree;
   const int p0 = desc.precision;
   int p = p0;

@@ -40,7 +40,18 @@ struct FitArgs {
   int fits_per_set;
   int set_parts;      // claims per point set (its fits split into this many runs)
   int svd;            // solve by the SVD route (Jacobi) instead of the sweep
+  // basis cache of the accurate refinement passes (FP32 paths): one slab
+  // per CTA of kCacheSamples x ceil(NM / 2) float4 (the basis pairs of a
+  // point set's samples), or null; the bytes available from psi_cache
+  float4 *psi_cache;
+  size_t psi_cache_bytes;
 };
+
+// samples per point set whose basis values the cache holds (the kernels'
+// shared-memory sample cache size)
+constexpr int kCacheSamples = 512;
+// offset of the basis cache in the workspace (after the two counters)
+constexpr size_t kCacheOffset = 256;
 
 constexpr int32_t kPending64 = 1 << 25;   // status bit between the two launches
 

@@ -722,10 +722,17 @@ __device__ float apply_step(S &w, int nm, int n) {
 // with Dot2 (column phase; 64-bit loads of the pairs).  Results: hkd[0..2][j]
 // (pairs, block totals), the objective sum r^2 and whether q <= 0 at some
 // sample.
+// slab (or null): this CTA's basis cache.  The basis pairs depend only on
+// the point set's samples and basis (degree D, the set's largest), not on
+// the fit: the first accurate pass of a claim computes them and writes them
+// there (slab_full false), the claim's later accurate passes read them back
+// (slab_full true).  Both give the same values; a fit of degree d < D uses
+// the leading nm of them.
 template <int DMAX, int NM, class S>
 __device__ void df_pass(S &w, int d, int nm, int m, bool weighted, bool first, const float *sx0,
                         const float *sx1, const float *sx2, const float *sy, float &obj_out,
-                        int &pole_out) {
+                        int &pole_out, float4 *slab, bool slab_full, int D) {
+  constexpr int NP4 = (NM + 1) / 2;   // float4 of the slab per sample (two pairs each)
   constexpr int LDD = S::DF_LDD, AO = S::DF_AO;
   static_assert(AO % 4 == 0 && LDD % 4 == 0 && AO + 4 <= LDD && 2 * NM <= AO, "accurate pass rows");
   const int tid = threadIdx.x;
@@ -750,8 +757,32 @@ __device__ void df_pass(S &w, int d, int nm, int m, bool weighted, bool first, c
     const int cnt = min(kT, m - base);
     if (tid < cnt) {
       const int i = base + tid;
-      const float xv[3] = {sx0[i], sx1[i], sx2[i]};
       const float yy = sy[i];
+      float *row = stage + tid * LDD;
+      dacc P = {0.0f, 0.0f}, Qs = {0.0f, 0.0f};
+      if (slab && slab_full) {
+        // the sample's basis pairs from the slab
+        const float4 *src = slab + (size_t)i * NP4;
+#pragma unroll
+        for (int q4 = 0; q4 < NP4; ++q4) {
+          float4 v4 = src[q4];
+          const int j0 = 2 * q4, j1 = 2 * q4 + 1;
+          if (j0 >= nm) v4.x = v4.y = 0.0f;
+          if (j1 >= nm) v4.z = v4.w = 0.0f;
+          *reinterpret_cast<float4 *>(row + 4 * q4) = v4;
+          {
+            const float2 u = w.uvq[0][j0], v = w.uvq[1][j0];
+            dacc_fma(P, dfl{u.x, u.y}, dfl{v4.x, v4.y});
+            dacc_fma(Qs, dfl{v.x, v.y}, dfl{v4.x, v4.y});
+          }
+          if (j1 < NM) {
+            const float2 u = w.uvq[0][j1], v = w.uvq[1][j1];
+            dacc_fma(P, dfl{u.x, u.y}, dfl{v4.z, v4.w});
+            dacc_fma(Qs, dfl{v.x, v.y}, dfl{v4.z, v4.w});
+          }
+        }
+      } else {
+      const float xv[3] = {sx0[i], sx1[i], sx2[i]};
       dfl Q[3][DMAX + 1];
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
@@ -772,12 +803,11 @@ __device__ void df_pass(S &w, int d, int nm, int m, bool weighted, bool first, c
           dfl sk = df_make(w.Tm[v][0][k]);
 #pragma unroll
           for (int l = 1; l <= k; ++l) sk = df_add(sk, df_mulf(pw[l], w.Tm[v][l][k]));
-          Q[v][k] = (k <= d) ? sk : df_make(0.0f);
+          Q[v][k] = (k <= D) ? sk : df_make(0.0f);
         }
       }
-      float *row = stage + tid * LDD;
-      dacc P = {0.0f, 0.0f}, Qs = {0.0f, 0.0f};
-      float2 prev = make_float2(0.0f, 0.0f);
+      const int nmD = num_monomials(D);
+      float2 prev = make_float2(0.0f, 0.0f), prevs = prev;
       int j = 0;
 #pragma unroll
       for (int sd = 0; sd <= DMAX; ++sd)
@@ -790,16 +820,25 @@ __device__ void df_pass(S &w, int d, int nm, int m, bool weighted, bool first, c
             if (ea) ps = Q[0][ea];
             if (eb) ps = ea ? df_mul(ps, Q[1][eb]) : Q[1][eb];
             if (ec) ps = (ea || eb) ? df_mul(ps, Q[2][ec]) : Q[2][ec];
+            // the set's basis (degree D) to the slab, the fit's (degree d) here
+            const dfl pss = j < nmD ? ps : df_make(0.0f);
             if (j >= nm) ps = df_make(0.0f);
-            if (j & 1)
+            if (j & 1) {
               *reinterpret_cast<float4 *>(row + 2 * (j - 1)) = make_float4(prev.x, prev.y, ps.h, ps.l);
-            else
+              if (slab) slab[(size_t)i * NP4 + (j >> 1)] = make_float4(prevs.x, prevs.y, pss.h, pss.l);
+            } else {
               prev = make_float2(ps.h, ps.l);
+              prevs = make_float2(pss.h, pss.l);
+            }
             const float2 u = w.uvq[0][j], v = w.uvq[1][j];
             dacc_fma(P, dfl{u.x, u.y}, ps);
             dacc_fma(Qs, dfl{v.x, v.y}, ps);
           }
-      if (NM & 1) *reinterpret_cast<float4 *>(row + 2 * (NM - 1)) = make_float4(prev.x, prev.y, 0.0f, 0.0f);
+      if (NM & 1) {
+        *reinterpret_cast<float4 *>(row + 2 * (NM - 1)) = make_float4(prev.x, prev.y, 0.0f, 0.0f);
+        if (slab) slab[(size_t)i * NP4 + NP4 - 1] = make_float4(prevs.x, prevs.y, 0.0f, 0.0f);
+      }
+      }   // basis pairs
       const dfl pv = dacc_get(P), qv = dacc_get(Qs);
       pole |= !(qv.h > 0.0f);
       const dfl e = df_add(df_mulf(qv, yy), df_neg(pv));
@@ -1031,7 +1070,17 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
   const int64_t parts = a.point_off ? max(a.set_parts, 1) : 1;
   const int64_t run = (G + parts - 1) / parts;
   int64_t unit = blockIdx.x;
+  // this CTA's slab of the basis cache (accurate passes of the FP32 paths,
+  // point sets of at most MC samples), or null
+  float4 *slab = nullptr;
+  if constexpr (sizeof(Real) == 4 && WF::MC > 0) {
+    static_assert(WF::MC == kCacheSamples, "slab size");
+    constexpr size_t kSlabF4 = (size_t)WF::MC * ((NM + 1) / 2);
+    if (a.psi_cache && (size_t)(blockIdx.x + 1) * kSlabF4 * sizeof(float4) <= a.psi_cache_bytes)
+      slab = a.psi_cache + (size_t)blockIdx.x * kSlabF4;
+  }
   for (int claim = 0;; ++claim) {
+    bool psi_in_slab = false;   // the slab holds this claim's basis pairs
     if (a.counter) {
       if (tid == 0) w.next_fit[claim & 1] = (long long)atomicAdd(a.counter, 1ull);
       __syncthreads();
@@ -1827,7 +1876,9 @@ __global__ void __launch_bounds__(kT, (sizeof(Real) == 4 && DMAX <= 3) ? (GM == 
       int pole = 0;
       if (dfp) {
         if constexpr (sizeof(Real) == 4)
-          df_pass<DMAX, NM>(w, d, nm, m, a.weighted != 0, first_df, sx0, sx1, sx2, sy, obj, pole);
+          df_pass<DMAX, NM>(w, d, nm, m, a.weighted != 0, first_df, sx0, sx1, sx2, sy, obj, pole,
+                            cached ? slab : nullptr, psi_in_slab, D);
+        psi_in_slab = psi_in_slab || (slab != nullptr && cached);
         ++acc_passes;
         if (first_df) {
           // exact sample means mu_j = S_j / m (pairs; mu_0 = 1), then the

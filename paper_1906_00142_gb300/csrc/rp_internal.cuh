@@ -88,8 +88,10 @@ size_t search_workspace_bytes(int64_t K, int64_t Q);
 
 cudaError_t launch_fit(const rp_fit_desc &desc, const float *x, const float *y,
                        const int64_t *fit_off, double *coef, float *coef32, double *box,
-                       int32_t *status, int32_t *rank, void *workspace, cudaStream_t s);
+                       int32_t *status, int32_t *rank, void *workspace, size_t workspace_bytes,
+                       cudaStream_t s);
 size_t fit_workspace_bytes(const rp_fit_desc &desc);
+size_t fit_cache_workspace_bytes(const rp_fit_desc &desc);   // + the basis cache
 cudaError_t fit_static_scratch(void **ptr, size_t *bytes);   // rp_fit_noalloc's scratch
 bool fit_precision_supported(int precision);
 int fit_max_ctas_per_sm(const rp_fit_desc &desc);   // residency limit of the launch desc selects

@@ -29,7 +29,7 @@ def gpu_fit(inst, precision, degree=None, max_refine=8, degrees=True, tol=1e-8):
     out = rp.rp_fit(dev(inst["x"]), dev(inst["y"]), dev(inst["fit_off"]), d,
                     precision=precision, max_refine=max_refine, tol=tol,
                     degrees=dev(inst["degree"]) if degrees else None)
-    return {k: host(v) for k, v in out.items()}
+    return {k: host(v) for k, v in out.items() if k != "workspace"}
 
 
 def compare(inst, g, ref=None, weighted=True):

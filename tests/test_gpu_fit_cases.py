@@ -51,7 +51,7 @@ def test_fit_unweighted_rows(precision):
     x, y, off, deg = inst["x"], inst["y"], inst["fit_off"], inst["degree"]
     out = rp.rp_fit(dev(x), dev(y), dev(off), 3, precision=precision, degrees=dev(deg),
                     weighted=False)
-    g = {k: host(v) for k, v in out.items()}
+    g = {k: host(v) for k, v in out.items() if k != "workspace"}
     compare(inst, g, weighted=False)
 
 
@@ -71,7 +71,7 @@ def test_fit_shared_point_sets(precision, degrees):
     d = int(inst["degree"].max())
     out = rp.rp_fit(dev(xp), dev(inst["y"]), dev(inst["fit_off"]), d, precision=precision,
                     degrees=dev(inst["degree"]), point_off=dev(poff), fits_per_point_set=8)
-    g = {k: host(v) for k, v in out.items()}
+    g = {k: host(v) for k, v in out.items() if k != "workspace"}
     assert not (g["status"] & rp.RP_FIT_TIMEOUT).any()
     compare(inst, g)
     # a fit whose value count differs from its set's point count: empty
@@ -106,7 +106,7 @@ def test_fit_svd_solver(precision):
                 degree=np.concatenate([base["degree"], np.full(2, 3, np.int8)]))
     out = rp.rp_fit(dev(inst["x"]), dev(inst["y"]), dev(inst["fit_off"]), 3, precision=precision,
                     degrees=dev(inst["degree"]), solver="svd")
-    g = {k: host(v) for k, v in out.items()}
+    g = {k: host(v) for k, v in out.items() if k != "workspace"}
     ref = oracle.fit(inst["x"], inst["y"], inst["fit_off"], inst["degree"])
     compare(inst, g, ref)
     rd = (ref["status"] & oracle.FS_RANK_DEFICIENT) != 0

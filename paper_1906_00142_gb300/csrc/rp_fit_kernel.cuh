@@ -722,7 +722,9 @@ __device__ float apply_step(S &w, int nm, int n) {
 // with Dot2 (column phase; 64-bit loads of the pairs).  Results: hkd[0..2][j]
 // (pairs, block totals), the objective sum r^2 and whether q <= 0 at some
 // sample.
-// slab (or null): this CTA's basis cache.  The basis pairs depend only on
+// slab (or null): this CTA's basis cache, float4 q (pairs 2q, 2q + 1) of
+// sample i at q kCacheSamples + i (a warp's accesses are consecutive
+// 16-byte words).  The basis pairs depend only on
 // the point set's samples and basis (degree D, the set's largest), not on
 // the fit: the first accurate pass of a claim computes them and writes them
 // there (slab_full false), the claim's later accurate passes read them back
@@ -762,10 +764,9 @@ __device__ void df_pass(S &w, int d, int nm, int m, bool weighted, bool first, c
       dacc P = {0.0f, 0.0f}, Qs = {0.0f, 0.0f};
       if (slab && slab_full) {
         // the sample's basis pairs from the slab
-        const float4 *src = slab + (size_t)i * NP4;
 #pragma unroll
         for (int q4 = 0; q4 < NP4; ++q4) {
-          float4 v4 = src[q4];
+          float4 v4 = __ldcg(slab + (size_t)q4 * kCacheSamples + i);   // L2 only
           const int j0 = 2 * q4, j1 = 2 * q4 + 1;
           if (j0 >= nm) v4.x = v4.y = 0.0f;
           if (j1 >= nm) v4.z = v4.w = 0.0f;
@@ -825,7 +826,7 @@ __device__ void df_pass(S &w, int d, int nm, int m, bool weighted, bool first, c
             if (j >= nm) ps = df_make(0.0f);
             if (j & 1) {
               *reinterpret_cast<float4 *>(row + 2 * (j - 1)) = make_float4(prev.x, prev.y, ps.h, ps.l);
-              if (slab) slab[(size_t)i * NP4 + (j >> 1)] = make_float4(prevs.x, prevs.y, pss.h, pss.l);
+              if (slab) __stcg(slab + (size_t)(j >> 1) * kCacheSamples + i, make_float4(prevs.x, prevs.y, pss.h, pss.l));
             } else {
               prev = make_float2(ps.h, ps.l);
               prevs = make_float2(pss.h, pss.l);
@@ -836,7 +837,7 @@ __device__ void df_pass(S &w, int d, int nm, int m, bool weighted, bool first, c
           }
       if (NM & 1) {
         *reinterpret_cast<float4 *>(row + 2 * (NM - 1)) = make_float4(prev.x, prev.y, 0.0f, 0.0f);
-        if (slab) slab[(size_t)i * NP4 + NP4 - 1] = make_float4(prevs.x, prevs.y, 0.0f, 0.0f);
+        if (slab) __stcg(slab + (size_t)(NP4 - 1) * kCacheSamples + i, make_float4(prevs.x, prevs.y, 0.0f, 0.0f));
       }
       }   // basis pairs
       const dfl pv = dacc_get(P), qv = dacc_get(Qs);

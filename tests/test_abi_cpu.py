@@ -90,6 +90,13 @@ def test_tuning_argument_validation_without_launch(lib):
     ws = C.c_size_t(0)
     d = rp.FitDesc(5, 100, 3, 1, 4, 0, 1e-12, None)
     assert lib.rp_fit_workspace_size(C.byref(d), C.byref(ws)) == 0 and ws.value == 32
+    # the basis cache: none at FP64 precision (the counters only); bad
+    # arguments rejected
+    d64 = rp.FitDesc(5, 100, 3, 0, 4, 0, 1e-12, None)
+    assert lib.rp_fit_cache_workspace_size(C.byref(d64), C.byref(ws)) == 0 and ws.value == 32
+    assert lib.rp_fit_cache_workspace_size(C.byref(d), None) == -1
+    bad = rp.FitDesc(5, 100, 9, 1, 4, 0, 1e-12, None)
+    assert lib.rp_fit_cache_workspace_size(C.byref(bad), C.byref(ws)) == -1
 
 
 def test_search_workspace_size(lib):

@@ -3,6 +3,7 @@ shared-memory sample cache (512) and far beyond it, unweighted rows
 (RP_FIT_UNWEIGHTED), and batches of a single degree 1 or 4."""
 import numpy as np
 import pytest
+import torch
 
 import oracle
 import paper_1906_00142_gb300 as rp
@@ -80,6 +81,34 @@ def test_fit_shared_point_sets(precision, degrees):
                      fits_per_point_set=8)
     st = host(out2["status"])
     assert (st[-8:] & rp.RP_FIT_EMPTY).all()
+
+
+@pytest.mark.parametrize("precision,degrees", [("fp32", None), ("tf32", None), ("fp32", (2, 3))])
+def test_basis_cache_leaves_results_unchanged(precision, degrees):
+    """The accurate passes' basis cache (a workspace of
+    rp_fit_cache_workspace_size bytes) changes no output bit: the same fits
+    with the cache (dynamic schedule) and without any workspace (static
+    schedule, no cache), on shared point sets whose fits reuse the slab, and
+    on sets whose fits have different degrees (the slab holds the set's
+    degree-D basis, a lower-degree fit uses its leading part)."""
+    need_gpu()
+    if degrees is None:
+        inst = W.batched_instance(24, seed=131, m=512, d=3)
+    else:
+        inst = W.batched_instance(24, seed=132, degree_choices=degrees, m_range=(64, 512))
+    xp, poff = W.shared_points(inst)
+    d = int(inst["degree"].max())
+    args = (dev(xp), dev(inst["y"]), dev(inst["fit_off"]), d)
+    kw = dict(precision=precision, degrees=dev(inst["degree"]), point_off=dev(poff), fits_per_point_set=8)
+    cached = rp.rp_fit(*args, **kw)
+    ws = cached["workspace"]
+    assert ws.numel() >= 256 and ws.numel() == rp.rp_fit_cache_workspace_size(
+        rp.FitDesc(len(inst["fit_off"]) - 1, len(inst["y"]), d, rp.PREC[precision], 8, 0, 1e-8, None))
+    plain = rp.rp_fit(*args, schedule="static", **kw)
+    for k in ("coef", "coef32", "box", "status", "rank"):
+        assert torch.equal(cached[k], plain[k]), k
+    acc = (host(cached["status"]) >> 16) & 255
+    assert acc.max() >= 2          # later accurate passes of a claim read the slab
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])

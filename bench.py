@@ -8,7 +8,7 @@ One step = the whole path over one batch of synthetic input:
 Metric: rational fits/s of the whole step (the step's queries/s is reported
 beside it), timed over a stream of steps: step k+1's fit runs on a
 high-priority stream while step k's pack and search run on a second one
-(two buffer sets; the serial step time is reported beside it).  Inputs are
+(three buffer sets; the serial step time is reported beside it).  Inputs are
 resident in HBM before timing; L2 is flushed (160 MiB write, inside the
 timed region) before each step's fit.
 
@@ -285,9 +285,10 @@ def oracle_rates(inst, q, gd, budget_s=20.0):
     nf = nk * N_METRICS
     step_s = (t_fit / nf) * N_KERNELS * N_METRICS + (t_pack / nk) * N_KERNELS + \
         (t_search / max(nq, 1)) * N_QUERIES
-    sample = (f"{nf} fits ({nk} kernels), pack of {nk} kernels, {nq} queries; "
-              f"scaled to {N_KERNELS * N_METRICS} fits + {N_QUERIES} queries per step")
     full = nf == N_KERNELS * N_METRICS and nq == N_QUERIES
+    sample = (f"{nf} fits ({nk} kernels), pack of {nk} kernels, {nq} queries; " +
+              ("the whole step" if full else
+               f"scaled to {N_KERNELS * N_METRICS} fits + {N_QUERIES} queries per step"))
     return dict(step_s=step_s, cores=oracle.get_threads(), sample=sample,
                 wall_s=t_fit + t_pack + t_search, scaled=not full,
                 fit_s=t_fit / nf, search_s=t_search / max(nq, 1),
@@ -862,7 +863,7 @@ def main():
     # The headline: the same steps as a stream of batches on two compute
     # streams.  Step k's fit runs on the fit stream; its pack and search run
     # on the evaluation stream once the fit is done, while step k+1's fit
-    # starts on the fit stream (two sets of fit outputs, programs and search
+    # starts on the fit stream (three sets of fit outputs, programs and search
     # outputs).  The search of step k then fills the SMs that step k+1's fit
     # has not yet taken and those the FP64 launch of a step leaves idle.
     # Every step does all of its work; L2 is flushed before each fit (the
@@ -1029,7 +1030,7 @@ def main():
     e2e_serial_ms = max_over_ranks(statistics.mean(e_ms) if e_ms else float("nan"), ws, dev)
 
     # end to end as a stream of batches: the two-stream schedule above with
-    # every step's inputs copied in and results copied out (two buffer sets)
+    # every step's inputs copied in and results copied out (three buffer sets)
     pipe_io["h"] = h
     pipe_io["in"] = [d_in] + [{k: torch.empty_like(v) for k, v in d_in.items()} for _ in range(NB - 1)]
     pipe_io["out"] = [h_out] + [{k: torch.empty_like(v).pin_memory() for k, v in h_out.items()}
@@ -1100,10 +1101,10 @@ def main():
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                         "pipelined": "the two-stream schedule of the headline with each step's "
                                      "copy-in on a copy stream ahead of its fit and its copy-out on a "
-                                     "second copy stream (two buffer sets); L2 flushed before each fit",
+                                     "second copy stream (three buffer sets); L2 flushed before each fit",
                         "serial_ms_per_step": e2e_serial_ms},
                 "schedule": {"pipelined": "fit of step k+1 on a high-priority stream while pack + search "
-                                          "of step k run on a second (two buffer sets); L2 flushed before "
+                                          "of step k run on a second (three buffer sets); L2 flushed before "
                                           "each fit, inside the timed region",
                              "serial_ms_per_step": serial_ms_per_step},
                 "gpu_launches": {"all": 3 + search_launches, "fit": 2,

@@ -954,8 +954,9 @@ def main():
     ms_per_step = max_over_ranks(pipe_ms, ws, dev)
     value = job_rate(ws, F, ms_per_step)
     # the pipelined steps reproduce the serial steps' results
-    assert all(torch.equal(p_srch[b]["argmin"], p_srch[0]["argmin"]) for b in range(NB)), \
-        "pipelined argmin mismatch"
+    if args.only == "all":
+        assert all(torch.equal(p_srch[b]["argmin"], p_srch[0]["argmin"]) for b in range(NB)), \
+            "pipelined argmin mismatch"
 
     # the timed steps' results, kept for the comparison with the oracle
     g_res = {"coef": fit_out["coef"].cpu().numpy(), "box": fit_out["box"].cpu().numpy(),

@@ -78,8 +78,10 @@ typedef enum rp_status {
 #define RP_FIT_ACC_MASK 0xFF0000
 #define RP_FIT_FP64_PASS (1 << 24) /* FP32 and tensor-core precisions: the fit's own solve dropped
                                      pivots at its drop tolerance or stopped short of tol, so the
-                                     fit was solved again with RP_PREC_FP64 arithmetic (the
-                                     other bits then describe that solve) */
+                                     fit was solved again with RP_PREC_FP64 arithmetic (its basis
+                                     and design Grams summed in double-float arithmetic from FP64
+                                     rows, ~1e-14 relative; the other bits then describe that
+                                     solve) */
 
 /* Per-query status bits (rp_eval_search). */
 #define RP_Q_NO_VALID 1           /* no configuration valid: argmin = -1 */

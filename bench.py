@@ -44,8 +44,8 @@ WORKLOAD = ("batched fit 1024 kernels x 8 metrics (the metrics of a kernel share
 # 2048 fits of 512 samples in the shared-point layout; traffic scales with
 # the fit count), valid only for the kernel sources they were taken on
 # (SHA-256 of the files below) and that layout.
-FIT_TRAFFIC = {"sources_sha256": "ecfb0fdc136e6c2c3e8ba645ca9dad1bcdad47a3c38af3c581a4ed3041fea4f4",
-               "bytes_per_fit": (6360832 + 3547136) / 2048, "layout": "shared point sets"}
+FIT_TRAFFIC = {"sources_sha256": "9acbc2561a56b06c2fb9041ae7b1e02fb4b25b0537a0dbc0ca92fe0f700b006c",
+               "bytes_per_fit": (6259968 + 2311680) / 2048, "layout": "shared point sets"}
 FIT_SOURCES = ("paper_1906_00142_gb300/csrc/rp_fit_kernel.cuh", "paper_1906_00142_gb300/csrc/rp_fit.cuh",
                "paper_1906_00142_gb300/csrc/rp_fit_f32.cu", "paper_1906_00142_gb300/csrc/rp_tc.cuh")
 

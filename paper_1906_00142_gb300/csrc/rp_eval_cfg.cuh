@@ -22,25 +22,27 @@ struct HwC {
   float issue;
 };
 
-// #Rep = ceil(c0 c1 / D) for c0 c1 >= 1 (c0, c1 < 2^32) and 1 <= D < 2^22.
-// Exact when the quotient is below 2^22: the float estimate q0 is then within
-// 2 of it, so the remainder c0 c1 - q0 D lies in (-3D, 4D), is formed exactly
-// in 32-bit wrap-around arithmetic and is exact in FP32; its ceiling quotient
-// by D is rounded up and corrected with exact FMA residuals.  Above 2^22 the
-// float estimate (relative error < 2^-21) is used.
+// #Rep = ceil(c0 c1 / D) for 1 <= c0, c1 < 2^32 and 1 <= D < 2^30.
+// The float estimate qf of the quotient is within 6 float roundings (3.6e-7
+// relative) of it.  Below 2^20 it is therefore within 0.4 of the quotient,
+// so q0 = floor(qf) leaves a remainder r = c0 c1 - q0 D in (-D, 2D), exact in
+// 32-bit wrap-around arithmetic, and the ceiling is q0 + [r > 0] + [r > D].
+// Above 2^20 ceil(qf) is used (relative error below 1.4e-6).
 __device__ __forceinline__ float rep_count(uint32_t c0, uint32_t c1, uint32_t D) {
-  const float Df = (float)D;
-  const float qf = __fdividef((float)c0 * (float)c1, Df);
-  const uint32_t q0 = (uint32_t)fminf(qf, 4194304.0f);
-  const float rf = (float)(int32_t)(c0 * c1 - q0 * D);
-  float k = ceilf(__fdividef(rf, Df));
-  k += fmaf(k, Df, -rf) < 0.0f ? 1.0f : 0.0f;
-  k -= fmaf(k - 1.0f, Df, -rf) >= 0.0f ? 1.0f : 0.0f;
-  return qf < 4194304.0f ? (float)q0 + k : ceilf(qf);
+  const float qf = __fdividef((float)c0 * (float)c1, (float)D);
+  const uint32_t q0 = (uint32_t)fminf(qf, 1048576.0f);
+  const int32_t r = (int32_t)(c0 * c1 - q0 * D);
+  const uint32_t q = q0 + (r > 0 ? 1u : 0u) + (r > (int32_t)D ? 1u : 0u);
+  return qf < 1048576.0f ? (float)q : ceilf(qf);
 }
 
-// floor(a / b) for 0 <= a < 2^24, 1 <= b < 2^24 (exact).
+// floor(a / b) for 0 <= a < 2^24, 1 <= b < 2^24 (exact).  Below 2^21 the
+// quotient of a + 1/2 lies at least 1/(2b) from every integer and
+// __fdividef's error (2 ulp, under (a + 1/2) 2^-22 / b) is smaller, so its
+// truncation is the floor; above, the estimate is corrected (a is a table or
+// hardware constant: the branch is uniform across a warp).
 __device__ __forceinline__ int floor_div_small(int a, int b) {
+  if (a < (1 << 21)) return (int)__fdividef((float)a + 0.5f, (float)b);
   int q = (int)(__fdividef((float)a, (float)b));
   q -= (q * b > a);
   q += ((q + 1) * b <= a);

@@ -133,6 +133,13 @@ std::string codegen_source(const void *program_host, int64_t K, int d, int64_t k
            "    const float4 *__restrict__ q, long long Q, int *argmin, float *best, float *second,\n"
            "    int *status) {\n"
            "  using namespace rpk;\n"
+           "  // the coefficient table in shared memory: every lane of a warp reads\n"
+           "  // the same row (broadcast 16-byte loads)\n"
+           "  __shared__ float4 s_tab[sizeof(g_tab) / 16];\n"
+           "  for (int j = threadIdx.x; j < (int)(sizeof(g_tab) / 16); j += blockDim.x)\n"
+           "    s_tab[j] = reinterpret_cast<const float4 *>(g_tab)[j];\n"
+           "  __syncthreads();\n"
+           "  const float *tab = reinterpret_cast<const float *>(s_tab);\n"
            "  CfgTab cfg;\n"
            "  for (int c = 0; c < kNcfg; ++c) {\n"
            "    cfg.la[c] = kLa[c]; cfg.lb[c] = kLb[c]; cfg.wpb[c] = kWpb[c];\n"
@@ -156,7 +163,7 @@ std::string codegen_source(const void *program_host, int64_t K, int d, int64_t k
            "    } else {\n"
            "      bool any_pole = false;\n"
            "      for (int c = 0; c < kNcfg; ++c) {\n"
-           "        const CfgOut o = eval_cfg<%d, true>(c, s, g_tab, cfg, hw);\n"
+           "        const CfgOut o = eval_cfg<%d, true>(c, s, tab, cfg, hw);\n"
            "        any_pole |= o.pole;\n"
            "        const bool better = o.ex < b1;\n"
            "        const bool second_better = !better && o.ex < b2;\n"
